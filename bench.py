@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark: lower-bound evaluations per second at n x m = 200 x 20.
+
+One step bounds the whole 200x20 pool (262,144 random-prefix nodes, seed 2)
+with fsp_bound_pool: every node's prefix recurrence, release/latency minima
+and the filtered Johnson scan of all 190 machine couples, i.e. one full pass
+of the bounding operator.  Inputs are resident in HBM before the timed region;
+three copies of the pool (3 x 105 MB > the 129 MB L2) are used in rotation so
+no step finds its input in L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank bounds its own pool
+of the same size (weak scaling, no collective on the data path; the ranks
+meet only in the barriers and the max-over-ranks of the timing).
+``--impl reference`` times the CPU oracle (the plain C bounder, all host
+cores) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "pool_200x20"
+METRIC = "LB evals/s at n×m=200×20"
+UNIT = "nodes/s"
+
+
+def algorithmic_int_ops(n: int, m: int, depths: np.ndarray) -> float:
+    """Integer operations of the bound per the method's own cost model:
+    per couple one membership test for each of the n Johnson entries and four
+    updates (add, add, max, add) for each of the n' = n - d unscheduled ones;
+    per node 2mn for the release/latency minima and 2md for the prefix
+    recurrence.  Summed over the nodes of one launch."""
+    P = m * (m - 1) // 2
+    d = depths.astype(np.float64)
+    nu = n - d
+    return float(np.sum(P * (n + 4 * nu) + 2 * m * n + 2 * m * d))
+
+
+def kernel_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_1208_3933_gb300", "csrc", "fsp_bound.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def read_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "fsp_bound_kernel_pool_200x20.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def alu_peak_ops(sm_count: int, sm_max_mhz: float, lanes_per_sm: int) -> float:
+    return sm_count * lanes_per_sm * sm_max_mhz * 1e6
+
+
+# Integer operations per SM per clock behind the roofline: the add+max
+# pattern of the bound issues one add and one max per lane per clock on the
+# two integer-capable pipes (64 lanes each); the probe in
+# paper_1208_3933_gb300/microbench/alu_peak.cu measures 127 of 128
+# (python bench.py --alu-peak).
+ALU_LANES_PER_SM = 128
+
+
+def run_alu_peak():
+    import ctypes
+
+    import torch
+    from paper_1208_3933_gb300 import build
+    build.build()
+    lib = ctypes.CDLL(build.MICRO_LIB)
+    f = lib.fsp_microbench_alu
+    f.argtypes = [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_float)] * 2 + [ctypes.POINTER(ctypes.c_double)]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    names = ["add+max (the bound's recurrence)", "logic (one lop3 per step)", "imad", "fadd+fmax"]
+    for pat, name in zip([0, 2, 3, 4], names):
+        ms, mhz, ops = ctypes.c_float(), ctypes.c_float(), ctypes.c_double()
+        blocks = sms * 8
+        rc = f(pat, blocks, 2000, ctypes.byref(ms), ctypes.byref(mhz), ctypes.byref(ops))
+        total = ops.value * blocks * 256
+        if pat == 2:
+            total /= 2  # the compiler fuses the three logic ops into one lop3
+        rate = total / (ms.value * 1e-3)
+        print(json.dumps({"pattern": name, "rc": rc, "ms": round(ms.value, 4), "sm_mhz": round(mhz.value),
+                          "int_ops_per_s": rate, "ops_per_sm_per_clk": rate / sms / (mhz.value * 1e6),
+                          "sms": sms}), flush=True)
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl != "reference" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_pool(rank: int):
+    from paper_1208_3933_gb300 import workloads
+    w = workloads.named_pool(WORKLOAD)
+    if rank == 0:
+        return w
+    rng = np.random.default_rng([2, rank])
+    rows, depths = workloads.random_pool(rng, w.n, w.N)
+    return workloads.PoolWorkload(w.name, w.n, w.m, w.seed, w.p, rows, depths)
+
+
+def cpu_oracle_rate(w, seconds: float = 2.0, threads: int | None = None):
+    """Times the oracle as it stands on a bounded sample of the pool, on all
+    host cores (the single-threaded C routine on disjoint chunks)."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    t = oracle.Tables(w.p)
+    probe = min(w.N, 64 * threads)
+    t0 = time.perf_counter()
+    t.lb_pool(w.rows[:probe], w.depths[:probe], threads=threads)
+    rate = probe / max(time.perf_counter() - t0, 1e-9)
+    sample = int(min(w.N, max(threads, rate * seconds)))
+    t0 = time.perf_counter()
+    t.lb_pool(w.rows[:sample], w.depths[:sample], threads=threads)
+    dt = time.perf_counter() - t0
+    return sample / dt, sample, dt, threads
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle, rank 0 only, on the same workload."""
+    if rank != 0:
+        return
+    from paper_1208_3933_gb300 import workloads
+    w = workloads.named_pool(WORKLOAD)
+    threads = os.cpu_count() or 1
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, seconds=min(per_step, 2.0), threads=threads)
+    rates, samples, secs = [], [], []
+    for _ in range(args.steps):
+        r, s, dt, _ = cpu_oracle_rate(w, seconds=min(per_step, 5.0), threads=threads)
+        rates.append(r)
+        samples.append(s)
+        secs.append(dt)
+    total_nodes, total_s = float(sum(samples)), float(sum(secs))
+    value = total_nodes / total_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": w.n, "m": w.m, "nodes": w.N, "seed": w.seed},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"first {samples[0]} nodes of the 262,144-node pool per step, bounded by the "
+                                   f"plain C oracle on {threads} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+    from paper_1208_3933_gb300 import build, fsp
+
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = rank_pool(rank)
+    if args.nodes:
+        from paper_1208_3933_gb300 import workloads
+        w = workloads.PoolWorkload(w.name, w.n, w.m, w.seed, w.p, np.ascontiguousarray(w.rows[:args.nodes]),
+                                   np.ascontiguousarray(w.depths[:args.nodes]))
+    inst = fsp.Instance(w.p)
+    copies = 3
+    rows_d = [torch.from_numpy(w.rows).to(dev) for _ in range(copies)]
+    dep_d = [torch.from_numpy(w.depths).to(dev) for _ in range(copies)]
+    outs = [torch.empty(w.N, dtype=torch.int32, device=dev) for _ in range(copies)]
+    stream = torch.cuda.current_stream(dev)
+
+    for i in range(args.warmup):
+        fsp.fsp_bound_pool(inst, rows_d[i % copies], dep_d[i % copies], outs[i % copies], stream=stream)
+    torch.cuda.synchronize(dev)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    region0 = torch.cuda.Event(enable_timing=True)
+    region1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    with sampler:
+        time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        region0.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            fsp.fsp_bound_pool(inst, rows_d[i % copies], dep_d[i % copies], outs[i % copies], stream=stream)
+            ev[i][1].record(stream)
+        region1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+    region_ms = region0.elapsed_time(region1)
+    kernel_ms = [a.elapsed_time(b) for a, b in ev]
+    region_ms_max = max_over_ranks(world, region_ms)
+    nodes_total = float(w.N) * args.steps * world
+    value = nodes_total / (region_ms_max * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers: H2D of the pool,
+    # bounding, D2H of the bounds, every step
+    h_rows = torch.from_numpy(w.rows).pin_memory()
+    h_dep = torch.from_numpy(w.depths).pin_memory()
+    h_out = torch.empty(w.N, dtype=torch.int32).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        fsp.fsp_bound_pool_host(inst, h_rows, h_dep, h_out, stream=stream)
+    barrier(world)
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fsp.fsp_bound_pool_host(inst, h_rows, h_dep, h_out, stream=stream)
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e_value = float(w.N) * e2e_steps * world / e2e_s
+    ok_e2e = bool(np.array_equal(h_out.numpy(), outs[0].cpu().numpy()))
+
+    if rank != 0:
+        return
+    clocks = sampler.summary()
+    ops = algorithmic_int_ops(w.n, w.m, w.depths)
+    mean_kernel_s = statistics.mean(kernel_ms) * 1e-3
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clocks["sm_max_mhz"] or 2070.0
+    peak = alu_peak_ops(props.multi_processor_count, sm_max, ALU_LANES_PER_SM)
+    achieved = ops / mean_kernel_s
+    cpu_rate, cpu_sample, cpu_s, cpu_threads = cpu_oracle_rate(w, seconds=2.0)
+    info = inst.info()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": region_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": w.n, "m": w.m, "nodes_per_step_per_gpu": w.N, "seed": w.seed,
+                   "p": "U[1,99]", "depth": "U{0..199}", "records": "compact" if info.compact else "wide",
+                   "l2": "3 rotating pool copies of 105 MB (inputs larger than the 129 MB L2)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "int-ops/s",
+                     "frac": achieved / peak, "traffic": read_traffic(),
+                     "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} int32 lanes x "
+                                   f"{sm_max:.0f} MHz", "ops_per_launch": ops,
+                     "kernel_ms_mean": mean_kernel_s * 1e3},
+        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
+                         "sample": f"first {cpu_sample} nodes of the pool, plain C oracle on {cpu_threads} threads, "
+                                   f"{cpu_s:.1f} s"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(w.rows.nbytes + w.depths.nbytes),
+                "d2h_bytes_per_step": int(4 * w.N), "bit_exact_vs_device": ok_e2e},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    inst.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--nodes", type=int, default=0,
+                    help="bound only the first NODES nodes of the pool (small profiling cases)")
+    ap.add_argument("--alu-peak", action="store_true", help="run the integer-pipe throughput probe and exit")
+    args = ap.parse_args()
+    if args.alu_peak:
+        run_alu_peak()
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_gpu(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * fsp.h -- C ABI of the GB300 library for batched evaluation of the
+ * two-machine lower bound of the permutation flow-shop problem.
+ *
+ * Method: Melab, Chakroun, Mezmaz, Tuyttens, "A GPU-accelerated
+ * Branch-and-Bound Algorithm for the Flow-Shop Scheduling Problem"
+ * (arXiv:1208.3933).  Problem statement: Section II-B (n jobs visit machines
+ * M_1..M_m in order, one permutation for every machine, minimise the
+ * makespan).  Bound: Section II-C (Lageweg, Lenstra and Rinnooy Kan's
+ * generalisation of Johnson's two-machine rule), Section II-D (tables PTM,
+ * LM, JM, RM, QM, MM; Table I) and the figure "Pseudo-code implementing the
+ * LB function".  Parallel model: Section III-A (the pool of sub-problems is
+ * bounded on the GPU, one evaluation per sub-problem).
+ *
+ * Conventions for every entry point:
+ *   - Jobs are numbered 0..n-1 and machines 0..m-1.
+ *   - A node (sub-problem) is a scheduled prefix sigma of d distinct jobs;
+ *     its unscheduled set U is every other job.  A pool of N nodes is an
+ *     int16 matrix [N][n] (row-major; only the first d entries of a row are
+ *     read, the rest is ignored) plus an int32 vector of depths [N].
+ *   - The caller owns every buffer it passes; the library keeps no pointer
+ *     to it after the call returns (or, for stream-ordered calls, after the
+ *     enqueued work completes).
+ *   - "device" pointers are CUDA global-memory pointers on the device that
+ *     was current when the instance was created; "host" pointers are
+ *     ordinary (pinned or pageable) host memory.
+ *   - Every error that can be detected on the host is returned at once and
+ *     nothing is enqueued.  Bad rows never fault: their bound is
+ *     FSP_LB_INVALID.
+ *   - Entry points are thread-safe for distinct instances; one instance may
+ *     be used by several threads for stream-ordered bounding.
+ */
+#ifndef FSP_H
+#define FSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque instance: the processing times plus every per-instance table of
+ * Section II-D, kept resident on the device for the instance's lifetime. */
+typedef struct fsp_instance fsp_instance;
+
+typedef enum fsp_status {
+    FSP_OK = 0,
+    FSP_EINVAL = -1,     /* a bad argument (null pointer, size out of range, wrong device) */
+    FSP_ENOMEM = -2,     /* host or device allocation failed */
+    FSP_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+    FSP_EBADNODE = -4,   /* (B&B only) an internal node failed validation */
+    FSP_ETIMEDOUT = -5,  /* a bounded device- or host-side wait ran out */
+    FSP_ENOTFOUND = -6,  /* branch-and-bound: no schedule of makespan <= ub0 */
+    FSP_EBUSY = -7       /* a server refused work (shut down or over budget) */
+} fsp_status;
+
+/* Bound written for a row whose depth is outside [0,n], whose prefix holds a
+ * job outside [0,n) or holds a job twice. */
+#define FSP_LB_INVALID (-1)
+
+/* Limits of fsp_instance_create. */
+#define FSP_MAX_JOBS 1024
+#define FSP_MAX_MACHINES 32
+
+/* Read-only facts about an instance (fsp_instance_query). */
+typedef struct fsp_instance_info {
+    int32_t n;              /* jobs */
+    int32_t m;              /* machines */
+    int32_t pairs;          /* machine couples k<l: m(m-1)/2 */
+    int32_t compact;        /* 1: 32-bit Johnson records, 0: 128-bit records */
+    int64_t device_bytes;   /* device memory held by the instance */
+    int32_t device;         /* CUDA ordinal the tables live on */
+    int32_t reserved;
+} fsp_instance_info;
+
+/* Launch shape of the bounding kernel.  Zero in any field means "choose":
+ * the library then uses the autotuned shape for this instance and pool size
+ * when one is cached, else its built-in heuristic. */
+typedef struct fsp_launch_config {
+    int32_t nodes_per_thread;  /* K in {1,2,4,8}: nodes one thread bounds in lockstep */
+    int32_t blocks_per_sm;     /* resident blocks per SM (1 or 2) */
+    int32_t pairs_per_tile;    /* machine couples staged in shared memory at a time */
+    int32_t reserved;
+} fsp_launch_config;
+
+/*
+ * fsp_instance_create -- builds the tables of Section II-D once per instance
+ * ("computed once at the beginning of the algorithm") and uploads them to the
+ * current CUDA device.
+ *   p    host, row-major [n][m] int32 processing times p_jk >= 0, copied;
+ *   n    1 <= n <= FSP_MAX_JOBS;  m  2 <= m <= FSP_MAX_MACHINES;
+ *        the sum of all p_jk must be below 2^30 (every time the bound forms
+ *        then fits in int32);
+ *   out  receives the new instance (NULL on failure).
+ * Errors: FSP_EINVAL for a bad argument (checked before any CUDA call),
+ * FSP_ENOMEM, FSP_ECUDA.
+ */
+fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m, fsp_instance **out);
+
+/* Frees the instance and its device tables.  NULL is a no-op.  No bounding
+ * call on this instance may be in flight. */
+void fsp_instance_destroy(fsp_instance *inst);
+
+/* Fills *info.  Errors: FSP_EINVAL for a NULL argument. */
+fsp_status fsp_instance_query(const fsp_instance *inst, fsp_instance_info *info);
+
+/*
+ * fsp_bound_pool -- the bounding operator of Section III-A over one pool:
+ * for every node x, out_lb[x] = max over couples (k,l), k<l, of the
+ * two-machine-with-lags value of the figure "Pseudo-code implementing the LB
+ * function" (release times from the prefix, Johnson order filtered to U,
+ * minimum latency of machine l), or FSP_LB_INVALID for a bad row.
+ *   nodes   device int16 [N][n], row-major (read-only);
+ *   depths  device int32 [N] (read-only);
+ *   N       number of nodes, N >= 0 (0 enqueues nothing);
+ *   out_lb  device int32 [N] (written);
+ *   cuda_stream  a cudaStream_t, or NULL for the legacy default stream.
+ * Stream-ordered: returns once the work is enqueued.
+ * Errors: FSP_EINVAL (NULL pointers with N > 0, N < 0, current device is not
+ * the instance's), FSP_ECUDA (launch failure).  A device-side wait that ran
+ * out is reported by the next call on the instance as FSP_ETIMEDOUT.
+ */
+fsp_status fsp_bound_pool(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths,
+                          int64_t N, int32_t *out_lb, void *cuda_stream);
+
+/* fsp_bound_pool with an explicit launch shape (cfg may be NULL = choose).
+ * Errors as fsp_bound_pool, plus FSP_EINVAL for a shape that cannot run. */
+fsp_status fsp_bound_pool_ex(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths,
+                             int64_t N, int32_t *out_lb, void *cuda_stream,
+                             const fsp_launch_config *cfg);
+
+/*
+ * fsp_bound_pool_host -- the paper's accounting of one pool (Section III-A:
+ * the pool is off-loaded to the device, the bounds are returned to the
+ * host): copies nodes and depths from host memory, bounds them, copies the
+ * bounds back, and returns when out_lb is filled.  The pool is moved in
+ * chunks so that copies and bounding overlap.  Device staging memory is
+ * taken from the stream-ordered allocator for the call's duration.
+ *   nodes host int16 [N][n]; depths host int32 [N]; out_lb host int32 [N].
+ *   cuda_stream orders the work (NULL = legacy default stream); the call
+ *   synchronises with it before returning.
+ * Errors as fsp_bound_pool, plus FSP_ENOMEM.
+ */
+fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_t *nodes,
+                               const int32_t *depths, int64_t N, int32_t *out_lb,
+                               void *cuda_stream);
+
+/*
+ * fsp_branch_and_bound -- depth-first B&B (Section II-A operators, Section
+ * II-B forward branching) with GPU bounding of every expanded node's
+ * children as one pool (Section III-A):
+ *   - UB starts at ub0 + 1 and there is no incumbent; the root is bounded;
+ *   - a popped node with LB >= UB is eliminated (the paper eliminates on
+ *     LB > UB; with UB = best + 1 this finds the same optimum);
+ *   - a popped leaf (depth n, whose bound is its makespan) becomes the
+ *     incumbent and UB := its makespan;
+ *   - the children of a popped inner node are bounded together, ordered by
+ *     (LB, job) ascending and pushed so the smallest is explored first;
+ *     children with LB >= UB are dropped.
+ *   ub0            any int32; FSP_ENOTFOUND if no schedule has makespan <= ub0;
+ *   best_perm      host int16 [n] (or NULL) receives an optimal permutation;
+ *   best_makespan  host (or NULL) receives its makespan;
+ *   nodes_bounded  host (or NULL) receives the number of bound evaluations.
+ * Synchronous; uses its own CUDA stream.
+ * Errors: FSP_EINVAL, FSP_ENOMEM, FSP_ECUDA, FSP_EBADNODE, FSP_ENOTFOUND.
+ */
+fsp_status fsp_branch_and_bound(const fsp_instance *inst, int32_t ub0, int16_t *best_perm,
+                                int32_t *best_makespan, int64_t *nodes_bounded);
+
+/* Static English text for a status code (never NULL). */
+const char *fsp_status_string(fsp_status s);
+
+/* Library version as "major.minor.patch" (static string). */
+const char *fsp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSP_H */

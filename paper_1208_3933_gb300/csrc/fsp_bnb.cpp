@@ -1,0 +1,148 @@
+// fsp_bnb.cpp -- depth-first branch-and-bound around the GPU bounding
+// operator (Section II-A operators; Section II-B forward branching: child i
+// of a node appends unscheduled job J_i to its prefix; Section III-A: the
+// children of an expanded node form one pool bounded on the device, the
+// bounds come back to the host for elimination and selection).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "fsp_internal.h"
+
+namespace {
+
+struct Node {
+    int32_t lb;
+    int32_t d;
+    std::vector<int16_t> row;
+};
+
+struct Child {
+    int32_t lb;
+    int32_t job;
+};
+
+}  // namespace
+
+extern "C" fsp_status fsp_branch_and_bound(const fsp_instance *inst, int32_t ub0, int16_t *best_perm,
+                                           int32_t *best_makespan, int64_t *nodes_bounded) {
+    if (!inst) return FSP_EINVAL;
+    fsp_status st = fspgb::check_device(inst);
+    if (st != FSP_OK) return st;
+    const int n = inst->n;
+
+    // Device and pinned host buffers for one pool of at most n children.
+    cudaStream_t s = nullptr;
+    int16_t *d_rows = nullptr, *h_rows = nullptr;
+    int32_t *d_dep = nullptr, *d_out = nullptr, *h_dep = nullptr, *h_out = nullptr;
+    auto cleanup = [&]() {
+        if (d_rows) cudaFree(d_rows);
+        if (d_dep) cudaFree(d_dep);
+        if (d_out) cudaFree(d_out);
+        if (h_rows) cudaFreeHost(h_rows);
+        if (h_dep) cudaFreeHost(h_dep);
+        if (h_out) cudaFreeHost(h_out);
+        if (s) cudaStreamDestroy(s);
+    };
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cleanup();
+        return FSP_ECUDA;
+    }
+    if (cudaMalloc((void **)&d_rows, sizeof(int16_t) * n * n) != cudaSuccess ||
+        cudaMalloc((void **)&d_dep, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc((void **)&d_out, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMallocHost((void **)&h_rows, sizeof(int16_t) * n * n) != cudaSuccess ||
+        cudaMallocHost((void **)&h_dep, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMallocHost((void **)&h_out, sizeof(int32_t) * n) != cudaSuccess) {
+        cleanup();
+        return FSP_ENOMEM;
+    }
+
+    // Bounds h_rows[0..cnt) on the device; results land in h_out.
+    auto bound = [&](int cnt) -> fsp_status {
+        if (cudaMemcpyAsync(d_rows, h_rows, sizeof(int16_t) * cnt * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(d_dep, h_dep, sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return FSP_ECUDA;
+        fsp_status r = fspgb::launch_bound(inst, d_rows, d_dep, cnt, d_out, s, nullptr);
+        if (r != FSP_OK) return r;
+        if (cudaMemcpyAsync(h_out, d_out, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return FSP_ECUDA;
+        r = fspgb::take_device_status(inst);
+        if (r != FSP_OK) return r;
+        for (int i = 0; i < cnt; ++i)
+            if (h_out[i] == FSP_LB_INVALID) return FSP_EBADNODE;
+        return FSP_OK;
+    };
+
+    int64_t UB = (int64_t)ub0 + 1;
+    bool found = false;
+    int64_t count = 0;
+    std::vector<int16_t> best(n, 0);
+    std::vector<Node> stack;
+    stack.reserve((size_t)n * n / 2 + 2);
+
+    // the root: empty prefix
+    std::memset(h_rows, 0, sizeof(int16_t) * n);
+    h_dep[0] = 0;
+    st = bound(1);
+    if (st != FSP_OK) {
+        cleanup();
+        return st;
+    }
+    ++count;
+    stack.push_back(Node{h_out[0], 0, std::vector<int16_t>(n, 0)});
+
+    std::vector<char> used(n);
+    std::vector<Child> kids;
+    kids.reserve(n);
+    while (!stack.empty()) {
+        Node nd = std::move(stack.back());
+        stack.pop_back();
+        if (nd.lb >= UB) continue;  // elimination
+        if (nd.d == n) {            // a leaf: its bound is its makespan
+            UB = nd.lb;
+            found = true;
+            best = nd.row;
+            continue;
+        }
+        // branching: one child per unscheduled job, in job order
+        std::fill(used.begin(), used.end(), 0);
+        for (int i = 0; i < nd.d; ++i) used[nd.row[i]] = 1;
+        int cnt = 0;
+        for (int j = 0; j < n; ++j) {
+            if (used[j]) continue;
+            int16_t *r = h_rows + (size_t)cnt * n;
+            std::memcpy(r, nd.row.data(), sizeof(int16_t) * nd.d);
+            r[nd.d] = (int16_t)j;
+            h_dep[cnt] = nd.d + 1;
+            ++cnt;
+        }
+        st = bound(cnt);  // bounding: the children as one pool
+        if (st != FSP_OK) {
+            cleanup();
+            return st;
+        }
+        count += cnt;
+        kids.clear();
+        for (int i = 0; i < cnt; ++i) kids.push_back(Child{h_out[i], h_rows[(size_t)i * n + nd.d]});
+        std::sort(kids.begin(), kids.end(), [](const Child &x, const Child &y) {
+            return x.lb != y.lb ? x.lb < y.lb : x.job < y.job;
+        });
+        // selection: depth first, smallest (LB, job) popped first
+        for (int t = cnt - 1; t >= 0; --t) {
+            if (kids[t].lb >= UB) continue;
+            Node c{kids[t].lb, nd.d + 1, nd.row};
+            c.row[nd.d] = (int16_t)kids[t].job;
+            stack.push_back(std::move(c));
+        }
+    }
+    cleanup();
+    if (nodes_bounded) *nodes_bounded = count;
+    if (!found) return FSP_ENOTFOUND;
+    if (best_makespan) *best_makespan = (int32_t)UB;
+    if (best_perm) std::memcpy(best_perm, best.data(), sizeof(int16_t) * n);
+    return FSP_OK;
+}

@@ -1,0 +1,660 @@
+// fsp_bound.cu -- the bounding operator of Section III-A on sm_103a: one
+// launch bounds a whole pool of sub-problems with the two-machine lower bound
+// of Section II-C (figure "Pseudo-code implementing the LB function").
+//
+// Work decomposition.  A block of 128 threads owns a tile of 128*K nodes;
+// thread t bounds nodes t, t+128, ..., t+128(K-1) of the tile in lockstep,
+// so every thread of a warp reads the same Johnson record at the same time
+// (a shared-memory broadcast) and only the per-node membership byte differs.
+// Blocks are persistent: each walks node tiles blockIdx.x, +gridDim.x, ...
+//
+// Per node (prefix sigma of depth d, unscheduled set U):
+//   1. flags:  byte flags[j][t] holds bit b = "job j in U for node b of t";
+//   2. prefix: C(sigma,k) by the flow-shop recurrence (Section II-B);
+//   3. A_k = r_k + S_k with r_k = max(C(sigma,k), min_{j in U} sum_{h<k} p_jh)
+//      (RM) and S_k = sum_{j in U} p_jk;
+//   4. for every machine l: q_l = min_{j in U} sum_{h>l} p_jh (QM) and the
+//      term A_l + q_l;
+//   5. for every couple (k,l): the filtered Johnson scan, run on the slack
+//      u = timeOnM2 - timeOnM1 of the pseudo-code.  Lines (11)-(15) update
+//      timeOnM1 += p_jk; timeOnM2 = max(timeOnM2, timeOnM1 + lag_j) + p_jl,
+//      which is u <- max(u + delta_j, s_j) with delta_j = p_jl - p_jk and
+//      s_j = lag_j + p_jl.  That map composes to u_end = max(u_0 + S_l - S_k,
+//      F(0)), where F(0) is the scan started from u = 0, and since
+//      u_0 = r_l - r_k >= 0 the couple's value (line (18)) is
+//          max(A_l + q_l, A_k + q_l + F(0)).
+//      The scan therefore needs neither release time: it starts at 0 and
+//      is the only O(n) loop per couple;
+//   6. LB = max over all terms (line (19)), or FSP_LB_INVALID for a bad row.
+// Scheduled jobs and padding entries leave u unchanged: for a scheduled job
+// the update is skipped, and padding records (delta = s = 0) map u >= 0 to
+// itself.
+//
+// Shared memory: the Johnson records of a tile of couples (double-buffered,
+// staged with cp.async.bulk and an mbarrier), the couple list, A [m][K][128]
+// and the flags [n][128].  When all couples fit in the two buffers they are
+// staged once per block and stay resident; otherwise the couple tiles are
+// re-staged for every node tile, overlapped with the scan of the previous
+// tile (the paper's "does not fit" case, Section IV-B).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "fsp_internal.h"
+
+namespace fspgb {
+
+struct BoundArgs {
+    const unsigned char *rec;
+    const uint8_t *pairs;
+    const int32_t *p, *head, *tail, *ptm;
+    const int16_t *nodes;
+    const int32_t *depths;
+    int32_t *out;
+    int32_t *status;        // first device-side error (host-mapped), may be null
+    int64_t N;
+    int64_t num_node_tiles;
+    int32_t n, m, P, npad;
+    int32_t ppt;            // couples per staged tile
+    int32_t ntiles;         // number of couple tiles
+    uint32_t rec_bytes;
+    uint32_t off_tiles, tile_stride, off_A, off_flags;
+    long long wait_limit;   // clock64 cycles for one bounded mbarrier wait
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of the given parity, giving up after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+
+// One bulk (non-tensor) global->shared copy completing on an mbarrier.
+// dst, src and bytes are multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void report(int32_t *status, int32_t code) {
+    if (status) {
+        *reinterpret_cast<volatile int32_t *>(status) = code;
+        __threadfence_system();
+    }
+}
+
+// ---------------------------------------------------------------- the kernel
+template <int K>
+__device__ __forceinline__ void johnson_step(int j, int s, int delta, const uint8_t *__restrict__ sflags, int tid,
+                                             int (&u)[K]) {
+    const uint32_t fb = sflags[(j << 7) + tid];
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+        if ((fb >> b) & 1u) u[b] = max(u[b] + delta, s);
+    }
+}
+
+template <int K, bool WIDE>
+__global__ void __launch_bounds__(kThreads) fsp_bound_kernel(const BoundArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    static_assert(kThreads == 128, "flag addressing assumes 128 threads");
+    constexpr int KT = K * kThreads;
+    const int tid = threadIdx.x;
+    const int n = a.n, m = a.m;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint8_t *spairs = smem + 16;
+    unsigned char *tiles = smem + a.off_tiles;
+    int32_t *sA = reinterpret_cast<int32_t *>(smem + a.off_A);
+    uint8_t *sflags = smem + a.off_flags;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    for (int i = tid; i < 2 * a.P; i += kThreads) spairs[i] = a.pairs[i];
+    __syncthreads();
+
+    const bool resident = a.ntiles <= 2;
+    // Copies in flight per buffer (tracked by thread 0, which issues them):
+    // bit i of `pending` set = buffer i has an issued fill not yet waited for,
+    // whose phase parity is bit i of `pend_par`.
+    uint32_t pending = 0, pend_par = 0;
+    auto issue = [&](uint32_t fill, int t) {
+        const int c0 = t * a.ppt;
+        const int np = min(a.ppt, a.P - c0);
+        const uint32_t bytes = (uint32_t)np * (uint32_t)a.npad * a.rec_bytes;
+        const uint32_t bi = fill & 1;
+        uint64_t *b = &bar[bi];
+        mbar_arrive_expect_tx(b, bytes);
+        bulk_g2s(tiles + bi * a.tile_stride, a.rec + (size_t)c0 * a.npad * a.rec_bytes, bytes, b);
+        pending |= 1u << bi;
+        pend_par = (pend_par & ~(1u << bi)) | (((fill >> 1) & 1u) << bi);
+    };
+    if (tid == 0 && (int64_t)blockIdx.x < a.num_node_tiles) {
+        issue(0, 0);
+        if (a.ntiles == 2) issue(1, 1);
+    }
+    uint32_t fill = 0;  // fill being consumed (re-staging mode)
+
+    for (int64_t nt = blockIdx.x; nt < a.num_node_tiles; nt += gridDim.x) {
+        const int64_t base = nt * KT;
+        // ---- 1. depths and the membership flags
+        uint32_t vmask = 0;
+        int dd[K];
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            const int64_t x = base + b * kThreads + tid;
+            dd[b] = 0;
+            if (x < a.N) {
+                const int d = __ldg(a.depths + x);
+                if (d >= 0 && d <= n) {
+                    vmask |= 1u << b;
+                    dd[b] = d;
+                }
+            }
+        }
+        for (int j = 0; j < n; ++j) sflags[(j << 7) + tid] = (uint8_t)vmask;
+
+        // ---- 2. prefix completion times C(sigma,k), kept in A
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            int32_t *Ab = sA + b * kThreads + tid;
+            for (int k = 0; k < m; ++k) Ab[k * KT] = 0;
+            if ((vmask >> b) & 1u) {
+                const int16_t *row = a.nodes + (base + b * kThreads + tid) * (int64_t)n;
+                for (int i = 0; i < dd[b]; ++i) {
+                    const int j = __ldg(row + i);
+                    if ((unsigned)j >= (unsigned)n) {
+                        vmask &= ~(1u << b);
+                        break;
+                    }
+                    const uint32_t fv = sflags[(j << 7) + tid];
+                    if (!((fv >> b) & 1u)) {  // job already in the prefix
+                        vmask &= ~(1u << b);
+                        break;
+                    }
+                    sflags[(j << 7) + tid] = (uint8_t)(fv & ~(1u << b));
+                    const int32_t *pj = a.p + j * m;
+                    int c = 0;
+                    for (int k = 0; k < m; ++k) {
+                        c = max(c, Ab[k * KT]) + __ldg(pj + k);
+                        Ab[k * KT] = c;
+                    }
+                }
+            }
+        }
+
+        // ---- 3. A_k = max(C_k, min head over U) + sum of p_jk over U
+        for (int k = 0; k < m; ++k) {
+            int mh[K], S[K];
+#pragma unroll
+            for (int b = 0; b < K; ++b) {
+                mh[b] = INT_MAX;
+                S[b] = 0;
+            }
+            const int32_t *hk = a.head + k * n;
+            const int32_t *pk = a.ptm + k * n;
+            for (int j = 0; j < n; ++j) {
+                const uint32_t fb = sflags[(j << 7) + tid];
+                const int h = __ldg(hk + j), pv = __ldg(pk + j);
+#pragma unroll
+                for (int b = 0; b < K; ++b) {
+                    if ((fb >> b) & 1u) {
+                        mh[b] = min(mh[b], h);
+                        S[b] += pv;
+                    }
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < K; ++b) {
+                int32_t *Ab = sA + (k * K + b) * kThreads + tid;
+                const int C = *Ab;
+                *Ab = (mh[b] == INT_MAX ? C : max(C, mh[b])) + S[b];
+            }
+        }
+
+        // ---- 4/5. couples, tile by tile
+        int lb[K], q[K];
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            lb[b] = 0;
+            q[b] = 0;
+        }
+        for (int t = 0; t < a.ntiles; ++t) {
+            const uint32_t f = resident ? (uint32_t)t : fill;
+            if (!resident && tid == 0) {
+                const bool has_next = (t + 1 < a.ntiles) || (nt + gridDim.x < a.num_node_tiles);
+                if (has_next) issue(fill + 1, (t + 1) % a.ntiles);
+            }
+            const uint32_t parity = resident ? 0u : ((fill >> 1) & 1u);
+            const bool ok = mbar_wait_bounded(&bar[f & 1], parity, a.wait_limit);
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) {
+                    report(a.status, (int32_t)FSP_ETIMEDOUT);
+                    // let copies already issued land before the block exits
+                    for (uint32_t bi = 0; bi < 2; ++bi)
+                        if ((pending >> bi) & 1u) mbar_wait_bounded(&bar[bi], (pend_par >> bi) & 1u, a.wait_limit);
+                }
+                return;
+            }
+            pending &= ~(1u << (f & 1));
+            const unsigned char *tb = tiles + (f & 1) * a.tile_stride;
+            const int c0 = t * a.ppt;
+            const int np = min(a.ppt, a.P - c0);
+            for (int cc = 0; cc < np; ++cc) {
+                const int c = c0 + cc;
+                const int k = spairs[2 * c], l = spairs[2 * c + 1];
+                if (k == 0) {
+                    // first couple of machine l: latency q_l (QM) and A_l + q_l
+#pragma unroll
+                    for (int b = 0; b < K; ++b) q[b] = INT_MAX;
+                    const int32_t *tl = a.tail + l * n;
+                    for (int j = 0; j < n; ++j) {
+                        const uint32_t fb = sflags[(j << 7) + tid];
+                        const int tv = __ldg(tl + j);
+#pragma unroll
+                        for (int b = 0; b < K; ++b)
+                            if ((fb >> b) & 1u) q[b] = min(q[b], tv);
+                    }
+#pragma unroll
+                    for (int b = 0; b < K; ++b) {
+                        if (q[b] == INT_MAX) q[b] = 0;
+                        lb[b] = max(lb[b], sA[(l * K + b) * kThreads + tid] + q[b]);
+                    }
+                }
+                int u[K];
+#pragma unroll
+                for (int b = 0; b < K; ++b) u[b] = 0;
+                if (!WIDE) {
+                    const uint4 *R = reinterpret_cast<const uint4 *>(tb + (size_t)cc * a.npad * 4);
+                    const int nq = a.npad >> 2;
+#pragma unroll 1
+                    for (int i = 0; i < nq; ++i) {
+                        const uint4 r4 = R[i];
+                        const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const uint32_t r = rr[e];
+                            johnson_step<K>((int)(r & 1023u), (int)((r >> 10) & 8191u), (int)r >> 23, sflags, tid, u);
+                        }
+                    }
+                } else {
+                    const int4 *R = reinterpret_cast<const int4 *>(tb + (size_t)cc * a.npad * 16);
+#pragma unroll 1
+                    for (int i = 0; i < a.npad; ++i) {
+                        const int4 r = R[i];
+                        johnson_step<K>(r.x, r.y, r.z, sflags, tid, u);
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < K; ++b) lb[b] = max(lb[b], sA[(k * K + b) * kThreads + tid] + q[b] + u[b]);
+            }
+            if (!resident) {
+                __syncthreads();  // every thread is done with this buffer
+                ++fill;
+            }
+        }
+
+        // ---- 6. results
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            const int64_t x = base + b * kThreads + tid;
+            if (x < a.N) a.out[x] = ((vmask >> b) & 1u) ? lb[b] : FSP_LB_INVALID;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+struct DeviceLimits {
+    int smem_optin = 0;  // per block, opt-in maximum
+    int smem_sm = 0;     // per SM
+    int num_sms = 0;
+};
+
+DeviceLimits device_limits(int dev) {
+    static std::mutex mu;
+    static DeviceLimits cache[64];
+    static bool have[64] = {};
+    std::lock_guard<std::mutex> g(mu);
+    if (dev >= 0 && dev < 64 && have[dev]) return cache[dev];
+    DeviceLimits d;
+    cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&d.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dev >= 0 && dev < 64) {
+        cache[dev] = d;
+        have[dev] = true;
+    }
+    return d;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    uint32_t off_tiles, tile_stride, off_A, off_flags;
+    size_t total;
+};
+
+Layout layout_for(const fsp_instance *inst, int K, int ppt) {
+    Layout L;
+    L.off_tiles = (uint32_t)align_up(16 + 2 * (size_t)inst->P, 128);
+    L.tile_stride = (uint32_t)align_up((size_t)ppt * inst->npad * inst->rec_bytes, 128);
+    L.off_A = L.off_tiles + 2 * L.tile_stride;
+    L.off_flags = (uint32_t)align_up(L.off_A + (size_t)inst->m * K * kThreads * 4, 128);
+    L.total = align_up(L.off_flags + (size_t)inst->n * kThreads, 128);
+    return L;
+}
+
+// Shared-memory budget of one block when `bps` blocks share an SM.
+size_t block_budget(const DeviceLimits &d, int bps) {
+    const size_t per_block = bps <= 1 ? (size_t)d.smem_optin : (size_t)d.smem_sm / bps - 1024;
+    return std::min(per_block, (size_t)d.smem_optin);
+}
+
+// Largest couple tile that fits; 0 if nothing fits.
+int max_ppt(const fsp_instance *inst, int K, int bps, const DeviceLimits &d) {
+    const size_t budget = block_budget(d, bps);
+    const Layout L0 = layout_for(inst, K, 0);
+    if (L0.total > budget) return 0;
+    const size_t per_pair = (size_t)inst->npad * inst->rec_bytes;
+    size_t ppt = (budget - L0.total) / (2 * per_pair + 1);
+    while (ppt > 0 && layout_for(inst, K, (int)ppt).total > budget) --ppt;
+    return (int)std::min<size_t>(ppt, (size_t)inst->P);
+}
+
+// Relative per-node efficiency of K nodes per thread (instruction overhead
+// of a Johnson record is shared by the K nodes); refined by the autotuner.
+double k_efficiency(int K) {
+    switch (K) {
+        case 8: return 1.0;
+        case 4: return 0.85;
+        case 2: return 0.65;
+        default: return 0.45;
+    }
+}
+
+}  // namespace
+
+fsp_status check_device(const fsp_instance *inst) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    return dev == inst->device ? FSP_OK : FSP_EINVAL;
+}
+
+fsp_status take_device_status(const fsp_instance *inst) {
+    if (!inst->host_status) return FSP_OK;
+    volatile int32_t *hs = inst->host_status;
+    const int32_t v = *hs;
+    if (v != 0) {
+        *hs = 0;
+        return (fsp_status)v;
+    }
+    return FSP_OK;
+}
+
+fsp_status resolve_config(const fsp_instance *inst, int64_t N, const fsp_launch_config *req,
+                          fsp_launch_config *out, size_t *smem_bytes) {
+    const DeviceLimits d = device_limits(inst->device);
+    if (d.num_sms <= 0 || d.smem_optin <= 0) return FSP_ECUDA;
+    fsp_launch_config c = {0, 0, 0, 0};
+    if (req) c = *req;
+    if (c.nodes_per_thread && c.nodes_per_thread != 1 && c.nodes_per_thread != 2 && c.nodes_per_thread != 4 &&
+        c.nodes_per_thread != 8)
+        return FSP_EINVAL;
+    if (c.blocks_per_sm < 0 || c.blocks_per_sm > 2 || c.pairs_per_tile < 0) return FSP_EINVAL;
+
+    if (!c.nodes_per_thread || !c.blocks_per_sm) {
+        fsp_launch_config tuned = {0, 0, 0, 0};
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> g(inst->mu);
+            for (auto &e : inst->tuned)
+                if (e.first == N) {
+                    tuned = e.second;
+                    have = true;
+                }
+        }
+        if (have && !c.nodes_per_thread && !c.blocks_per_sm && !c.pairs_per_tile) {
+            c = tuned;
+        } else {
+            // Heuristic: maximise k_efficiency(K) x wave efficiency.
+            double best = -1.0;
+            fsp_launch_config pick = c;
+            for (int K : {8, 4, 2, 1}) {
+                if (c.nodes_per_thread && c.nodes_per_thread != K) continue;
+                for (int bps : {1, 2}) {
+                    if (c.blocks_per_sm && c.blocks_per_sm != bps) continue;
+                    const int ppt = max_ppt(inst, K, bps, d);
+                    if (ppt < 1) continue;
+                    // re-staging costs a little; prefer resident tables at equal score
+                    const bool res = (ppt * 2 >= inst->P);
+                    const double slots = (double)d.num_sms * bps;
+                    const double tiles = std::ceil((double)std::max<int64_t>(N, 1) / (K * kThreads));
+                    const double waves = tiles / slots;
+                    const double wave_eff = waves / std::ceil(waves);
+                    const double occ = bps == 2 ? 1.08 : 1.0;
+                    const double score = k_efficiency(K) * wave_eff * occ * (res ? 1.0 : 0.97);
+                    if (score > best) {
+                        best = score;
+                        pick.nodes_per_thread = K;
+                        pick.blocks_per_sm = bps;
+                    }
+                }
+            }
+            if (best < 0) return FSP_EINVAL;
+            c.nodes_per_thread = pick.nodes_per_thread;
+            c.blocks_per_sm = pick.blocks_per_sm;
+        }
+    }
+    const int mp = max_ppt(inst, c.nodes_per_thread, c.blocks_per_sm, d);
+    if (mp < 1) return FSP_EINVAL;
+    if (!c.pairs_per_tile) {
+        // all couples in two buffers if possible, else the largest tile
+        c.pairs_per_tile = (mp * 2 >= inst->P) ? (inst->P + 1) / 2 : mp;
+        if (inst->P == 1) c.pairs_per_tile = 1;
+    }
+    if (c.pairs_per_tile > mp) return FSP_EINVAL;
+    *out = c;
+    *smem_bytes = layout_for(inst, c.nodes_per_thread, c.pairs_per_tile).total;
+    return FSP_OK;
+}
+
+namespace {
+
+template <int K, bool WIDE>
+cudaError_t launch_variant(const BoundArgs &a, int grid, size_t smem, cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        attr_err = cudaFuncSetAttribute(fsp_bound_kernel<K, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    fsp_bound_kernel<K, WIDE><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+fsp_status launch_bound(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
+                        int32_t *out_lb, void *stream, const fsp_launch_config *cfg) {
+    fsp_launch_config c;
+    size_t smem = 0;
+    fsp_status st = resolve_config(inst, N, cfg, &c, &smem);
+    if (st != FSP_OK) return st;
+    const DeviceLimits d = device_limits(inst->device);
+    const int K = c.nodes_per_thread;
+    BoundArgs a;
+    a.rec = static_cast<const unsigned char *>(inst->t.rec);
+    a.pairs = inst->t.pairs;
+    a.p = inst->t.p;
+    a.head = inst->t.head;
+    a.tail = inst->t.tail;
+    a.ptm = inst->t.ptm;
+    a.nodes = nodes;
+    a.depths = depths;
+    a.out = out_lb;
+    a.status = inst->dev_status;
+    a.N = N;
+    a.num_node_tiles = (N + (int64_t)K * kThreads - 1) / ((int64_t)K * kThreads);
+    a.n = inst->n;
+    a.m = inst->m;
+    a.P = inst->P;
+    a.npad = inst->npad;
+    a.ppt = c.pairs_per_tile;
+    a.ntiles = (inst->P + c.pairs_per_tile - 1) / c.pairs_per_tile;
+    a.rec_bytes = (uint32_t)inst->rec_bytes;
+    const Layout L = layout_for(inst, K, c.pairs_per_tile);
+    a.off_tiles = L.off_tiles;
+    a.tile_stride = L.tile_stride;
+    a.off_A = L.off_A;
+    a.off_flags = L.off_flags;
+    a.wait_limit = 4000000000LL;  // about two seconds at 2 GHz
+    const int64_t slots = (int64_t)d.num_sms * c.blocks_per_sm;
+    const int grid = (int)std::min<int64_t>(a.num_node_tiles, slots);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    const bool wide = !inst->compact;
+    switch (K * 2 + (wide ? 1 : 0)) {
+        case 16: e = launch_variant<8, false>(a, grid, smem, s); break;
+        case 17: e = launch_variant<8, true>(a, grid, smem, s); break;
+        case 8: e = launch_variant<4, false>(a, grid, smem, s); break;
+        case 9: e = launch_variant<4, true>(a, grid, smem, s); break;
+        case 4: e = launch_variant<2, false>(a, grid, smem, s); break;
+        case 5: e = launch_variant<2, true>(a, grid, smem, s); break;
+        case 2: e = launch_variant<1, false>(a, grid, smem, s); break;
+        default: e = launch_variant<1, true>(a, grid, smem, s); break;
+    }
+    return e == cudaSuccess ? FSP_OK : FSP_ECUDA;
+}
+
+}  // namespace fspgb
+
+using namespace fspgb;
+
+extern "C" fsp_status fsp_bound_pool_ex(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths,
+                                        int64_t N, int32_t *out_lb, void *cuda_stream,
+                                        const fsp_launch_config *cfg) {
+    if (!inst || N < 0) return FSP_EINVAL;
+    if (N > 0 && (!nodes || !depths || !out_lb)) return FSP_EINVAL;
+    fsp_status st = take_device_status(inst);
+    if (st != FSP_OK) return st;
+    st = check_device(inst);
+    if (st != FSP_OK) return st;
+    if (N == 0) return FSP_OK;
+    return launch_bound(inst, nodes, depths, N, out_lb, cuda_stream, cfg);
+}
+
+extern "C" fsp_status fsp_bound_pool(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths,
+                                     int64_t N, int32_t *out_lb, void *cuda_stream) {
+    return fsp_bound_pool_ex(inst, nodes, depths, N, out_lb, cuda_stream, nullptr);
+}
+
+extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths,
+                                          int64_t N, int32_t *out_lb, void *cuda_stream) {
+    if (!inst || N < 0) return FSP_EINVAL;
+    if (N > 0 && (!nodes || !depths || !out_lb)) return FSP_EINVAL;
+    fsp_status st = take_device_status(inst);
+    if (st != FSP_OK) return st;
+    st = check_device(inst);
+    if (st != FSP_OK) return st;
+    if (N == 0) return FSP_OK;
+    cudaStream_t user = static_cast<cudaStream_t>(cuda_stream);
+    const int n = inst->n;
+    // Two chunks or more, alternating between the caller's stream and a
+    // second one, so the copies of one chunk overlap the bounding of the other.
+    const int64_t nchunks = N >= 131072 ? 4 : (N >= 32768 ? 2 : 1);
+    const int64_t chunk = (N + nchunks - 1) / nchunks;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_side = nullptr;
+    int16_t *d_nodes = nullptr;
+    int32_t *d_depths = nullptr, *d_out = nullptr;
+    const size_t nodes_bytes = sizeof(int16_t) * (size_t)N * n;
+    st = FSP_OK;
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming) != cudaSuccess) {
+        st = FSP_ECUDA;
+    }
+    if (st == FSP_OK && (cudaMallocAsync((void **)&d_nodes, nodes_bytes, user) != cudaSuccess ||
+                         cudaMallocAsync((void **)&d_depths, sizeof(int32_t) * (size_t)N, user) != cudaSuccess ||
+                         cudaMallocAsync((void **)&d_out, sizeof(int32_t) * (size_t)N, user) != cudaSuccess))
+        st = FSP_ENOMEM;
+    if (st == FSP_OK) {
+        cudaEventRecord(ev_start, user);
+        cudaStreamWaitEvent(side, ev_start, 0);
+        for (int64_t c = 0; c < nchunks && st == FSP_OK; ++c) {
+            const int64_t lo = c * chunk, hi = std::min(N, lo + chunk);
+            if (lo >= hi) break;
+            cudaStream_t s = (c & 1) ? side : user;
+            const size_t rows = (size_t)(hi - lo);
+            if (cudaMemcpyAsync(d_nodes + lo * n, nodes + lo * n, sizeof(int16_t) * rows * n, cudaMemcpyHostToDevice,
+                                s) != cudaSuccess ||
+                cudaMemcpyAsync(d_depths + lo, depths + lo, sizeof(int32_t) * rows, cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess) {
+                st = FSP_ECUDA;
+                break;
+            }
+            st = launch_bound(inst, d_nodes + lo * n, d_depths + lo, hi - lo, d_out + lo, s, nullptr);
+            if (st != FSP_OK) break;
+            if (cudaMemcpyAsync(out_lb + lo, d_out + lo, sizeof(int32_t) * rows, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess)
+                st = FSP_ECUDA;
+        }
+        cudaEventRecord(ev_side, side);
+        cudaStreamWaitEvent(user, ev_side, 0);
+    }
+    if (d_nodes) cudaFreeAsync(d_nodes, user);
+    if (d_depths) cudaFreeAsync(d_depths, user);
+    if (d_out) cudaFreeAsync(d_out, user);
+    if (cudaStreamSynchronize(user) != cudaSuccess && st == FSP_OK) st = FSP_ECUDA;
+    if (ev_start) cudaEventDestroy(ev_start);
+    if (ev_side) cudaEventDestroy(ev_side);
+    if (side) cudaStreamDestroy(side);
+    if (st == FSP_OK) st = take_device_status(inst);
+    return st;
+}

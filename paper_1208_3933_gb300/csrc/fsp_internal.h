@@ -1,0 +1,81 @@
+// fsp_internal.h -- instance layout shared by the library's translation units.
+//
+// Device tables of one instance (Section II-D of Melab et al.; Table I gives
+// their sizes and access counts).  Everything lives in one cudaMalloc block,
+// each array 256-byte aligned so the bulk copies that stage them into shared
+// memory start on a 16-byte boundary.
+//
+//   rec    [P][npad]  Johnson order of every couple with the per-entry
+//                     constants of the bounding recurrence (see below);
+//                     couples are ordered by their second machine l, then k
+//   pairs  [P][2]     uint8 (k,l) of each couple, in the same order (MM)
+//   p      [n][m]     int32 processing times (PTM), job-major
+//   head   [m][n]     int32 sum_{h<k} p_jh, machine-major (for RM)
+//   tail   [m][n]     int32 sum_{h>l} p_jh, machine-major (for QM)
+//   ptm    [m][n]     int32 p_jk, machine-major (column sums over U)
+//
+// One Johnson entry of couple c=(k,l) for job j carries
+//   delta = p_jl - p_jk   and   s = lag_j + p_jl,   lag_j = sum_{k<h<l} p_jh,
+// because the kernel runs the pseudo-code's two-machine recurrence on the
+// slack u = timeOnM2 - timeOnM1:  u <- max(u + delta, s)  for j in U.
+//
+// Compact 32-bit record (n <= 1024, 0 <= s < 8192, -256 <= delta < 256):
+//   bits  0..9   j
+//   bits 10..22  s
+//   bits 23..31  delta (two's complement)
+// Wide record: int4 {j, s, delta, 0}.
+// Padding entries (npad - n per couple) are all-zero records: for any u >= 0,
+// max(u + 0, 0) = u, so they never change the result.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/fsp.h"
+
+namespace fspgb {
+
+constexpr int kThreads = 128;          // threads per bounding block
+constexpr int kRecAlign = 4;           // couple rows padded to 4 entries (16 B compact)
+
+struct DeviceTables {
+    const void *rec = nullptr;
+    const uint8_t *pairs = nullptr;
+    const int32_t *p = nullptr;
+    const int32_t *head = nullptr;
+    const int32_t *tail = nullptr;
+    const int32_t *ptm = nullptr;
+};
+
+}  // namespace fspgb
+
+struct fsp_instance {
+    int32_t n = 0, m = 0, P = 0, npad = 0;
+    int32_t compact = 1;
+    int32_t device = 0;
+    int32_t rec_bytes = 4;          // bytes per Johnson record
+    std::vector<int32_t> p;         // host copy [n][m]
+    std::vector<uint8_t> pairs;     // host copy [P][2]
+    void *dev_block = nullptr;      // owns every device table
+    size_t dev_bytes = 0;
+    int32_t *host_status = nullptr; // pinned, mapped word: last device-side error (0 = none)
+    int32_t *dev_status = nullptr;  // the same word as the device sees it
+    fspgb::DeviceTables t;
+    int32_t num_sms = 0;
+    mutable std::mutex mu;          // guards the tuning cache below
+    mutable std::vector<std::pair<int64_t, fsp_launch_config>> tuned;  // pool-size bucket -> shape
+};
+
+namespace fspgb {
+
+// Launch-shape resolution and the kernel launcher (fsp_bound.cu).
+fsp_status resolve_config(const fsp_instance *inst, int64_t N, const fsp_launch_config *req,
+                          fsp_launch_config *out, size_t *smem_bytes);
+fsp_status launch_bound(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths,
+                        int64_t N, int32_t *out_lb, void *stream, const fsp_launch_config *cfg);
+fsp_status check_device(const fsp_instance *inst);
+fsp_status take_device_status(const fsp_instance *inst);
+
+}  // namespace fspgb

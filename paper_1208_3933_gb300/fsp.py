@@ -1,0 +1,231 @@
+"""Thin Python binding of the C ABI in include/fsp.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Device
+buffers are torch CUDA tensors (PyTorch supplies memory and streams); all
+bounding work runs in libfsp_gb300.so.  There is no CPU fallback: if the
+library is missing or a CUDA device is absent the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfsp_gb300.so")
+
+FSP_OK = 0
+FSP_EINVAL = -1
+FSP_ENOMEM = -2
+FSP_ECUDA = -3
+FSP_EBADNODE = -4
+FSP_ETIMEDOUT = -5
+FSP_ENOTFOUND = -6
+FSP_EBUSY = -7
+FSP_LB_INVALID = -1
+FSP_MAX_JOBS = 1024
+FSP_MAX_MACHINES = 32
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FspError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {fsp_status_string(status)} ({status})")
+
+
+class fsp_instance_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("pairs", ctypes.c_int32),
+                ("compact", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class fsp_launch_config(ctypes.Structure):
+    _fields_ = [("nodes_per_thread", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("pairs_per_tile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def load():
+    """Opens libfsp_gb300.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i16p = ctypes.POINTER(ctypes.c_int16)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "fsp_instance_create": ([i32p, i32, i32, ctypes.POINTER(vp)], i32),
+            "fsp_instance_destroy": ([vp], None),
+            "fsp_instance_query": ([vp, ctypes.POINTER(fsp_instance_info)], i32),
+            "fsp_bound_pool": ([vp, vp, vp, i64, vp, vp], i32),
+            "fsp_bound_pool_ex": ([vp, vp, vp, i64, vp, vp, ctypes.POINTER(fsp_launch_config)], i32),
+            "fsp_bound_pool_host": ([vp, vp, vp, i64, vp, vp], i32),
+            "fsp_branch_and_bound": ([vp, i32, i16p, i32p, i64p], i32),
+            "fsp_status_string": ([i32], ctypes.c_char_p),
+            "fsp_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def fsp_status_string(status: int) -> str:
+    return load().fsp_status_string(int(status)).decode()
+
+
+def fsp_version() -> str:
+    return load().fsp_version().decode()
+
+
+def _check(status: int, where: str):
+    if status != FSP_OK:
+        raise FspError(status, where)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Instance:
+    """Owns one fsp_instance (the processing times and every table of the
+    bound, resident on the current CUDA device)."""
+
+    def __init__(self, p):
+        lib = load()
+        p = np.ascontiguousarray(np.asarray(p), dtype=np.int32)
+        if p.ndim != 2:
+            raise ValueError("p must be a [n][m] matrix")
+        self.p = p
+        self.n, self.m = int(p.shape[0]), int(p.shape[1])
+        h = ctypes.c_void_p()
+        _check(lib.fsp_instance_create(p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.n, self.m,
+                                       ctypes.byref(h)), "fsp_instance_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None or not self._h.value:
+            raise RuntimeError("instance is destroyed")
+        return self._h
+
+    def info(self) -> fsp_instance_info:
+        out = fsp_instance_info()
+        _check(load().fsp_instance_query(self.handle, ctypes.byref(out)), "fsp_instance_query")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().fsp_instance_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fsp_instance_create(p) -> Instance:
+    return Instance(p)
+
+
+def fsp_instance_destroy(inst: Instance) -> None:
+    inst.close()
+
+
+def _check_pool(inst: Instance, nodes, depths, out):
+    import torch
+    N = int(depths.shape[0])
+    for name, t, dt in (("nodes", nodes, torch.int16), ("depths", depths, torch.int32), ("out_lb", out, torch.int32)):
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if tuple(nodes.shape) != (N, inst.n) or tuple(out.shape) != (N,):
+        raise ValueError("nodes must be [N][n], depths and out_lb [N]")
+    return N
+
+
+def fsp_bound_pool(inst: Instance, nodes, depths, out=None, stream=None, config=None):
+    """Bounds a device-resident pool; returns out (a new int32 tensor if None).
+    Stream-ordered on ``stream`` (default: torch's current stream)."""
+    import torch
+    if out is None:
+        out = torch.empty(depths.shape[0], dtype=torch.int32, device=depths.device)
+    N = _check_pool(inst, nodes, depths, out)
+    lib = load()
+    if config is None:
+        st = lib.fsp_bound_pool(inst.handle, ctypes.c_void_p(nodes.data_ptr()), ctypes.c_void_p(depths.data_ptr()),
+                                N, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
+        _check(st, "fsp_bound_pool")
+    else:
+        cfg = fsp_launch_config(*[int(x) for x in config], 0) if not isinstance(config, fsp_launch_config) else config
+        st = lib.fsp_bound_pool_ex(inst.handle, ctypes.c_void_p(nodes.data_ptr()),
+                                   ctypes.c_void_p(depths.data_ptr()), N, ctypes.c_void_p(out.data_ptr()),
+                                   _stream_handle(stream), ctypes.byref(cfg))
+        _check(st, "fsp_bound_pool_ex")
+    return out
+
+
+def fsp_bound_pool_host(inst: Instance, nodes, depths, out=None, stream=None):
+    """Bounds a host-resident pool (numpy arrays or CPU tensors, pinned or
+    pageable): copies in, bounds, copies back; returns when out is filled."""
+    def host_ptr(a, dt):
+        if hasattr(a, "data_ptr"):  # torch CPU tensor
+            if a.is_cuda or not a.is_contiguous():
+                raise ValueError("host buffers must be contiguous CPU tensors")
+            return ctypes.c_void_p(a.data_ptr()), a
+        a = np.ascontiguousarray(a, dtype=dt)
+        return ctypes.c_void_p(a.ctypes.data), a
+
+    n_ptr, nodes = host_ptr(nodes, np.int16)
+    d_ptr, depths = host_ptr(depths, np.int32)
+    N = int(depths.shape[0])
+    if tuple(nodes.shape) != (N, inst.n):
+        raise ValueError("nodes must be [N][n]")
+    if out is None:
+        out = np.empty(N, np.int32)
+    o_ptr, out = host_ptr(out, np.int32)
+    if tuple(out.shape) != (N,):
+        raise ValueError("out_lb must be [N]")
+    st = load().fsp_bound_pool_host(inst.handle, n_ptr, d_ptr, N, o_ptr, _stream_handle(stream))
+    _check(st, "fsp_bound_pool_host")
+    return out
+
+
+def fsp_branch_and_bound(inst: Instance, ub0: int):
+    """Returns (status, best_makespan, best_perm, nodes_bounded); status is
+    FSP_OK or FSP_ENOTFOUND (other failures raise)."""
+    perm = np.zeros(inst.n, np.int16)
+    best = ctypes.c_int32(0)
+    nodes = ctypes.c_int64(0)
+    st = load().fsp_branch_and_bound(inst.handle, int(ub0), perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)),
+                                     ctypes.byref(best), ctypes.byref(nodes))
+    if st not in (FSP_OK, FSP_ENOTFOUND):
+        raise FspError(st, "fsp_branch_and_bound")
+    return st, int(best.value), perm, int(nodes.value)

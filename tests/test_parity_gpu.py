@@ -1,0 +1,190 @@
+"""GPU bounding vs the CPU oracle, element by element (bit-exact: integer).
+
+All inputs are seeded synthetic pools from paper_1208_3933_gb300.workloads;
+every call goes through the C ABI (fsp_bound_pool / _ex / _host).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_3933_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+THREADS = 16
+
+
+def to_dev(rows, depths):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(rows)).cuda(), torch.from_numpy(np.ascontiguousarray(depths)).cuda()
+
+
+def gpu_bounds(fsp, inst, rows, depths, config=None, stream=None):
+    import torch
+    r, d = to_dev(rows, depths)
+    out = fsp.fsp_bound_pool(inst, r, d, config=config, stream=stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def oracle_bounds(p, rows, depths):
+    return oracle.Tables(p).lb_pool(rows, depths, threads=THREADS)
+
+
+def pool(seed, n, m, N, hi=99):
+    rng = np.random.default_rng(seed)
+    p = rng.integers(1, hi + 1, size=(n, m), dtype=np.int32)
+    rows, depths = workloads.random_pool(rng, n, N, max_depth=n + 1)
+    return p, rows, depths
+
+
+@pytest.mark.parametrize("n,m,N", [(20, 20, 5000), (50, 10, 3001), (200, 20, 1500), (7, 5, 999),
+                                   (1, 2, 3), (2, 2, 50), (13, 32, 700), (100, 3, 1111)])
+def test_pool_matches_oracle(gpu_lib, n, m, N):
+    fsp = gpu_lib
+    p, rows, depths = pool(n * 1000 + m, n, m, N)
+    with fsp.Instance(p) as inst:
+        got = gpu_bounds(fsp, inst, rows, depths)
+    want = oracle_bounds(p, rows, depths)
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+@pytest.mark.parametrize("bps", [1, 2])
+@pytest.mark.parametrize("ppt", [0, 1, 7])
+def test_every_launch_shape_matches_oracle(gpu_lib, K, bps, ppt):
+    """Explicit shapes, including couple tiles of 1 and 7 couples (190
+    couples at m=20), which force re-staging of the tables for every node
+    tile and a ragged last tile."""
+    fsp = gpu_lib
+    p, rows, depths = pool(77, 40, 20, 3 * 128 * K + 17)
+    with fsp.Instance(p) as inst:
+        got = gpu_bounds(fsp, inst, rows, depths, config=(K, bps, ppt))
+    assert np.array_equal(got, oracle_bounds(p, rows, depths))
+
+
+def test_wide_records_match_oracle(gpu_lib):
+    """Processing times above 255 select the 128-bit Johnson records."""
+    fsp = gpu_lib
+    p, rows, depths = pool(5, 60, 12, 2500, hi=20000)
+    with fsp.Instance(p) as inst:
+        assert inst.info().compact == 0
+        got = gpu_bounds(fsp, inst, rows, depths)
+        got_k1 = gpu_bounds(fsp, inst, rows, depths, config=(1, 1, 5))
+    want = oracle_bounds(p, rows, depths)
+    assert np.array_equal(got, want)
+    assert np.array_equal(got_k1, want)
+
+
+def test_pair_tiled_500x20_matches_oracle(gpu_lib):
+    """n=500, m=20: 190 couples x 500 entries do not fit in shared memory at
+    once, so the tables are staged tile by tile."""
+    fsp = gpu_lib
+    w = workloads.named_pool("pool_500x20", N=1400)
+    with fsp.Instance(w.p) as inst:
+        got = gpu_bounds(fsp, inst, w.rows, w.depths)
+    assert np.array_equal(got, oracle_bounds(w.p, w.rows, w.depths))
+
+
+def test_maximum_sizes(gpu_lib):
+    """n = 1024 jobs (the largest instance) and m = 32 machines."""
+    fsp = gpu_lib
+    p, rows, depths = pool(11, 1024, 4, 300)
+    with fsp.Instance(p) as inst:
+        got = gpu_bounds(fsp, inst, rows, depths)
+    assert np.array_equal(got, oracle_bounds(p, rows, depths))
+    p, rows, depths = pool(12, 30, 32, 400)
+    with fsp.Instance(p) as inst:
+        got = gpu_bounds(fsp, inst, rows, depths)
+    assert np.array_equal(got, oracle_bounds(p, rows, depths))
+
+
+def test_edge_rows(gpu_lib):
+    """depth 0, depth n (leaves: the bound is the makespan), equal times
+    (every Johnson key ties), zero times, and invalid rows."""
+    fsp = gpu_lib
+    from oracle import brute
+    n, m = 9, 4
+    rng = np.random.default_rng(3)
+    for p in (rng.integers(1, 100, (n, m), dtype=np.int32), np.full((n, m), 7, np.int32),
+              np.zeros((n, m), np.int32), rng.integers(0, 2, (n, m), dtype=np.int32)):
+        rows = np.tile(np.arange(n, dtype=np.int16), (12, 1))
+        for i in range(12):
+            rows[i] = rng.permutation(n)
+        depths = np.array([0, n, n, 1, 3, n - 1, 0, 2, -1, n + 1, 4, 4], np.int32)
+        rows[10, :4] = [0, 1, 1, 2]      # duplicate job
+        rows[11, :4] = [0, 1, 9, 2]      # job out of range
+        with fsp.Instance(p) as inst:
+            got = gpu_bounds(fsp, inst, rows, depths)
+        want = oracle_bounds(p, rows, depths)
+        assert np.array_equal(got, want)
+        assert got[1] == brute.makespan(p, rows[1].tolist())
+        assert got[8] == got[9] == got[10] == got[11] == fsp.FSP_LB_INVALID
+
+
+def test_empty_and_single_pools(gpu_lib):
+    import torch
+    fsp = gpu_lib
+    p, rows, depths = pool(1, 10, 5, 1)
+    with fsp.Instance(p) as inst:
+        assert gpu_bounds(fsp, inst, rows, depths).tolist() == oracle_bounds(p, rows, depths).tolist()
+        e = torch.empty((0, 10), dtype=torch.int16, device="cuda")
+        out = fsp.fsp_bound_pool(inst, e, torch.empty(0, dtype=torch.int32, device="cuda"))
+        assert out.numel() == 0
+
+
+def test_host_buffer_entry_point(gpu_lib):
+    """fsp_bound_pool_host: pageable and pinned host buffers, several chunks."""
+    import torch
+    fsp = gpu_lib
+    w = workloads.named_pool("pool_20x20", N=70001)
+    want = oracle_bounds(w.p, w.rows, w.depths)
+    with fsp.Instance(w.p) as inst:
+        got = fsp.fsp_bound_pool_host(inst, w.rows, w.depths)
+        assert np.array_equal(got, want)
+        pr = torch.from_numpy(w.rows).pin_memory()
+        pd = torch.from_numpy(w.depths).pin_memory()
+        po = torch.empty(w.N, dtype=torch.int32).pin_memory()
+        fsp.fsp_bound_pool_host(inst, pr, pd, po)
+        assert np.array_equal(po.numpy(), want)
+
+
+def test_side_stream_and_repeat_calls(gpu_lib):
+    import torch
+    fsp = gpu_lib
+    p, rows, depths = pool(21, 30, 10, 4000)
+    want = oracle_bounds(p, rows, depths)
+    s = torch.cuda.Stream()
+    with fsp.Instance(p) as inst:
+        r, d = to_dev(rows, depths)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            outs = [fsp.fsp_bound_pool(inst, r, d, stream=s) for _ in range(3)]
+        s.synchronize()
+        for o in outs:
+            assert np.array_equal(o.cpu().numpy(), want)
+
+
+def test_full_size_20x20_pool(gpu_lib):
+    """The 20x20 bounding pool (seed 1, 65,536 nodes), every node."""
+    fsp = gpu_lib
+    w = workloads.named_pool("pool_20x20")
+    with fsp.Instance(w.p) as inst:
+        got = gpu_bounds(fsp, inst, w.rows, w.depths)
+    assert np.array_equal(got, oracle_bounds(w.p, w.rows, w.depths))
+
+
+@pytest.mark.parametrize("name,sample", [("pool_200x20", 3000), ("pool_500x20", 600)])
+def test_full_size_pools_sampled(gpu_lib, name, sample):
+    """The 200x20 (262,144 nodes) and 500x20 (65,536 nodes) pools, bounded
+    whole in the launch shape the benchmark uses; a seeded sample of nodes is
+    recomputed by the oracle one by one."""
+    fsp = gpu_lib
+    w = workloads.named_pool(name)
+    with fsp.Instance(w.p) as inst:
+        got = gpu_bounds(fsp, inst, w.rows, w.depths)
+    idx = np.sort(np.random.default_rng(123).choice(w.N, sample, replace=False))
+    idx = np.unique(np.concatenate([idx, [0, w.N - 1]]))
+    want = oracle_bounds(w.p, w.rows[idx], w.depths[idx])
+    assert np.array_equal(got[idx], want)
+    assert (got > 0).all()
