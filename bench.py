@@ -271,8 +271,17 @@ def run_gpu(args, world, rank, local):
     outs = [torch.empty(w.N, dtype=torch.int32, device=dev) for _ in range(copies)]
     stream = torch.cuda.current_stream(dev)
 
+    # launch shape: forced (profiling) or autotuned on this pool, outside the timed region
+    cfg = None
+    if args.config:
+        cfg = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.config.split(",") if kv}
+        tuned_ms = None
+    else:
+        _, tuned_ms = fsp.fsp_autotune(inst, rows_d[0], dep_d[0], outs[0], stream=stream)
+    launch = fsp.fsp_tuned_config(inst, w.N) if cfg is None else cfg
+
     for i in range(args.warmup):
-        fsp.fsp_bound_pool(inst, rows_d[i % copies], dep_d[i % copies], outs[i % copies], stream=stream)
+        fsp.fsp_bound_pool(inst, rows_d[i % copies], dep_d[i % copies], outs[i % copies], stream=stream, config=cfg)
     torch.cuda.synchronize(dev)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -286,7 +295,8 @@ def run_gpu(args, world, rank, local):
         region0.record(stream)
         for i in range(args.steps):
             ev[i][0].record(stream)
-            fsp.fsp_bound_pool(inst, rows_d[i % copies], dep_d[i % copies], outs[i % copies], stream=stream)
+            fsp.fsp_bound_pool(inst, rows_d[i % copies], dep_d[i % copies], outs[i % copies], stream=stream,
+                               config=cfg)
             ev[i][1].record(stream)
         region1.record(stream)
         torch.cuda.synchronize(dev)
@@ -330,7 +340,8 @@ def run_gpu(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": w.n, "m": w.m, "nodes_per_step_per_gpu": w.N, "seed": w.seed,
                    "p": "U[1,99]", "depth": "U{0..199}", "records": "compact" if info.compact else "wide",
-                   "l2": "3 rotating pool copies of 105 MB (inputs larger than the 129 MB L2)"},
+                   "l2": "3 rotating pool copies of 105 MB (inputs larger than the 129 MB L2)",
+                   "launch": launch, "autotune_ms": tuned_ms},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "int-ops/s",
                      "frac": achieved / peak, "traffic": read_traffic(),
                      "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} int32 lanes x "
@@ -351,12 +362,14 @@ def run_gpu(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--nodes", type=int, default=0,
                     help="bound only the first NODES nodes of the pool (small profiling cases)")
     ap.add_argument("--alu-peak", action="store_true", help="run the integer-pipe throughput probe and exit")
+    ap.add_argument("--config", default="",
+                    help="force a launch shape, e.g. kernel=2,warps_per_block=14 (profiling); default: autotuned")
     args = ap.parse_args()
     if args.alu_peak:
         run_alu_peak()

@@ -75,11 +75,28 @@ typedef struct fsp_instance_info {
 
 /* Launch shape of the bounding kernel.  Zero in any field means "choose":
  * the library then uses the autotuned shape for this instance and pool size
- * when one is cached, else its built-in heuristic. */
+ * when one is cached, else its built-in heuristic.  Two kernels compute the
+ * same bound:
+ *   FSP_KERNEL_LOCKSTEP  each thread bounds K nodes, all threads of a warp
+ *                        walk the same couple (suits few couples, m <= 8);
+ *   FSP_KERNEL_LANES     each warp bounds 32 nodes, its lanes walk 32
+ *                        different couples (suits m >= 9). */
+#define FSP_KERNEL_AUTO 0
+#define FSP_KERNEL_LOCKSTEP 1
+#define FSP_KERNEL_LANES 2
+/* Lanes kernel staging: all records resident in shared memory (warps then
+ * work independently), or streamed through two tile buffers. */
+#define FSP_STAGING_AUTO 0
+#define FSP_STAGING_RESIDENT 1
+#define FSP_STAGING_STREAMED 2
 typedef struct fsp_launch_config {
-    int32_t nodes_per_thread;  /* K in {1,2,4,8}: nodes one thread bounds in lockstep */
-    int32_t blocks_per_sm;     /* resident blocks per SM (1 or 2) */
-    int32_t pairs_per_tile;    /* machine couples staged in shared memory at a time */
+    int32_t kernel;              /* FSP_KERNEL_* */
+    int32_t nodes_per_thread;    /* lockstep: K in {1,2,4,8} */
+    int32_t blocks_per_sm;       /* lockstep: resident blocks per SM (1 or 2) */
+    int32_t pairs_per_tile;      /* lockstep: couples staged in shared memory at a time */
+    int32_t warps_per_block;     /* lanes: 1..16 warps of 32 nodes */
+    int32_t positions_per_tile;  /* lanes, streamed: Johnson positions per tile (multiple of 4) */
+    int32_t staging;             /* lanes: FSP_STAGING_* */
     int32_t reserved;
 } fsp_launch_config;
 
@@ -166,6 +183,79 @@ fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_t *nodes,
  */
 fsp_status fsp_branch_and_bound(const fsp_instance *inst, int32_t ub0, int16_t *best_perm,
                                 int32_t *best_makespan, int64_t *nodes_bounded);
+
+/*
+ * fsp_autotune -- picks the launch shape for pools of N nodes of this
+ * instance.  The paper notes that the best configuration depends on the
+ * instance and pool size and must be found at run time by testing (Section
+ * VI); this times every shape of both kernels that fits the device on the
+ * given pool (the bounds are written to out_lb), requires all of them to
+ * produce identical bounds, and remembers the fastest in the instance, so
+ * later fsp_bound_pool calls with the same N use it.
+ *   nodes, depths, out_lb  device buffers as in fsp_bound_pool, N >= 1;
+ *   cache_path  NULL, or a text file: a cached entry for (device, n, m,
+ *               record format, N) is used without timing, and a new result
+ *               is appended;
+ *   best, best_ms  (optional) the chosen shape and its time per launch in ms
+ *               (-1 when it came from the cache).
+ * Synchronous on cuda_stream.  Errors: FSP_EINVAL, FSP_ECUDA (a launch failed
+ * or two shapes disagreed), FSP_ETIMEDOUT.
+ */
+fsp_status fsp_autotune(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
+                        int32_t *out_lb, void *cuda_stream, const char *cache_path,
+                        fsp_launch_config *best, float *best_ms);
+
+/* The launch shape fsp_bound_pool would use for N nodes (autotuned if
+ * fsp_autotune ran for this N, else the built-in heuristic).
+ * Errors: FSP_EINVAL, FSP_ECUDA. */
+fsp_status fsp_tuned_config(const fsp_instance *inst, int64_t N, fsp_launch_config *cfg);
+
+/* One pool of a batch: N nodes of instance `inst`, with device buffers laid
+ * out as in fsp_bound_pool. */
+typedef struct fsp_pool_desc {
+    const fsp_instance *inst;
+    const int16_t *nodes;   /* device [N][inst->n] */
+    const int32_t *depths;  /* device [N] */
+    int32_t *out_lb;        /* device [N] */
+    int64_t N;
+} fsp_pool_desc;
+
+/* A batch plan: many pools, possibly of different instances and sizes,
+ * bounded together by one persistent launch. */
+typedef struct fsp_batch fsp_batch;
+
+/*
+ * fsp_batch_create -- plans the batched form of the bounding operator
+ * (Section III-A applied to several pools at once): every pool is cut into
+ * 32-node work items, ordered longest first, and the plan (per-pool arguments,
+ * work items and a work counter) is uploaded to the current device, which
+ * must be the device of every instance.
+ *   pools  host array of `count` descriptors (copied; the device buffers they
+ *          name must stay valid while the batch is launched);
+ *   warps_per_block  1..16, or 0 to choose;
+ *   out    receives the plan.
+ * Every instance must use 32-bit Johnson records (fsp_instance_info.compact).
+ * Errors: FSP_EINVAL, FSP_ENOMEM, FSP_ECUDA.
+ */
+fsp_status fsp_batch_create(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block,
+                            fsp_batch **out);
+
+/* Enqueues the whole batch on the stream as one persistent kernel (after a
+ * reset of its work counter): each warp claims work items until none is
+ * left.  Stream-ordered; launches of one plan must not overlap.
+ * Errors: FSP_EINVAL (NULL, wrong device), FSP_ECUDA. */
+fsp_status fsp_batch_launch(fsp_batch *batch, void *cuda_stream);
+
+/* As fsp_batch_launch, through a CUDA graph (counter reset + kernel) captured
+ * on the first call and replayed afterwards. */
+fsp_status fsp_batch_launch_graph(fsp_batch *batch, void *cuda_stream);
+
+/* Work items, nodes, warps per block and blocks of a plan (any may be NULL). */
+fsp_status fsp_batch_query(const fsp_batch *batch, int64_t *work_items, int64_t *nodes,
+                           int32_t *warps_per_block, int32_t *blocks);
+
+/* Frees the plan; none of its launches may be in flight.  NULL is a no-op. */
+void fsp_batch_destroy(fsp_batch *batch);
 
 /* Static English text for a status code (never NULL). */
 const char *fsp_status_string(fsp_status s);

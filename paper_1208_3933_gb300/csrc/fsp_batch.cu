@@ -1,0 +1,313 @@
+// fsp_batch.cu -- many pools of many instances bounded in one persistent
+// launch (the batched form of the bounding operator of Section III-A).
+//
+// A batch plan lists every pool's 32-node work items, longest first (cost =
+// couple groups x Johnson positions of the pool's instance), and uploads the
+// list and the per-pool arguments to the device once.  One persistent launch
+// of fsp_lanes_batch then covers the whole plan: each warp claims work items
+// from a device counter, sets up its 32 nodes (lane = node), and scans the
+// instance's couple groups (lane = couple) reading the Johnson records from
+// L2/L1, so warps of one block may work on different instances.  The launch
+// can be captured once in a CUDA graph (counter reset + kernel) and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fsp_internal.h"
+#include "fsp_lanes_device.cuh"
+#include "fsp_ptx.cuh"
+
+namespace fspgb {
+
+template <int MP>
+__global__ void __launch_bounds__(512, 1)
+    fsp_lanes_batch(const LanesArgs *__restrict__ pools, const int2 *__restrict__ items, int64_t nitems,
+                    int32_t *counter, int32_t n_max, int32_t aq_stride, uint32_t off_aq) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *F = reinterpret_cast<uint32_t *>(smem) + (size_t)warp * n_max;
+    int32_t *AQ = reinterpret_cast<int32_t *>(smem + off_aq) + (size_t)warp * 32 * aq_stride;
+    for (;;) {
+        int claim = 0;
+        if (lane == 0) claim = atomicAdd(counter, 1);
+        claim = __shfl_sync(kFull, claim, 0);
+        if ((int64_t)claim >= nitems) break;
+        const int2 it = __ldg(items + claim);
+        const LanesArgs &a = pools[it.x];
+        const int64_t x = (int64_t)it.y * 32 + lane;
+        int bterm = 0;
+        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * aq_stride, bterm);
+        int lb[32];
+#pragma unroll
+        for (int b = 0; b < 32; ++b) lb[b] = 0;
+        const int G = a.G, npad = a.npad, m = a.m;
+        for (int g = 0; g < G; ++g) {
+            const int kk = __ldg(a.gpairs + 2 * (g * 32 + lane)), ll = __ldg(a.gpairs + 2 * (g * 32 + lane) + 1);
+            float u[32];
+#pragma unroll
+            for (int b = 0; b < 32; ++b) u[b] = 0.f;
+            const uint32_t *R = reinterpret_cast<const uint32_t *>(a.grec) + (size_t)g * npad * 32 + lane;
+#pragma unroll 4
+            for (int i = 0; i < npad; ++i) {
+                const uint32_t r = __ldg(R + i * 32);
+                const uint32_t fw = F[r & 1023u];
+                const float sf = __int_as_float(0x4B000000 | ((r >> 10) & 8191u)) - 8388608.0f;
+                const float df = __int_as_float(0x4B000000 | (uint32_t)(((int)r >> 23) + 256)) - 8388864.0f;
+#pragma unroll
+                for (int b = 0; b < 32; ++b)
+                    if ((fw >> b) & 1u) u[b] = fmaxf(u[b] + df, sf);
+            }
+            couple_epilogue(AQ, aq_stride, m, kk, ll, u, lb);
+        }
+        const int best = transpose_max(lb, lane);
+        if (x < a.N) a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
+        __syncwarp();  // the flag and row arrays are rewritten by the next item
+    }
+}
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <int MP>
+cudaError_t launch_batch_variant(const LanesArgs *pools, const int2 *items, int64_t nitems, int32_t *counter,
+                                 int n_max, int stride, uint32_t off_aq, int grid, int threads, size_t smem,
+                                 cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        attr_err = cudaFuncSetAttribute(fsp_lanes_batch<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    fsp_lanes_batch<MP><<<grid, threads, smem, s>>>(pools, items, nitems, counter, n_max, stride, off_aq);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+}  // namespace fspgb
+
+using namespace fspgb;
+
+struct fsp_batch {
+    int device = 0;
+    int64_t nitems = 0;
+    int mp = 8, n_max = 1, stride = 1, warps = 16, grid = 1;
+    uint32_t off_aq = 0;
+    size_t smem = 0;
+    void *dev_block = nullptr;  // pools, items and the work counter
+    LanesArgs *d_pools = nullptr;
+    int2 *d_items = nullptr;
+    int32_t *d_counter = nullptr;
+    int64_t nodes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::mutex mu;
+};
+
+namespace {
+
+fsp_status enqueue(fsp_batch *b, cudaStream_t s) {
+    if (b->nitems == 0) return FSP_OK;
+    if (cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), s) != cudaSuccess) return FSP_ECUDA;
+    cudaError_t e;
+    switch (b->mp) {
+        case 8:
+            e = launch_batch_variant<8>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
+                                        b->off_aq, b->grid, 32 * b->warps, b->smem, s);
+            break;
+        case 12:
+            e = launch_batch_variant<12>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
+                                         b->off_aq, b->grid, 32 * b->warps, b->smem, s);
+            break;
+        case 16:
+            e = launch_batch_variant<16>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
+                                         b->off_aq, b->grid, 32 * b->warps, b->smem, s);
+            break;
+        case 20:
+            e = launch_batch_variant<20>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
+                                         b->off_aq, b->grid, 32 * b->warps, b->smem, s);
+            break;
+        case 24:
+            e = launch_batch_variant<24>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
+                                         b->off_aq, b->grid, 32 * b->warps, b->smem, s);
+            break;
+        default:
+            e = launch_batch_variant<32>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
+                                         b->off_aq, b->grid, 32 * b->warps, b->smem, s);
+            break;
+    }
+    return e == cudaSuccess ? FSP_OK : FSP_ECUDA;
+}
+
+}  // namespace
+
+extern "C" fsp_status fsp_batch_create(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block,
+                                       fsp_batch **out) {
+    if (!out) return FSP_EINVAL;
+    *out = nullptr;
+    if (count < 0 || (count > 0 && !pools) || warps_per_block < 0 || warps_per_block > 16) return FSP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    int n_max = 1, m_max = 2, mp = 8;
+    for (int32_t i = 0; i < count; ++i) {
+        const fsp_pool_desc &p = pools[i];
+        if (!p.inst || p.N < 0 || (p.N > 0 && (!p.nodes || !p.depths || !p.out_lb))) return FSP_EINVAL;
+        if (p.inst->device != dev || !p.inst->compact) return FSP_EINVAL;
+        n_max = std::max(n_max, p.inst->n);
+        m_max = std::max(m_max, p.inst->m);
+        mp = std::max(mp, p.inst->mpad);
+    }
+    fsp_batch *b = new (std::nothrow) fsp_batch();
+    if (!b) return FSP_ENOMEM;
+    b->device = dev;
+    b->mp = mp;
+    b->n_max = n_max;
+    b->stride = (m_max + (m_max + 1) / 2) | 1;
+    // work items, longest first: couple groups x Johnson positions of the instance
+    std::vector<int2> items;
+    std::vector<LanesArgs> args((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        const fsp_pool_desc &p = pools[i];
+        const fsp_instance *inst = p.inst;
+        LanesArgs &a = args[i];
+        std::memset(&a, 0, sizeof a);
+        a.grec = static_cast<const unsigned char *>(inst->t.grec);
+        a.gpairs = inst->t.gpairs;
+        a.hsort = reinterpret_cast<const int2 *>(inst->t.hsort);
+        a.tsort = reinterpret_cast<const int2 *>(inst->t.tsort);
+        a.ptot = inst->t.ptot;
+        a.pp = inst->t.pp;
+        a.nodes = p.nodes;
+        a.depths = p.depths;
+        a.out = p.out_lb;
+        a.status = inst->dev_status;
+        a.N = p.N;
+        a.n = inst->n;
+        a.m = inst->m;
+        a.G = inst->G;
+        a.npad = inst->npad;
+        a.mpad = inst->mpad;
+        a.rec_bytes = (uint32_t)inst->rec_bytes;
+        a.aq_stride = b->stride;
+        a.wait_limit = 4000000000LL;
+        const int64_t nb = (p.N + 31) / 32;
+        for (int64_t k = 0; k < nb; ++k) items.push_back(make_int2(i, (int)k));
+        b->nodes += p.N;
+    }
+    std::stable_sort(items.begin(), items.end(), [&](const int2 &x, const int2 &y) {
+        const int64_t cx = (int64_t)args[x.x].G * args[x.x].npad, cy = (int64_t)args[y.x].G * args[y.x].npad;
+        return cx > cy;
+    });
+    b->nitems = (int64_t)items.size();
+    // shared memory: flags [warps][n_max] words, rows [warps][32][stride] ints
+    const int smem_optin = max_smem_per_block(dev);
+    int W = warps_per_block ? warps_per_block : 16;
+    for (; W >= 1; --W) {
+        const uint32_t off_aq = (uint32_t)align_up((size_t)W * n_max * 4, 128);
+        const size_t total = align_up(off_aq + (size_t)W * 32 * b->stride * 4, 128);
+        if (total <= (size_t)smem_optin) {
+            b->off_aq = off_aq;
+            b->smem = total;
+            break;
+        }
+        if (warps_per_block) break;
+    }
+    if (!b->smem) {
+        delete b;
+        return FSP_EINVAL;
+    }
+    b->warps = W;
+    const int64_t blocks_needed = (b->nitems + W - 1) / W;
+    b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, num_sms(dev)));
+    const size_t off_items = align_up(sizeof(LanesArgs) * std::max(1, count), 256);
+    const size_t off_ctr = align_up(off_items + sizeof(int2) * std::max<int64_t>(1, b->nitems), 256);
+    const size_t bytes = off_ctr + 256;
+    unsigned char *blk = nullptr;
+    if (cudaMalloc((void **)&blk, bytes) != cudaSuccess) {
+        delete b;
+        return FSP_ENOMEM;
+    }
+    if ((count && cudaMemcpy(blk, args.data(), sizeof(LanesArgs) * count, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (b->nitems &&
+         cudaMemcpy(blk + off_items, items.data(), sizeof(int2) * b->nitems, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemset(blk + off_ctr, 0, 256) != cudaSuccess) {
+        cudaFree(blk);
+        delete b;
+        return FSP_ECUDA;
+    }
+    b->dev_block = blk;
+    b->d_pools = reinterpret_cast<LanesArgs *>(blk);
+    b->d_items = reinterpret_cast<int2 *>(blk + off_items);
+    b->d_counter = reinterpret_cast<int32_t *>(blk + off_ctr);
+    *out = b;
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_batch_launch(fsp_batch *b, void *cuda_stream) {
+    if (!b) return FSP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    if (dev != b->device) return FSP_EINVAL;
+    std::lock_guard<std::mutex> g(b->mu);
+    return enqueue(b, static_cast<cudaStream_t>(cuda_stream));
+}
+
+extern "C" fsp_status fsp_batch_launch_graph(fsp_batch *b, void *cuda_stream) {
+    if (!b) return FSP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    if (dev != b->device) return FSP_EINVAL;
+    std::lock_guard<std::mutex> g(b->mu);
+    if (!b->exec) {
+        cudaStream_t cap = nullptr;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return FSP_ECUDA;
+        fsp_status st = FSP_OK;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            st = FSP_ECUDA;
+        } else {
+            st = enqueue(b, cap);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+            if (st == FSP_OK && e != cudaSuccess) st = FSP_ECUDA;
+            if (st == FSP_OK && cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+                st = FSP_ECUDA;
+                b->exec = nullptr;
+            }
+            if (graph) {
+                if (st == FSP_OK)
+                    b->graph = graph;
+                else
+                    cudaGraphDestroy(graph);
+            }
+        }
+        cudaStreamDestroy(cap);
+        if (st != FSP_OK) return st;
+    }
+    return cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? FSP_OK : FSP_ECUDA;
+}
+
+extern "C" fsp_status fsp_batch_query(const fsp_batch *b, int64_t *work_items, int64_t *nodes,
+                                      int32_t *warps_per_block, int32_t *blocks) {
+    if (!b) return FSP_EINVAL;
+    if (work_items) *work_items = b->nitems;
+    if (nodes) *nodes = b->nodes;
+    if (warps_per_block) *warps_per_block = b->warps;
+    if (blocks) *blocks = b->grid;
+    return FSP_OK;
+}
+
+extern "C" void fsp_batch_destroy(fsp_batch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->dev_block) cudaFree(b->dev_block);
+    delete b;
+}

@@ -45,6 +45,7 @@
 #include <mutex>
 
 #include "fsp_internal.h"
+#include "fsp_ptx.cuh"
 
 namespace fspgb {
 
@@ -65,62 +66,6 @@ struct BoundArgs {
     uint32_t off_tiles, tile_stride, off_A, off_flags;
     long long wait_limit;   // clock64 cycles for one bounded mbarrier wait
 };
-
-// ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Waits for the phase of the given parity, giving up after `limit` cycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > limit) return false;
-    }
-    return true;
-}
-
-// One bulk (non-tensor) global->shared copy completing on an mbarrier.
-// dst, src and bytes are multiples of 16.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void report(int32_t *status, int32_t code) {
-    if (status) {
-        *reinterpret_cast<volatile int32_t *>(status) = code;
-        __threadfence_system();
-    }
-}
 
 // ---------------------------------------------------------------- the kernel
 template <int K>
@@ -270,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) fsp_bound_kernel(const BoundArgs a) 
             const bool ok = mbar_wait_bounded(&bar[f & 1], parity, a.wait_limit);
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) {
-                    report(a.status, (int32_t)FSP_ETIMEDOUT);
+                    report_status(a.status, (int32_t)FSP_ETIMEDOUT);
                     // let copies already issued land before the block exits
                     for (uint32_t bi = 0; bi < 2; ++bi)
                         if ((pending >> bi) & 1u) mbar_wait_bounded(&bar[bi], (pend_par >> bi) & 1u, a.wait_limit);
@@ -363,7 +308,7 @@ DeviceLimits device_limits(int dev) {
     cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&d.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (dev >= 0 && dev < 64) {
+    if (dev >= 0 && dev < 64 && d.num_sms > 0) {
         cache[dev] = d;
         have[dev] = true;
     }
@@ -405,7 +350,7 @@ int max_ppt(const fsp_instance *inst, int K, int bps, const DeviceLimits &d) {
 }
 
 // Relative per-node efficiency of K nodes per thread (instruction overhead
-// of a Johnson record is shared by the K nodes); refined by the autotuner.
+// of a Johnson record is shared by the K nodes).
 double k_efficiency(int K) {
     switch (K) {
         case 8: return 1.0;
@@ -415,7 +360,113 @@ double k_efficiency(int K) {
     }
 }
 
+double wave_efficiency(double work_items, double slots) {
+    const double waves = work_items / slots;
+    return waves / std::ceil(waves);
+}
+
+fsp_status resolve_lockstep(const fsp_instance *inst, int64_t N, const DeviceLimits &d, fsp_launch_config &c) {
+    if (c.nodes_per_thread && c.nodes_per_thread != 1 && c.nodes_per_thread != 2 && c.nodes_per_thread != 4 &&
+        c.nodes_per_thread != 8)
+        return FSP_EINVAL;
+    if (c.blocks_per_sm < 0 || c.blocks_per_sm > 2 || c.pairs_per_tile < 0) return FSP_EINVAL;
+    if (!c.nodes_per_thread || !c.blocks_per_sm) {
+        double best = -1.0;
+        int bK = 0, bB = 0;
+        for (int K : {8, 4, 2, 1}) {
+            if (c.nodes_per_thread && c.nodes_per_thread != K) continue;
+            for (int bps : {1, 2}) {
+                if (c.blocks_per_sm && c.blocks_per_sm != bps) continue;
+                const int ppt = max_ppt(inst, K, bps, d);
+                if (ppt < 1) continue;
+                const bool res = (ppt * 2 >= inst->P);
+                const double tiles = std::ceil((double)std::max<int64_t>(N, 1) / (K * kThreads));
+                const double score = k_efficiency(K) * wave_efficiency(tiles, (double)d.num_sms * bps) *
+                                     (bps == 2 ? 1.08 : 1.0) * (res ? 1.0 : 0.97);
+                if (score > best) {
+                    best = score;
+                    bK = K;
+                    bB = bps;
+                }
+            }
+        }
+        if (best < 0) return FSP_EINVAL;
+        c.nodes_per_thread = bK;
+        c.blocks_per_sm = bB;
+    }
+    const int mp = max_ppt(inst, c.nodes_per_thread, c.blocks_per_sm, d);
+    if (mp < 1) return FSP_EINVAL;
+    if (!c.pairs_per_tile) c.pairs_per_tile = (mp * 2 >= inst->P) ? std::max(1, (inst->P + 1) / 2) : mp;
+    if (c.pairs_per_tile > mp) return FSP_EINVAL;
+    return FSP_OK;
+}
+
+fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits &d, fsp_launch_config &c) {
+    if (c.warps_per_block < 0 || c.warps_per_block > 16 || c.positions_per_tile < 0 ||
+        (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 2)
+        return FSP_EINVAL;
+    const int npad = inst->npad;
+    auto fits = [&](int W, int staging, int pos) {
+        fsp_launch_config t = c;
+        t.warps_per_block = W;
+        t.staging = staging;
+        t.positions_per_tile = pos;
+        size_t smem = 0;
+        return lanes_layout(inst, t, &smem) == FSP_OK;
+    };
+    // largest streamed tile (multiple of 4, at most npad) for W warps; 0 if none
+    auto best_chunk = [&](int W) {
+        for (int ch = npad; ch >= 4; ch -= 4)
+            if (fits(W, FSP_STAGING_STREAMED, ch)) return ch;
+        return 0;
+    };
+    // resident staging only on request: holding every record in shared memory
+    // leaves too little L1 for the setup's tables (measured slower at 20x20
+    // and 200x20), so the default streams the records
+    if (c.staging == FSP_STAGING_RESIDENT) {
+        int bW = 0;
+        for (int W = 16; W >= 1; --W) {
+            if (c.warps_per_block && c.warps_per_block != W) continue;
+            if (fits(W, FSP_STAGING_RESIDENT, 0)) {
+                bW = W;
+                break;
+            }
+        }
+        if (bW) {
+            c.warps_per_block = bW;
+            c.staging = FSP_STAGING_RESIDENT;
+            c.positions_per_tile = 0;
+            return FSP_OK;
+        }
+        return FSP_EINVAL;
+    }
+    c.staging = FSP_STAGING_STREAMED;
+    if (!c.warps_per_block) {
+        double best = -1.0;
+        int bW = 0;
+        for (int W = 16; W >= 1; --W) {
+            const int ch = c.positions_per_tile ? c.positions_per_tile : best_chunk(W);
+            if (ch < 4 || !fits(W, FSP_STAGING_STREAMED, ch)) continue;
+            if (!c.positions_per_tile && ch < std::min(npad, 64)) continue;
+            const double batches = std::ceil((double)std::max<int64_t>(N, 1) / (32.0 * W));
+            const double score = wave_efficiency(batches, d.num_sms) * std::min(1.0, W / 12.0);
+            if (score > best + 1e-9) {
+                best = score;
+                bW = W;
+            }
+        }
+        if (best < 0) return FSP_EINVAL;
+        c.warps_per_block = bW;
+    }
+    if (!c.positions_per_tile) c.positions_per_tile = best_chunk(c.warps_per_block);
+    if (c.positions_per_tile < 4) return FSP_EINVAL;
+    return fits(c.warps_per_block, FSP_STAGING_STREAMED, c.positions_per_tile) ? FSP_OK : FSP_EINVAL;
+}
+
 }  // namespace
+
+int max_smem_per_block(int device) { return device_limits(device).smem_optin; }
+int num_sms(int device) { return device_limits(device).num_sms; }
 
 fsp_status check_device(const fsp_instance *inst) {
     int dev = -1;
@@ -438,66 +489,26 @@ fsp_status resolve_config(const fsp_instance *inst, int64_t N, const fsp_launch_
                           fsp_launch_config *out, size_t *smem_bytes) {
     const DeviceLimits d = device_limits(inst->device);
     if (d.num_sms <= 0 || d.smem_optin <= 0) return FSP_ECUDA;
-    fsp_launch_config c = {0, 0, 0, 0};
+    fsp_launch_config c = {};
     if (req) c = *req;
-    if (c.nodes_per_thread && c.nodes_per_thread != 1 && c.nodes_per_thread != 2 && c.nodes_per_thread != 4 &&
-        c.nodes_per_thread != 8)
-        return FSP_EINVAL;
-    if (c.blocks_per_sm < 0 || c.blocks_per_sm > 2 || c.pairs_per_tile < 0) return FSP_EINVAL;
-
-    if (!c.nodes_per_thread || !c.blocks_per_sm) {
-        fsp_launch_config tuned = {0, 0, 0, 0};
-        bool have = false;
-        {
-            std::lock_guard<std::mutex> g(inst->mu);
-            for (auto &e : inst->tuned)
-                if (e.first == N) {
-                    tuned = e.second;
-                    have = true;
-                }
-        }
-        if (have && !c.nodes_per_thread && !c.blocks_per_sm && !c.pairs_per_tile) {
-            c = tuned;
-        } else {
-            // Heuristic: maximise k_efficiency(K) x wave efficiency.
-            double best = -1.0;
-            fsp_launch_config pick = c;
-            for (int K : {8, 4, 2, 1}) {
-                if (c.nodes_per_thread && c.nodes_per_thread != K) continue;
-                for (int bps : {1, 2}) {
-                    if (c.blocks_per_sm && c.blocks_per_sm != bps) continue;
-                    const int ppt = max_ppt(inst, K, bps, d);
-                    if (ppt < 1) continue;
-                    // re-staging costs a little; prefer resident tables at equal score
-                    const bool res = (ppt * 2 >= inst->P);
-                    const double slots = (double)d.num_sms * bps;
-                    const double tiles = std::ceil((double)std::max<int64_t>(N, 1) / (K * kThreads));
-                    const double waves = tiles / slots;
-                    const double wave_eff = waves / std::ceil(waves);
-                    const double occ = bps == 2 ? 1.08 : 1.0;
-                    const double score = k_efficiency(K) * wave_eff * occ * (res ? 1.0 : 0.97);
-                    if (score > best) {
-                        best = score;
-                        pick.nodes_per_thread = K;
-                        pick.blocks_per_sm = bps;
-                    }
-                }
-            }
-            if (best < 0) return FSP_EINVAL;
-            c.nodes_per_thread = pick.nodes_per_thread;
-            c.blocks_per_sm = pick.blocks_per_sm;
-        }
+    if (c.kernel < 0 || c.kernel > 2) return FSP_EINVAL;
+    const bool unset = c.kernel == 0 && !c.nodes_per_thread && !c.blocks_per_sm && !c.pairs_per_tile &&
+                       !c.warps_per_block && !c.positions_per_tile && !c.staging;
+    if (unset) {
+        std::lock_guard<std::mutex> g(inst->mu);
+        for (auto &e : inst->tuned)
+            if (e.first == N) c = e.second;
     }
-    const int mp = max_ppt(inst, c.nodes_per_thread, c.blocks_per_sm, d);
-    if (mp < 1) return FSP_EINVAL;
-    if (!c.pairs_per_tile) {
-        // all couples in two buffers if possible, else the largest tile
-        c.pairs_per_tile = (mp * 2 >= inst->P) ? (inst->P + 1) / 2 : mp;
-        if (inst->P == 1) c.pairs_per_tile = 1;
+    if (c.kernel == 0) c.kernel = inst->P >= 32 ? FSP_KERNEL_LANES : FSP_KERNEL_LOCKSTEP;
+    fsp_status st = c.kernel == FSP_KERNEL_LANES ? resolve_lanes(inst, N, d, c) : resolve_lockstep(inst, N, d, c);
+    if (st != FSP_OK) return st;
+    if (c.kernel == FSP_KERNEL_LANES) {
+        st = lanes_layout(inst, c, smem_bytes);
+        if (st != FSP_OK) return st;
+    } else {
+        *smem_bytes = layout_for(inst, c.nodes_per_thread, c.pairs_per_tile).total;
     }
-    if (c.pairs_per_tile > mp) return FSP_EINVAL;
     *out = c;
-    *smem_bytes = layout_for(inst, c.nodes_per_thread, c.pairs_per_tile).total;
     return FSP_OK;
 }
 
@@ -518,14 +529,8 @@ cudaError_t launch_variant(const BoundArgs &a, int grid, size_t smem, cudaStream
     return cudaGetLastError();
 }
 
-}  // namespace
-
-fsp_status launch_bound(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
-                        int32_t *out_lb, void *stream, const fsp_launch_config *cfg) {
-    fsp_launch_config c;
-    size_t smem = 0;
-    fsp_status st = resolve_config(inst, N, cfg, &c, &smem);
-    if (st != FSP_OK) return st;
+fsp_status launch_lockstep(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
+                           int32_t *out_lb, void *stream, const fsp_launch_config &c) {
     const DeviceLimits d = device_limits(inst->device);
     const int K = c.nodes_per_thread;
     BoundArgs a;
@@ -560,16 +565,28 @@ fsp_status launch_bound(const fsp_instance *inst, const int16_t *nodes, const in
     cudaError_t e;
     const bool wide = !inst->compact;
     switch (K * 2 + (wide ? 1 : 0)) {
-        case 16: e = launch_variant<8, false>(a, grid, smem, s); break;
-        case 17: e = launch_variant<8, true>(a, grid, smem, s); break;
-        case 8: e = launch_variant<4, false>(a, grid, smem, s); break;
-        case 9: e = launch_variant<4, true>(a, grid, smem, s); break;
-        case 4: e = launch_variant<2, false>(a, grid, smem, s); break;
-        case 5: e = launch_variant<2, true>(a, grid, smem, s); break;
-        case 2: e = launch_variant<1, false>(a, grid, smem, s); break;
-        default: e = launch_variant<1, true>(a, grid, smem, s); break;
+        case 16: e = launch_variant<8, false>(a, grid, L.total, s); break;
+        case 17: e = launch_variant<8, true>(a, grid, L.total, s); break;
+        case 8: e = launch_variant<4, false>(a, grid, L.total, s); break;
+        case 9: e = launch_variant<4, true>(a, grid, L.total, s); break;
+        case 4: e = launch_variant<2, false>(a, grid, L.total, s); break;
+        case 5: e = launch_variant<2, true>(a, grid, L.total, s); break;
+        case 2: e = launch_variant<1, false>(a, grid, L.total, s); break;
+        default: e = launch_variant<1, true>(a, grid, L.total, s); break;
     }
     return e == cudaSuccess ? FSP_OK : FSP_ECUDA;
+}
+
+}  // namespace
+
+fsp_status launch_bound(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
+                        int32_t *out_lb, void *stream, const fsp_launch_config *cfg) {
+    fsp_launch_config c;
+    size_t smem = 0;
+    fsp_status st = resolve_config(inst, N, cfg, &c, &smem);
+    if (st != FSP_OK) return st;
+    if (c.kernel == FSP_KERNEL_LANES) return launch_lanes(inst, nodes, depths, N, out_lb, stream, c);
+    return launch_lockstep(inst, nodes, depths, N, out_lb, stream, c);
 }
 
 }  // namespace fspgb

@@ -1,0 +1,348 @@
+// fsp_bound_lanes.cu -- the couple-lanes bounding kernels (sm_103a).
+//
+// Same operator as fsp_bound.cu (Section III-A: one evaluation of the
+// two-machine bound of Section II-C per sub-problem), mapped the other way
+// round: a warp owns 32 nodes, and its 32 lanes take 32 different machine
+// couples (k,l).  Each lane walks its couple's Johnson order (records laid
+// out [group][position][lane], so the 32 lanes read 32 consecutive words)
+// and updates the slack of all 32 nodes of the warp in registers,
+//     u_b <- max(u_b + delta_j, s_j)   when job j is unscheduled in node b,
+// where bit b of the warp's flag word for job j says so.  A lane's couple
+// value for node b is A_k + q_l + u_b (the slack form, see fsp_bound.cu); a
+// transpose-max over the 32 lanes (31 shuffles) then gives lane b the maximum
+// over all couples for node b, combined with the one-machine terms
+// max_l (A_l + q_l).
+//
+// With 32-bit records every value the scan forms is an integer below 2^24
+// (slack <= 8191 + 1024 * 255), so the scan runs in fp32: the add goes to the
+// FMA pipe and only the max to the integer ALU pipe, and the result is exact.
+// 128-bit records (large processing times) use the int32 path.
+//
+// Per node the shared memory holds one flag bit per job and a row with A_k
+// (int32) and q_l (int16), so a block keeps hundreds of nodes in flight.  Two
+// staging modes:
+//   resident  all record groups are copied to shared memory once per block
+//             (one cp.async.bulk per group on one mbarrier); warps are then
+//             independent and claim 32-node batches from a per-block counter,
+//             so one warp's setup overlaps the others' scans;
+//   streamed  records too large for shared memory are staged in tiles of
+//             (group, positions) through two buffers, the whole block moving
+//             from tile to tile together (the paper's "does not fit" case).
+//
+// Setup, one lane per node: (1) membership flags and row validation, (2) the
+// prefix recurrence C(sigma,k) (Section II-B) and the prefix's column sums
+// in registers, (3) the minima of RM and QM as the first unscheduled job of
+// each machine's head- (tail-) sorted job list, 32 list entries per step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <mutex>
+
+#include "fsp_internal.h"
+#include "fsp_lanes_device.cuh"
+#include "fsp_ptx.cuh"
+
+namespace fspgb {
+
+// ---------------------------------------------------------------- resident
+template <bool WIDE, int MP>
+__global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    int *ctr = reinterpret_cast<int *>(smem + 8);
+    uint8_t *sgp = smem + 16;
+    const unsigned char *tables = smem + a.off_tables;
+    uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * a.n;
+    int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
+
+    // this block's share of the warp batches
+    const int64_t b0 = (int64_t)blockIdx.x * a.num_batches / gridDim.x;
+    const int64_t b1 = (int64_t)(blockIdx.x + 1) * a.num_batches / gridDim.x;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+        *ctr = 0;
+    }
+    for (int i = threadIdx.x; i < a.G * 64; i += blockDim.x) sgp[i] = a.gpairs[i];
+    __syncthreads();
+    const size_t group_bytes = (size_t)a.npad * 32 * a.rec_bytes;
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(group_bytes * a.G));
+        for (int g = 0; g < a.G; ++g)
+            bulk_g2s(smem + a.off_tables + g * group_bytes, a.grec + g * group_bytes, (uint32_t)group_bytes, bar);
+    }
+    bool ready = false;
+    for (;;) {
+        int claim = 0;
+        if (lane == 0) claim = atomicAdd(ctr, 1);
+        const int64_t bt = b0 + __shfl_sync(kFull, claim, 0);
+        if (bt >= b1) break;
+        const int64_t x = bt * 32 + lane;
+        int bterm = 0;
+        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm);
+        if (!ready) {
+            if (!mbar_wait_bounded(bar, 0, a.wait_limit)) {
+                if (lane == 0) report_status(a.status, (int32_t)FSP_ETIMEDOUT);
+                if (threadIdx.x == 0) mbar_wait_bounded(bar, 0, a.wait_limit);  // let the copy land
+                return;
+            }
+            ready = true;
+        }
+        int lb[32];
+#pragma unroll
+        for (int b = 0; b < 32; ++b) lb[b] = 0;
+        for (int g = 0; g < a.G; ++g) {
+            const int kk = sgp[2 * (g * 32 + lane)], ll = sgp[2 * (g * 32 + lane) + 1];
+            if (!WIDE) {
+                float u[32];
+#pragma unroll
+                for (int b = 0; b < 32; ++b) u[b] = 0.f;
+                scan_compact(reinterpret_cast<const uint32_t *>(tables + g * group_bytes) + lane, a.npad, F, u);
+                couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, u, lb);
+            } else {
+                int u[32];
+#pragma unroll
+                for (int b = 0; b < 32; ++b) u[b] = 0;
+                scan_wide(reinterpret_cast<const int4 *>(tables + g * group_bytes) + lane, a.npad, F, u);
+                couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, u, lb);
+            }
+        }
+        const int best = transpose_max(lb, lane);
+        if (x < a.N) a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
+        __syncwarp();  // the flag and row arrays are rewritten by the next batch
+    }
+    // the issuing thread never leaves while its copy may still be landing
+    if (threadIdx.x == 0 && !ready) mbar_wait_bounded(bar, 0, a.wait_limit);
+}
+
+// ---------------------------------------------------------------- streamed
+template <bool WIDE, int MP>
+__global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint8_t *sgp = smem + 16;
+    uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * a.n;
+    int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    for (int i = threadIdx.x; i < a.G * 64; i += blockDim.x) sgp[i] = a.gpairs[i];
+    __syncthreads();
+
+    TilePipe tp{bar, smem + a.off_tables, a.tile_stride, a.ntiles <= 2};
+    auto tile_issue = [&](uint32_t fill, int t) {
+        const int g = t / a.nchunks, ch = t - g * a.nchunks;
+        const int pos = min(a.chunk, a.npad - ch * a.chunk);
+        const unsigned char *src = a.grec + ((size_t)g * a.npad + (size_t)ch * a.chunk) * 32 * a.rec_bytes;
+        tp.issue(fill, src, (uint32_t)pos * 32u * a.rec_bytes);
+    };
+    if (threadIdx.x == 0 && (int64_t)blockIdx.x < a.num_batches) {
+        tile_issue(0, 0);
+        if (a.ntiles == 2) tile_issue(1, 1);
+    }
+
+    for (int64_t bt = blockIdx.x; bt < a.num_batches; bt += gridDim.x) {
+        const int64_t x = bt * (int64_t)(32 * W) + warp * 32 + lane;
+        int bterm = 0;
+        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm);
+        int lb[32];
+        float uf[32];
+        int ui[32];
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+            lb[b] = 0;
+            uf[b] = 0.f;
+            ui[b] = 0;
+        }
+        int kk = 0, ll = 1;
+        for (int t = 0; t < a.ntiles; ++t) {
+            const int g = t / a.nchunks, ch = t - g * a.nchunks;
+            if (!tp.resident && threadIdx.x == 0) {
+                const bool has_next = (t + 1 < a.ntiles) || (bt + gridDim.x < a.num_batches);
+                if (has_next) tile_issue(tp.fill + 1, (t + 1) % a.ntiles);
+            }
+            if (!tp.wait(t, a.wait_limit)) {
+                if (threadIdx.x == 0) {
+                    report_status(a.status, (int32_t)FSP_ETIMEDOUT);
+                    tp.drain(a.wait_limit);
+                }
+                return;
+            }
+            const unsigned char *tb = tp.buf + tp.current(t) * tp.stride;
+            if (ch == 0) {
+#pragma unroll
+                for (int b = 0; b < 32; ++b) {
+                    uf[b] = 0.f;
+                    ui[b] = 0;
+                }
+                kk = sgp[2 * (g * 32 + lane)];
+                ll = sgp[2 * (g * 32 + lane) + 1];
+            }
+            const int npos = min(a.chunk, a.npad - ch * a.chunk);
+            if (!WIDE)
+                scan_compact(reinterpret_cast<const uint32_t *>(tb) + lane, npos, F, uf);
+            else
+                scan_wide(reinterpret_cast<const int4 *>(tb) + lane, npos, F, ui);
+            if (ch == a.nchunks - 1) {
+                if (!WIDE)
+                    couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, uf, lb);
+                else
+                    couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, ui, lb);
+            }
+            if (!tp.resident) {
+                __syncthreads();
+                ++tp.fill;
+            }
+        }
+        const int best = transpose_max(lb, lane);
+        if (x < a.N) a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
+        __syncwarp();  // the flag and row arrays are rewritten by the next batch
+    }
+}
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct LanesLayout {
+    uint32_t off_tables, tile_stride, off_flags, off_aq;
+    int32_t aq_stride;
+    size_t total;
+};
+
+int aq_stride_for(int m) { return (m + (m + 1) / 2) | 1; }
+
+LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident, int chunk) {
+    LanesLayout L;
+    L.off_tables = (uint32_t)align_up(16 + (size_t)inst->G * 64, 128);
+    const size_t group_bytes = (size_t)inst->npad * 32 * inst->rec_bytes;
+    if (resident) {
+        L.tile_stride = (uint32_t)group_bytes;
+        L.off_flags = (uint32_t)align_up(L.off_tables + group_bytes * inst->G, 128);
+    } else {
+        L.tile_stride = (uint32_t)align_up((size_t)chunk * 32 * inst->rec_bytes, 128);
+        L.off_flags = L.off_tables + 2 * L.tile_stride;
+    }
+    L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)warps * inst->n * 4, 128);
+    L.aq_stride = aq_stride_for(inst->m);
+    L.total = align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
+    return L;
+}
+
+template <typename K>
+cudaError_t set_smem_attr(K kernel) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+template <bool WIDE, int MP>
+cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int grid, int threads, size_t smem,
+                                 cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = set_smem_attr(fsp_lanes_resident<WIDE, MP>);
+        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP>);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    if (resident)
+        fsp_lanes_resident<WIDE, MP><<<grid, threads, smem, s>>>(a);
+    else
+        fsp_lanes_streamed<WIDE, MP><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool WIDE>
+cudaError_t launch_lanes_mp(const LanesArgs &a, int mp, bool resident, int grid, int threads, size_t smem,
+                            cudaStream_t s) {
+    switch (mp) {
+        case 8: return launch_lanes_variant<WIDE, 8>(a, resident, grid, threads, smem, s);
+        case 12: return launch_lanes_variant<WIDE, 12>(a, resident, grid, threads, smem, s);
+        case 16: return launch_lanes_variant<WIDE, 16>(a, resident, grid, threads, smem, s);
+        case 20: return launch_lanes_variant<WIDE, 20>(a, resident, grid, threads, smem, s);
+        case 24: return launch_lanes_variant<WIDE, 24>(a, resident, grid, threads, smem, s);
+        default: return launch_lanes_variant<WIDE, 32>(a, resident, grid, threads, smem, s);
+    }
+}
+
+}  // namespace
+
+fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, size_t *smem_bytes) {
+    const int W = c.warps_per_block;
+    if (W < 1 || W > 16) return FSP_EINVAL;
+    const bool resident = c.staging == FSP_STAGING_RESIDENT;
+    if (!resident && (c.positions_per_tile < 4 || (c.positions_per_tile & 3))) return FSP_EINVAL;
+    const int chunk = resident ? inst->npad : std::min(c.positions_per_tile, inst->npad);
+    const LanesLayout L = lanes_layout_for(inst, W, resident, chunk);
+    if (L.total > (size_t)max_smem_per_block(inst->device)) return FSP_EINVAL;
+    // the resident copy completes on one mbarrier: its byte count must fit the transaction counter
+    if (resident && (size_t)inst->npad * 32 * inst->rec_bytes * inst->G >= (1u << 20)) return FSP_EINVAL;
+    *smem_bytes = L.total;
+    return FSP_OK;
+}
+
+fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
+                        int32_t *out_lb, void *stream, const fsp_launch_config &cfg) {
+    size_t smem = 0;
+    fsp_status st = lanes_layout(inst, cfg, &smem);
+    if (st != FSP_OK) return st;
+    const int W = cfg.warps_per_block;
+    const bool resident = cfg.staging == FSP_STAGING_RESIDENT;
+    const int chunk = resident ? inst->npad : std::min(cfg.positions_per_tile, inst->npad);
+    const LanesLayout L = lanes_layout_for(inst, W, resident, chunk);
+    LanesArgs a;
+    a.grec = static_cast<const unsigned char *>(inst->t.grec);
+    a.gpairs = inst->t.gpairs;
+    a.hsort = reinterpret_cast<const int2 *>(inst->t.hsort);
+    a.tsort = reinterpret_cast<const int2 *>(inst->t.tsort);
+    a.ptot = inst->t.ptot;
+    a.pp = inst->t.pp;
+    a.nodes = nodes;
+    a.depths = depths;
+    a.out = out_lb;
+    a.status = inst->dev_status;
+    a.N = N;
+    a.n = inst->n;
+    a.m = inst->m;
+    a.G = inst->G;
+    a.npad = inst->npad;
+    a.mpad = inst->mpad;
+    a.chunk = chunk;
+    a.nchunks = (inst->npad + chunk - 1) / chunk;
+    a.ntiles = inst->G * a.nchunks;
+    a.rec_bytes = (uint32_t)inst->rec_bytes;
+    a.off_tables = L.off_tables;
+    a.tile_stride = L.tile_stride;
+    a.off_flags = L.off_flags;
+    a.off_aq = L.off_aq;
+    a.aq_stride = L.aq_stride;
+    a.wait_limit = 4000000000LL;
+    int grid;
+    if (resident) {
+        a.num_batches = (N + 31) / 32;
+        // at least one warp batch per warp of the grid
+        const int64_t per_block = std::max<int64_t>(1, W);
+        grid = (int)std::min<int64_t>((a.num_batches + per_block - 1) / per_block, (int64_t)num_sms(inst->device));
+    } else {
+        a.num_batches = (N + 32 * W - 1) / (32 * W);
+        grid = (int)std::min<int64_t>(a.num_batches, (int64_t)num_sms(inst->device));
+    }
+    grid = std::max(grid, 1);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaError_t e = inst->compact ? launch_lanes_mp<false>(a, inst->mpad, resident, grid, 32 * W, smem, s)
+                                        : launch_lanes_mp<true>(a, inst->mpad, resident, grid, 32 * W, smem, s);
+    return e == cudaSuccess ? FSP_OK : FSP_ECUDA;
+}
+
+}  // namespace fspgb

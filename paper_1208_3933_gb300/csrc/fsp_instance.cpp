@@ -119,6 +119,31 @@ extern "C" fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m
         }
     }
 
+    // Couple-lanes layout: couple c in group c/32, lane c%32, position-major.
+    inst->G = (P + 31) / 32;
+    const int G = inst->G;
+    std::vector<uint32_t> grec_c;
+    std::vector<int32_t> grec_w;
+    if (inst->compact)
+        grec_c.assign((size_t)G * npad * 32, 0u);
+    else
+        grec_w.assign((size_t)G * npad * 32 * 4, 0);
+    for (int c = 0; c < P; ++c) {
+        const int g = c / 32, lane = c % 32;
+        for (int i = 0; i < npad; ++i) {
+            const size_t dst = ((size_t)g * npad + i) * 32 + lane;
+            if (inst->compact)
+                grec_c[dst] = rec_c[(size_t)c * npad + i];
+            else
+                for (int f = 0; f < 4; ++f) grec_w[dst * 4 + f] = rec_w[((size_t)c * npad + i) * 4 + f];
+        }
+    }
+    std::vector<uint8_t> gpairs((size_t)G * 32 * 2, 0);
+    for (int slot = 0; slot < G * 32; ++slot) {
+        gpairs[2 * slot] = slot < P ? inst->pairs[2 * slot] : 0;
+        gpairs[2 * slot + 1] = slot < P ? inst->pairs[2 * slot + 1] : 1;
+    }
+
     std::vector<int32_t> head((size_t)m * n), tail((size_t)m * n), ptm((size_t)m * n);
     for (int j = 0; j < n; ++j) {
         int64_t acc = 0;
@@ -134,6 +159,42 @@ extern "C" fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m
         for (int k = 0; k < m; ++k) ptm[(size_t)k * n + j] = p[j * m + k];
     }
 
+    // Jobs sorted by head (resp. tail) per machine: the minimum over the
+    // unscheduled jobs is the first unscheduled entry of the sorted list.
+    std::vector<int32_t> hsort((size_t)m * n * 2), tsort((size_t)m * n * 2), ptot(m, 0);
+    {
+        std::vector<int32_t> idx(n);
+        for (int k = 0; k < m; ++k) {
+            for (int j = 0; j < n; ++j) idx[j] = j;
+            std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+                const int32_t x = head[(size_t)k * n + a], y = head[(size_t)k * n + b];
+                return x != y ? x < y : a < b;
+            });
+            for (int i = 0; i < n; ++i) {
+                hsort[((size_t)k * n + i) * 2] = idx[i];
+                hsort[((size_t)k * n + i) * 2 + 1] = head[(size_t)k * n + idx[i]];
+            }
+            for (int j = 0; j < n; ++j) idx[j] = j;
+            std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+                const int32_t x = tail[(size_t)k * n + a], y = tail[(size_t)k * n + b];
+                return x != y ? x < y : a < b;
+            });
+            for (int i = 0; i < n; ++i) {
+                tsort[((size_t)k * n + i) * 2] = idx[i];
+                tsort[((size_t)k * n + i) * 2 + 1] = tail[(size_t)k * n + idx[i]];
+            }
+            int64_t tot = 0;
+            for (int j = 0; j < n; ++j) tot += p[j * m + k];
+            ptot[k] = (int32_t)tot;
+        }
+    }
+
+    inst->mpad = m <= 8 ? 8 : m <= 12 ? 12 : m <= 16 ? 16 : m <= 20 ? 20 : m <= 24 ? 24 : 32;
+    const int mpad = inst->mpad;
+    std::vector<int32_t> pp((size_t)n * mpad, 0);
+    for (int j = 0; j < n; ++j)
+        for (int k = 0; k < m; ++k) pp[(size_t)j * mpad + k] = p[j * m + k];
+
     // One device block, every array 256-byte aligned.
     const size_t rec_sz = (size_t)P * npad * inst->rec_bytes;
     const size_t off_rec = 0;
@@ -142,7 +203,14 @@ extern "C" fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m
     const size_t off_head = align_up(off_p + sizeof(int32_t) * n * m, 256);
     const size_t off_tail = align_up(off_head + sizeof(int32_t) * n * m, 256);
     const size_t off_ptm = align_up(off_tail + sizeof(int32_t) * n * m, 256);
-    const size_t bytes = align_up(off_ptm + sizeof(int32_t) * n * m, 256);
+    const size_t grec_sz = (size_t)G * npad * 32 * inst->rec_bytes;
+    const size_t off_grec = align_up(off_ptm + sizeof(int32_t) * n * m, 256);
+    const size_t off_gpairs = align_up(off_grec + grec_sz, 256);
+    const size_t off_hsort = align_up(off_gpairs + gpairs.size(), 256);
+    const size_t off_tsort = align_up(off_hsort + sizeof(int32_t) * hsort.size(), 256);
+    const size_t off_ptot = align_up(off_tsort + sizeof(int32_t) * tsort.size(), 256);
+    const size_t off_pp = align_up(off_ptot + sizeof(int32_t) * m, 256);
+    const size_t bytes = align_up(off_pp + sizeof(int32_t) * pp.size(), 256);
 
     fsp_status st = FSP_OK;
     unsigned char *blk = nullptr;
@@ -158,7 +226,16 @@ extern "C" fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m
             cudaMemcpy(blk + off_p, p, sizeof(int32_t) * n * m, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(blk + off_head, head.data(), sizeof(int32_t) * n * m, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(blk + off_tail, tail.data(), sizeof(int32_t) * n * m, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(blk + off_ptm, ptm.data(), sizeof(int32_t) * n * m, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaMemcpy(blk + off_ptm, ptm.data(), sizeof(int32_t) * n * m, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(blk + off_grec, inst->compact ? (const void *)grec_c.data() : (const void *)grec_w.data(),
+                       grec_sz, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(blk + off_gpairs, gpairs.data(), gpairs.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(blk + off_hsort, hsort.data(), sizeof(int32_t) * hsort.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(blk + off_tsort, tsort.data(), sizeof(int32_t) * tsort.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(blk + off_ptot, ptot.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(blk + off_pp, pp.data(), sizeof(int32_t) * pp.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
             st = FSP_ECUDA;
         }
     }
@@ -189,6 +266,12 @@ extern "C" fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m
     inst->t.head = (const int32_t *)(blk + off_head);
     inst->t.tail = (const int32_t *)(blk + off_tail);
     inst->t.ptm = (const int32_t *)(blk + off_ptm);
+    inst->t.grec = blk + off_grec;
+    inst->t.gpairs = (const uint8_t *)(blk + off_gpairs);
+    inst->t.hsort = (const int32_t *)(blk + off_hsort);
+    inst->t.tsort = (const int32_t *)(blk + off_tsort);
+    inst->t.ptot = (const int32_t *)(blk + off_ptot);
+    inst->t.pp = (const int32_t *)(blk + off_pp);
     *out = inst;
     return FSP_OK;
 }

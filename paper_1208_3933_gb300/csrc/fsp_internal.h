@@ -5,18 +5,26 @@
 // each array 256-byte aligned so the bulk copies that stage them into shared
 // memory start on a 16-byte boundary.
 //
-//   rec    [P][npad]  Johnson order of every couple with the per-entry
-//                     constants of the bounding recurrence (see below);
-//                     couples are ordered by their second machine l, then k
-//   pairs  [P][2]     uint8 (k,l) of each couple, in the same order (MM)
-//   p      [n][m]     int32 processing times (PTM), job-major
-//   head   [m][n]     int32 sum_{h<k} p_jh, machine-major (for RM)
-//   tail   [m][n]     int32 sum_{h>l} p_jh, machine-major (for QM)
-//   ptm    [m][n]     int32 p_jk, machine-major (column sums over U)
+//   rec    [P][npad]      Johnson order of every couple with the per-entry
+//                         constants of the bounding recurrence (see below);
+//                         couples ordered by their second machine l, then k
+//   pairs  [P][2]         uint8 (k,l) of each couple, in the same order (MM)
+//   grec   [G][npad][32]  the same records regrouped for the couple-lanes
+//                         kernel: couple c sits in group c/32, lane c%32;
+//                         the slots past P are empty couples
+//   gpairs [G*32][2]      (k,l) per group slot; empty slots read (0,1)
+//   hsort  [m][n]         int2 (job, sum_{h<k} p_jh) sorted by the sum (RM)
+//   tsort  [m][n]         int2 (job, sum_{h>k} p_jh) sorted by the sum (QM)
+//   ptot   [m]            sum over all jobs of p_jk
+//   pp     [n][mpad]      p with rows zero-padded to mpad (vector loads)
+//   p      [n][m]         int32 processing times (PTM), job-major
+//   head   [m][n]         int32 sum_{h<k} p_jh, machine-major (for RM)
+//   tail   [m][n]         int32 sum_{h>l} p_jh, machine-major (for QM)
+//   ptm    [m][n]         int32 p_jk, machine-major (column sums over U)
 //
 // One Johnson entry of couple c=(k,l) for job j carries
 //   delta = p_jl - p_jk   and   s = lag_j + p_jl,   lag_j = sum_{k<h<l} p_jh,
-// because the kernel runs the pseudo-code's two-machine recurrence on the
+// because the kernels run the pseudo-code's two-machine recurrence on the
 // slack u = timeOnM2 - timeOnM1:  u <- max(u + delta, s)  for j in U.
 //
 // Compact 32-bit record (n <= 1024, 0 <= s < 8192, -256 <= delta < 256):
@@ -24,8 +32,10 @@
 //   bits 10..22  s
 //   bits 23..31  delta (two's complement)
 // Wide record: int4 {j, s, delta, 0}.
-// Padding entries (npad - n per couple) are all-zero records: for any u >= 0,
-// max(u + 0, 0) = u, so they never change the result.
+// Padding entries and empty couples are all-zero records: for any u >= 0,
+// max(u + 0, 0) = u, so they never change the result, and an empty couple
+// read as (0,1) contributes A_0 + q_1, which never exceeds couple (0,1)'s
+// own value.
 #pragma once
 
 #include <cstddef>
@@ -33,7 +43,7 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/fsp.h"
+#include "fsp.h"
 
 namespace fspgb {
 
@@ -43,6 +53,12 @@ constexpr int kRecAlign = 4;           // couple rows padded to 4 entries (16 B 
 struct DeviceTables {
     const void *rec = nullptr;
     const uint8_t *pairs = nullptr;
+    const void *grec = nullptr;
+    const uint8_t *gpairs = nullptr;
+    const int32_t *hsort = nullptr;  // int2 pairs
+    const int32_t *tsort = nullptr;  // int2 pairs
+    const int32_t *ptot = nullptr;
+    const int32_t *pp = nullptr;     // [n][mpad] p with zero-padded rows
     const int32_t *p = nullptr;
     const int32_t *head = nullptr;
     const int32_t *tail = nullptr;
@@ -53,6 +69,8 @@ struct DeviceTables {
 
 struct fsp_instance {
     int32_t n = 0, m = 0, P = 0, npad = 0;
+    int32_t G = 0;                  // couple groups of 32 (couple-lanes layout)
+    int32_t mpad = 0;               // m rounded up to 8, 12, 16, 20, 24 or 32
     int32_t compact = 1;
     int32_t device = 0;
     int32_t rec_bytes = 4;          // bytes per Johnson record
@@ -75,6 +93,12 @@ fsp_status resolve_config(const fsp_instance *inst, int64_t N, const fsp_launch_
                           fsp_launch_config *out, size_t *smem_bytes);
 fsp_status launch_bound(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths,
                         int64_t N, int32_t *out_lb, void *stream, const fsp_launch_config *cfg);
+// Couple-lanes kernel (fsp_bound_lanes.cu).
+fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &cfg, size_t *smem_bytes);
+fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
+                        int32_t *out_lb, void *stream, const fsp_launch_config &cfg);
+int max_smem_per_block(int device);
+int num_sms(int device);
 fsp_status check_device(const fsp_instance *inst);
 fsp_status take_device_status(const fsp_instance *inst);
 

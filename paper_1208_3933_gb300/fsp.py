@@ -44,9 +44,30 @@ class fsp_instance_info(ctypes.Structure):
                 ("device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+FSP_KERNEL_AUTO = 0
+FSP_KERNEL_LOCKSTEP = 1
+FSP_KERNEL_LANES = 2
+FSP_STAGING_AUTO = 0
+FSP_STAGING_RESIDENT = 1
+FSP_STAGING_STREAMED = 2
+
+
 class fsp_launch_config(ctypes.Structure):
-    _fields_ = [("nodes_per_thread", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("pairs_per_tile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("kernel", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("pairs_per_tile", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("positions_per_tile", ctypes.c_int32),
+                ("staging", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+
+
+def launch_config(**fields) -> fsp_launch_config:
+    """fsp_launch_config from keyword fields (missing ones are 0 = choose)."""
+    cfg = fsp_launch_config()
+    for k, v in fields.items():
+        setattr(cfg, k, int(v))
+    return cfg
 
 
 def load():
@@ -70,6 +91,9 @@ def load():
             "fsp_bound_pool_ex": ([vp, vp, vp, i64, vp, vp, ctypes.POINTER(fsp_launch_config)], i32),
             "fsp_bound_pool_host": ([vp, vp, vp, i64, vp, vp], i32),
             "fsp_branch_and_bound": ([vp, i32, i16p, i32p, i64p], i32),
+            "fsp_autotune": ([vp, vp, vp, i64, vp, vp, ctypes.c_char_p, ctypes.POINTER(fsp_launch_config),
+                              ctypes.POINTER(ctypes.c_float)], i32),
+            "fsp_tuned_config": ([vp, i64, ctypes.POINTER(fsp_launch_config)], i32),
             "fsp_status_string": ([i32], ctypes.c_char_p),
             "fsp_version": ([], ctypes.c_char_p),
         }
@@ -184,12 +208,34 @@ def fsp_bound_pool(inst: Instance, nodes, depths, out=None, stream=None, config=
                                 N, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
         _check(st, "fsp_bound_pool")
     else:
-        cfg = fsp_launch_config(*[int(x) for x in config], 0) if not isinstance(config, fsp_launch_config) else config
+        cfg = config if isinstance(config, fsp_launch_config) else launch_config(**dict(config))
         st = lib.fsp_bound_pool_ex(inst.handle, ctypes.c_void_p(nodes.data_ptr()),
                                    ctypes.c_void_p(depths.data_ptr()), N, ctypes.c_void_p(out.data_ptr()),
                                    _stream_handle(stream), ctypes.byref(cfg))
         _check(st, "fsp_bound_pool_ex")
     return out
+
+
+def fsp_autotune(inst: Instance, nodes, depths, out=None, stream=None, cache_path=None):
+    """Times every launch shape on this pool, keeps the fastest for N in the
+    instance; returns (config dict, ms per launch or -1 if cached)."""
+    import torch
+    if out is None:
+        out = torch.empty(depths.shape[0], dtype=torch.int32, device=depths.device)
+    N = _check_pool(inst, nodes, depths, out)
+    best = fsp_launch_config()
+    ms = ctypes.c_float(0)
+    st = load().fsp_autotune(inst.handle, ctypes.c_void_p(nodes.data_ptr()), ctypes.c_void_p(depths.data_ptr()), N,
+                             ctypes.c_void_p(out.data_ptr()), _stream_handle(stream),
+                             cache_path.encode() if cache_path else None, ctypes.byref(best), ctypes.byref(ms))
+    _check(st, "fsp_autotune")
+    return best.as_dict(), float(ms.value)
+
+
+def fsp_tuned_config(inst: Instance, N: int) -> dict:
+    cfg = fsp_launch_config()
+    _check(load().fsp_tuned_config(inst.handle, int(N), ctypes.byref(cfg)), "fsp_tuned_config")
+    return cfg.as_dict()
 
 
 def fsp_bound_pool_host(inst: Instance, nodes, depths, out=None, stream=None):

@@ -52,14 +52,32 @@ def test_pool_matches_oracle(gpu_lib, n, m, N):
 @pytest.mark.parametrize("K", [1, 2, 4, 8])
 @pytest.mark.parametrize("bps", [1, 2])
 @pytest.mark.parametrize("ppt", [0, 1, 7])
-def test_every_launch_shape_matches_oracle(gpu_lib, K, bps, ppt):
-    """Explicit shapes, including couple tiles of 1 and 7 couples (190
-    couples at m=20), which force re-staging of the tables for every node
-    tile and a ragged last tile."""
+def test_every_lockstep_shape_matches_oracle(gpu_lib, K, bps, ppt):
+    """Node-lockstep kernel, explicit shapes, including couple tiles of 1 and
+    7 couples (190 couples at m=20), which force re-staging of the tables for
+    every node tile and a ragged last tile."""
     fsp = gpu_lib
     p, rows, depths = pool(77, 40, 20, 3 * 128 * K + 17)
+    cfg = dict(kernel=fsp.FSP_KERNEL_LOCKSTEP, nodes_per_thread=K, blocks_per_sm=bps, pairs_per_tile=ppt)
     with fsp.Instance(p) as inst:
-        got = gpu_bounds(fsp, inst, rows, depths, config=(K, bps, ppt))
+        got = gpu_bounds(fsp, inst, rows, depths, config=cfg)
+    assert np.array_equal(got, oracle_bounds(p, rows, depths))
+
+
+@pytest.mark.parametrize("W", [1, 3, 16])
+@pytest.mark.parametrize("staging,positions", [(1, 0), (2, 0), (2, 4), (2, 12), (2, 64)])
+@pytest.mark.parametrize("nm", [(40, 20), (23, 9), (17, 5), (70, 12), (33, 27)])
+def test_every_lanes_shape_matches_oracle(gpu_lib, W, staging, positions, nm):
+    """Couple-lanes kernel, explicit shapes: 1 to 16 warps per block; records
+    resident (warps claim batches independently) or streamed with Johnson
+    positions staged 4, 12 or 64 at a time (re-staging, ragged last chunk);
+    couple counts below, at and above one warp of 32 (m = 5, 9, 12, 20, 27)."""
+    fsp = gpu_lib
+    n, m = nm
+    p, rows, depths = pool(78 + n, n, m, 2 * 32 * W * 3 + 19)
+    cfg = dict(kernel=fsp.FSP_KERNEL_LANES, warps_per_block=W, positions_per_tile=positions, staging=staging)
+    with fsp.Instance(p) as inst:
+        got = gpu_bounds(fsp, inst, rows, depths, config=cfg)
     assert np.array_equal(got, oracle_bounds(p, rows, depths))
 
 
@@ -70,10 +88,16 @@ def test_wide_records_match_oracle(gpu_lib):
     with fsp.Instance(p) as inst:
         assert inst.info().compact == 0
         got = gpu_bounds(fsp, inst, rows, depths)
-        got_k1 = gpu_bounds(fsp, inst, rows, depths, config=(1, 1, 5))
+        got_k1 = gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=1, nodes_per_thread=1, blocks_per_sm=1,
+                                                                   pairs_per_tile=5))
+        got_lanes = gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=2, warps_per_block=4,
+                                                                      positions_per_tile=16, staging=2))
+        got_res = gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=2, warps_per_block=4, staging=1))
     want = oracle_bounds(p, rows, depths)
     assert np.array_equal(got, want)
     assert np.array_equal(got_k1, want)
+    assert np.array_equal(got_lanes, want)
+    assert np.array_equal(got_res, want)
 
 
 def test_pair_tiled_500x20_matches_oracle(gpu_lib):
@@ -183,6 +207,9 @@ def test_full_size_pools_sampled(gpu_lib, name, sample):
     w = workloads.named_pool(name)
     with fsp.Instance(w.p) as inst:
         got = gpu_bounds(fsp, inst, w.rows, w.depths)
+        other = dict(kernel=fsp.FSP_KERNEL_LOCKSTEP)
+        got_other = gpu_bounds(fsp, inst, w.rows, w.depths, config=other)
+    assert np.array_equal(got, got_other)
     idx = np.sort(np.random.default_rng(123).choice(w.N, sample, replace=False))
     idx = np.unique(np.concatenate([idx, [0, w.N - 1]]))
     want = oracle_bounds(w.p, w.rows[idx], w.depths[idx])
