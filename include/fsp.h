@@ -92,7 +92,7 @@ typedef struct fsp_instance_info {
 typedef struct fsp_launch_config {
     int32_t kernel;              /* FSP_KERNEL_* */
     int32_t nodes_per_thread;    /* lockstep: K in {1,2,4,8} */
-    int32_t blocks_per_sm;       /* lockstep: resident blocks per SM (1 or 2) */
+    int32_t blocks_per_sm;       /* resident blocks per SM (1 or 2; lanes: streamed staging only) */
     int32_t pairs_per_tile;      /* lockstep: couples staged in shared memory at a time */
     int32_t warps_per_block;     /* lanes: 1..16 warps of 32 nodes */
     int32_t positions_per_tile;  /* lanes, streamed: Johnson positions per tile (multiple of 4) */

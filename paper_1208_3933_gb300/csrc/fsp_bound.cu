@@ -403,8 +403,9 @@ fsp_status resolve_lockstep(const fsp_instance *inst, int64_t N, const DeviceLim
 
 fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits &d, fsp_launch_config &c) {
     if (c.warps_per_block < 0 || c.warps_per_block > 16 || c.positions_per_tile < 0 ||
-        (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 2)
+        (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 2 || c.blocks_per_sm < 0 || c.blocks_per_sm > 2)
         return FSP_EINVAL;
+    if (!c.blocks_per_sm) c.blocks_per_sm = 1;
     const int npad = inst->npad;
     auto fits = [&](int W, int staging, int pos) {
         fsp_launch_config t = c;
@@ -436,6 +437,7 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
             c.warps_per_block = bW;
             c.staging = FSP_STAGING_RESIDENT;
             c.positions_per_tile = 0;
+            c.blocks_per_sm = 1;
             return FSP_OK;
         }
         return FSP_EINVAL;
@@ -444,12 +446,13 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     if (!c.warps_per_block) {
         double best = -1.0;
         int bW = 0;
-        for (int W = 16; W >= 1; --W) {
+        for (int W = 16 / c.blocks_per_sm; W >= 1; --W) {
             const int ch = c.positions_per_tile ? c.positions_per_tile : best_chunk(W);
             if (ch < 4 || !fits(W, FSP_STAGING_STREAMED, ch)) continue;
             if (!c.positions_per_tile && ch < std::min(npad, 64)) continue;
             const double batches = std::ceil((double)std::max<int64_t>(N, 1) / (32.0 * W));
-            const double score = wave_efficiency(batches, d.num_sms) * std::min(1.0, W / 12.0);
+            const double score = wave_efficiency(batches, (double)d.num_sms * c.blocks_per_sm) *
+                                 std::min(1.0, W * c.blocks_per_sm / 12.0);
             if (score > best + 1e-9) {
                 best = score;
                 bW = W;
@@ -466,6 +469,7 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
 }  // namespace
 
 int max_smem_per_block(int device) { return device_limits(device).smem_optin; }
+int max_smem_per_sm(int device) { return device_limits(device).smem_sm; }
 int num_sms(int device) { return device_limits(device).num_sms; }
 
 fsp_status check_device(const fsp_instance *inst) {

@@ -280,12 +280,16 @@ cudaError_t launch_lanes_mp(const LanesArgs &a, int mp, bool resident, int grid,
 
 fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, size_t *smem_bytes) {
     const int W = c.warps_per_block;
-    if (W < 1 || W > 16) return FSP_EINVAL;
+    const int bps = c.blocks_per_sm ? c.blocks_per_sm : 1;
+    if (W < 1 || W > 16 || bps < 1 || bps > 2 || W * bps > 16) return FSP_EINVAL;
     const bool resident = c.staging == FSP_STAGING_RESIDENT;
     if (!resident && (c.positions_per_tile < 4 || (c.positions_per_tile & 3))) return FSP_EINVAL;
     const int chunk = resident ? inst->npad : std::min(c.positions_per_tile, inst->npad);
     const LanesLayout L = lanes_layout_for(inst, W, resident, chunk);
-    if (L.total > (size_t)max_smem_per_block(inst->device)) return FSP_EINVAL;
+    const size_t budget = bps == 1 ? (size_t)max_smem_per_block(inst->device)
+                                   : std::min((size_t)max_smem_per_block(inst->device),
+                                              (size_t)max_smem_per_sm(inst->device) / 2 - 1024);
+    if (L.total > budget) return FSP_EINVAL;
     // the resident copy completes on one mbarrier: its byte count must fit the transaction counter
     if (resident && (size_t)inst->npad * 32 * inst->rec_bytes * inst->G >= (1u << 20)) return FSP_EINVAL;
     *smem_bytes = L.total;
@@ -336,7 +340,8 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
         grid = (int)std::min<int64_t>((a.num_batches + per_block - 1) / per_block, (int64_t)num_sms(inst->device));
     } else {
         a.num_batches = (N + 32 * W - 1) / (32 * W);
-        grid = (int)std::min<int64_t>(a.num_batches, (int64_t)num_sms(inst->device));
+        const int bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 1;
+        grid = (int)std::min<int64_t>(a.num_batches, (int64_t)num_sms(inst->device) * bps);
     }
     grid = std::max(grid, 1);
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -98,6 +98,7 @@ fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &cfg, 
 fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
                         int32_t *out_lb, void *stream, const fsp_launch_config &cfg);
 int max_smem_per_block(int device);
+int max_smem_per_sm(int device);
 int num_sms(int device);
 fsp_status check_device(const fsp_instance *inst);
 fsp_status take_device_status(const fsp_instance *inst);

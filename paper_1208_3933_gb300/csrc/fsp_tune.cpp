@@ -92,6 +92,11 @@ std::vector<fsp_launch_config> candidates(const fsp_instance *inst, int64_t N) {
             c.staging = FSP_STAGING_STREAMED;
             c.positions_per_tile = pos;
             add(c);
+            if (W <= 8) {
+                fsp_launch_config c2 = c;
+                c2.blocks_per_sm = 2;
+                add(c2);
+            }
         }
     }
     for (int K : {8, 4, 2, 1})

@@ -62,6 +62,11 @@ class fsp_launch_config(ctypes.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
 
 
+class fsp_pool_desc(ctypes.Structure):
+    _fields_ = [("inst", ctypes.c_void_p), ("nodes", ctypes.c_void_p), ("depths", ctypes.c_void_p),
+                ("out_lb", ctypes.c_void_p), ("N", ctypes.c_int64)]
+
+
 def launch_config(**fields) -> fsp_launch_config:
     """fsp_launch_config from keyword fields (missing ones are 0 = choose)."""
     cfg = fsp_launch_config()
@@ -94,6 +99,11 @@ def load():
             "fsp_autotune": ([vp, vp, vp, i64, vp, vp, ctypes.c_char_p, ctypes.POINTER(fsp_launch_config),
                               ctypes.POINTER(ctypes.c_float)], i32),
             "fsp_tuned_config": ([vp, i64, ctypes.POINTER(fsp_launch_config)], i32),
+            "fsp_batch_create": ([ctypes.POINTER(fsp_pool_desc), i32, i32, ctypes.POINTER(vp)], i32),
+            "fsp_batch_launch": ([vp, vp], i32),
+            "fsp_batch_launch_graph": ([vp, vp], i32),
+            "fsp_batch_query": ([vp, i64p, i64p, i32p, i32p], i32),
+            "fsp_batch_destroy": ([vp], None),
             "fsp_status_string": ([i32], ctypes.c_char_p),
             "fsp_version": ([], ctypes.c_char_p),
         }
@@ -275,3 +285,53 @@ def fsp_branch_and_bound(inst: Instance, ub0: int):
     if st not in (FSP_OK, FSP_ENOTFOUND):
         raise FspError(st, "fsp_branch_and_bound")
     return st, int(best.value), perm, int(nodes.value)
+
+
+class Batch:
+    """Owns one fsp_batch plan over pools given as (instance, nodes, depths,
+    out) with torch CUDA tensors; keeps them alive while the plan exists."""
+
+    def __init__(self, pools, warps_per_block: int = 0):
+        lib = load()
+        self._keep = list(pools)
+        descs = (fsp_pool_desc * max(1, len(pools)))()
+        for i, (inst, nodes, depths, out) in enumerate(pools):
+            N = _check_pool(inst, nodes, depths, out)
+            descs[i] = fsp_pool_desc(inst.handle.value, nodes.data_ptr(), depths.data_ptr(), out.data_ptr(), N)
+        h = ctypes.c_void_p()
+        _check(lib.fsp_batch_create(descs, len(pools), int(warps_per_block), ctypes.byref(h)), "fsp_batch_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(load().fsp_batch_launch(self._h, _stream_handle(stream)), "fsp_batch_launch")
+
+    def launch_graph(self, stream=None):
+        _check(load().fsp_batch_launch_graph(self._h, _stream_handle(stream)), "fsp_batch_launch_graph")
+
+    def query(self) -> dict:
+        items, nodes = ctypes.c_int64(), ctypes.c_int64()
+        warps, blocks = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().fsp_batch_query(self._h, ctypes.byref(items), ctypes.byref(nodes), ctypes.byref(warps),
+                                      ctypes.byref(blocks)), "fsp_batch_query")
+        return dict(work_items=items.value, nodes=nodes.value, warps_per_block=warps.value, blocks=blocks.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().fsp_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fsp_batch_create(pools, warps_per_block: int = 0) -> Batch:
+    return Batch(pools, warps_per_block)

@@ -1,0 +1,119 @@
+"""Batched persistent launch (many pools of many instances in one kernel) vs
+the oracle and vs one plain launch per pool: bit-exact, alone and in the mix."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_3933_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def small_batch(seeds, max_nodes):
+    """Instances of the batched workload's recipe (n from {20,50,100,200}, m
+    from {5,10,20}), with pools cut to at most max_nodes nodes."""
+    out = []
+    for w in workloads.batched_instances(seeds):
+        N = min(w.N, max_nodes)
+        out.append(workloads.PoolWorkload(w.name, w.n, w.m, w.seed, w.p, w.rows[:N].copy(), w.depths[:N].copy()))
+    return out
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_batch_matches_oracle_and_plain_launches(gpu_lib):
+    import torch
+    fsp = gpu_lib
+    ws = small_batch(range(100, 112), 700)
+    insts = [fsp.Instance(w.p) for w in ws]
+    bufs = [(dev(w.rows), dev(w.depths)) for w in ws]
+    outs = [torch.full((w.N,), -7, dtype=torch.int32, device="cuda") for w in ws]
+    pools = [(inst, r, d, o) for inst, (r, d), o in zip(insts, bufs, outs)]
+    with fsp.Batch(pools) as b:
+        q = b.query()
+        assert q["nodes"] == sum(w.N for w in ws)
+        b.launch()
+        torch.cuda.synchronize()
+        got = [o.cpu().numpy().copy() for o in outs]
+        for o in outs:
+            o.fill_(-7)
+        b.launch_graph()
+        b.launch_graph()
+        torch.cuda.synchronize()
+        got_graph = [o.cpu().numpy().copy() for o in outs]
+    for w, inst, (r, d), g, gg in zip(ws, insts, bufs, got, got_graph):
+        alone = fsp.fsp_bound_pool(inst, r, d)
+        torch.cuda.synchronize()
+        want = oracle.Tables(w.p).lb_pool(w.rows, w.depths, threads=16)
+        assert np.array_equal(g, want), w.name
+        assert np.array_equal(gg, want), w.name
+        assert np.array_equal(alone.cpu().numpy(), want), w.name
+    for inst in insts:
+        inst.close()
+
+
+def test_batch_with_empty_invalid_and_ragged_pools(gpu_lib):
+    import torch
+    fsp = gpu_lib
+    rng = np.random.default_rng(9)
+    specs = [(7, 5, 0), (33, 12, 45), (20, 20, 1), (64, 3, 97), (20, 20, 33)]
+    insts, pools, ref = [], [], []
+    for n, m, N in specs:
+        p = rng.integers(1, 100, (n, m), dtype=np.int32)
+        rows, depths = workloads.random_pool(rng, n, N, max_depth=n + 1)
+        if N > 3:
+            depths[0] = -2          # invalid depth
+            rows[1, :3] = [0, 0, 1]  # duplicate
+            depths[1] = 3
+        inst = fsp.Instance(p)
+        insts.append(inst)
+        out = torch.empty(N, dtype=torch.int32, device="cuda")
+        pools.append((inst, dev(rows.reshape(N, n)), dev(depths), out))
+        ref.append(oracle.Tables(p).lb_pool(rows.reshape(N, n), depths, threads=8))
+    with fsp.Batch(pools, warps_per_block=3) as b:
+        b.launch()
+        torch.cuda.synchronize()
+    for (inst, _, _, out), want in zip(pools, ref):
+        assert np.array_equal(out.cpu().numpy(), want)
+    for inst in insts:
+        inst.close()
+
+
+def test_batch_rejects_wide_instances(gpu_lib):
+    import torch
+    fsp = gpu_lib
+    p = np.full((10, 4), 5000, np.int32)
+    with fsp.Instance(p) as inst:
+        r = torch.zeros((3, 10), dtype=torch.int16, device="cuda")
+        d = torch.zeros(3, dtype=torch.int32, device="cuda")
+        o = torch.empty(3, dtype=torch.int32, device="cuda")
+        with pytest.raises(fsp.FspError):
+            fsp.Batch([(inst, r, d, o)])
+
+
+def test_full_batched_workload_sampled(gpu_lib):
+    """The 64-instance batched workload (seeds 100-163, pools of 1,024 to
+    65,536 nodes) in one graph launch; every pool is compared with its own
+    plain launch, and a sample of nodes with the oracle."""
+    import torch
+    fsp = gpu_lib
+    ws = workloads.batched_instances()
+    insts = [fsp.Instance(w.p) for w in ws]
+    bufs = [(dev(w.rows), dev(w.depths)) for w in ws]
+    outs = [torch.empty(w.N, dtype=torch.int32, device="cuda") for w in ws]
+    with fsp.Batch([(i, r, d, o) for i, (r, d), o in zip(insts, bufs, outs)]) as b:
+        b.launch_graph()
+        torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    for w, inst, (r, d), o in zip(ws, insts, bufs, outs):
+        got = o.cpu().numpy()
+        alone = fsp.fsp_bound_pool(inst, r, d)
+        torch.cuda.synchronize()
+        assert np.array_equal(got, alone.cpu().numpy()), w.name
+        idx = rng.choice(w.N, min(w.N, 64), replace=False)
+        assert np.array_equal(got[idx], oracle.Tables(w.p).lb_pool(w.rows[idx], w.depths[idx], threads=16)), w.name
+    for inst in insts:
+        inst.close()
