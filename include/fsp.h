@@ -257,6 +257,32 @@ fsp_status fsp_batch_query(const fsp_batch *batch, int64_t *work_items, int64_t 
 /* Frees the plan; none of its launches may be in flight.  NULL is a no-op. */
 void fsp_batch_destroy(fsp_batch *batch);
 
+/* Largest number of pools fsp_bound_batch_noalloc accepts in one call. */
+#define FSP_NOALLOC_MAX_POOLS 64
+
+/*
+ * fsp_bound_batch_noalloc -- the batched bound of fsp_batch_create followed by
+ * fsp_batch_launch, for callers that cannot allocate memory when they need a
+ * bound: a process whose GPU memory is already owned by another allocator, a
+ * serving loop that must not take cudaMalloc's implicit synchronisation, or
+ * code running where allocation is not permitted.  The paper has no
+ * counterpart; it exists for such callers only.
+ *   pools  host array of `count` descriptors, 0 <= count <= FSP_NOALLOC_MAX_POOLS
+ *          (more is refused with FSP_EINVAL); every instance must use 32-bit
+ *          records and live on the current device;
+ *   cuda_stream  orders the work (NULL = legacy default stream).
+ * No device or host memory is allocated: the plan and the work counter live in
+ * a fixed per-device array inside the library, sized for
+ * FSP_NOALLOC_MAX_POOLS pools.  Every call reuses that array (it keeps the
+ * previous call's plan; the counter is reset by each call), so two calls whose
+ * work overlaps on the GPU race: order them on one stream or synchronise
+ * between them.  The first call on a device looks up the array's address with
+ * that device current; make that first call outside any stream capture.
+ * Stream-ordered; the descriptors are consumed before the call returns.
+ * Errors: FSP_EINVAL, FSP_ECUDA.
+ */
+fsp_status fsp_bound_batch_noalloc(const fsp_pool_desc *pools, int32_t count, void *cuda_stream);
+
 /* Static English text for a status code (never NULL). */
 const char *fsp_status_string(fsp_status s);
 

@@ -1,0 +1,224 @@
+// fsp_noalloc.cu -- a batched bound that allocates no memory.
+//
+// Some callers cannot allocate device memory at the moment they need a bound:
+// a process whose GPU memory is already owned by another allocator (a
+// framework's caching allocator holding the whole device), a serving loop
+// that must not take cudaMalloc's implicit device synchronisation, or code
+// running where allocation is not permitted.  fsp_bound_batch_noalloc gives
+// them the batched bound of fsp_batch_create + fsp_batch_launch without any
+// allocation: the plan (one argument block per pool, the prefix sums of the
+// pools' work items) and the work counter live in the file-scope array below,
+// whose size caps the number of pools per call.
+//
+// The array is one per device and shared by every call: a call overwrites
+// the previous call's plan and re-zeroes the counter, so calls whose work
+// overlaps on the GPU race with each other.  The first call on a device looks
+// up the array's device address (cudaGetSymbolAddress) with that device
+// current; do that first call outside any stream capture.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "fsp_internal.h"
+#include "fsp_lanes_device.cuh"
+
+namespace fspgb {
+namespace {
+
+constexpr int kNoallocMaxPools = FSP_NOALLOC_MAX_POOLS;
+
+// Layout of the scratch array: [pools][LanesArgs] | [pools+1][int64 item
+// offsets] | [int32 counter], each part 256-byte aligned.
+constexpr size_t kArgsBytes = (sizeof(LanesArgs) * kNoallocMaxPools + 255) / 256 * 256;
+constexpr size_t kOffsBytes = (sizeof(int64_t) * (kNoallocMaxPools + 1) + 255) / 256 * 256;
+constexpr size_t kScratchBytes = kArgsBytes + kOffsBytes + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+// Work item `claim` of the plan belongs to the pool whose [offs[p], offs[p+1])
+// range holds it (pools are ordered longest items first on the host).
+__device__ __forceinline__ int pool_of(const int64_t *offs, int count, int64_t claim) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(offs + mid) <= claim)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int MP>
+__global__ void __launch_bounds__(512, 1)
+    fsp_lanes_batch_noalloc(const unsigned char *scratch, int count, int64_t nitems, int32_t n_max,
+                            int32_t aq_stride, uint32_t off_aq) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const LanesArgs *pools = reinterpret_cast<const LanesArgs *>(scratch);
+    const int64_t *offs = reinterpret_cast<const int64_t *>(scratch + kArgsBytes);
+    int32_t *counter = reinterpret_cast<int32_t *>(const_cast<unsigned char *>(scratch) + kArgsBytes + kOffsBytes);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *F = reinterpret_cast<uint32_t *>(smem) + (size_t)warp * n_max;
+    int32_t *AQ = reinterpret_cast<int32_t *>(smem + off_aq) + (size_t)warp * 32 * aq_stride;
+    for (;;) {
+        int claim = 0;
+        if (lane == 0) claim = atomicAdd(counter, 1);
+        claim = __shfl_sync(kFull, claim, 0);
+        if ((int64_t)claim >= nitems) break;
+        const int pi = pool_of(offs, count, claim);
+        const LanesArgs &a = pools[pi];
+        const int64_t x = ((int64_t)claim - __ldg(offs + pi)) * 32 + lane;
+        int bterm = 0;
+        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * aq_stride, bterm);
+        int lb[32];
+#pragma unroll
+        for (int b = 0; b < 32; ++b) lb[b] = 0;
+        for (int g = 0; g < a.G; ++g) {
+            const int kk = __ldg(a.gpairs + 2 * (g * 32 + lane)), ll = __ldg(a.gpairs + 2 * (g * 32 + lane) + 1);
+            float u[32];
+#pragma unroll
+            for (int b = 0; b < 32; ++b) u[b] = 0.f;
+            const uint32_t *R = reinterpret_cast<const uint32_t *>(a.grec) + (size_t)g * a.npad * 32 + lane;
+#pragma unroll 4
+            for (int i = 0; i < a.npad; ++i) {
+                const uint32_t r = __ldg(R + i * 32);
+                const uint32_t fw = F[r & 1023u];
+                const float sf = __int_as_float(0x4B000000 | ((r >> 10) & 8191u)) - 8388608.0f;
+                const float df = __int_as_float(0x4B000000 | (uint32_t)(((int)r >> 23) + 256)) - 8388864.0f;
+#pragma unroll
+                for (int b = 0; b < 32; ++b)
+                    if ((fw >> b) & 1u) u[b] = fmaxf(u[b] + df, sf);
+            }
+            couple_epilogue(AQ, aq_stride, a.m, kk, ll, u, lb);
+        }
+        const int best = transpose_max(lb, lane);
+        if (x < a.N) a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
+        __syncwarp();
+    }
+}
+
+// Device address of the scratch array, looked up once per device.
+std::mutex g_addr_mu;
+unsigned char *g_addr[64] = {};
+
+fsp_status scratch_address(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= 64) return FSP_EINVAL;
+    std::lock_guard<std::mutex> g(g_addr_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FSP_ECUDA;
+        g_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_addr[dev];
+    return FSP_OK;
+}
+
+template <int MP>
+cudaError_t launch_noalloc(const unsigned char *scratch, int count, int64_t nitems, int n_max, int stride,
+                           uint32_t off_aq, int grid, int threads, size_t smem, cudaStream_t s) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(fsp_lanes_batch_noalloc<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fsp_lanes_batch_noalloc<MP><<<grid, threads, smem, s>>>(scratch, count, nitems, n_max, stride, off_aq);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace fspgb
+
+using namespace fspgb;
+
+extern "C" fsp_status fsp_bound_batch_noalloc(const fsp_pool_desc *pools, int32_t count, void *cuda_stream) {
+    if (count < 0 || (count > 0 && !pools)) return FSP_EINVAL;
+    if (count > kNoallocMaxPools) return FSP_EINVAL;  // more pools than the scratch array holds
+    if (count == 0) return FSP_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    int n_max = 1, m_max = 2, mp = 8;
+    for (int32_t i = 0; i < count; ++i) {
+        const fsp_pool_desc &p = pools[i];
+        if (!p.inst || p.N < 0 || (p.N > 0 && (!p.nodes || !p.depths || !p.out_lb))) return FSP_EINVAL;
+        if (p.inst->device != dev || !p.inst->compact) return FSP_EINVAL;
+        n_max = std::max(n_max, p.inst->n);
+        m_max = std::max(m_max, p.inst->m);
+        mp = std::max(mp, p.inst->mpad);
+    }
+    unsigned char *scratch = nullptr;
+    fsp_status st = scratch_address(dev, &scratch);
+    if (st != FSP_OK) return st;
+
+    // The plan is built on the stack (no heap either): pools ordered by the
+    // cost of one work item, longest first, then their item prefix sums.
+    int order[kNoallocMaxPools];
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order, order + count, [&](int x, int y) {
+        const int64_t cx = (int64_t)pools[x].inst->G * pools[x].inst->npad;
+        const int64_t cy = (int64_t)pools[y].inst->G * pools[y].inst->npad;
+        return cx > cy;
+    });
+    const int stride = (m_max + (m_max + 1) / 2) | 1;
+    LanesArgs args[kNoallocMaxPools];
+    int64_t offs[kNoallocMaxPools + 1];
+    std::memset(args, 0, sizeof(LanesArgs) * count);
+    offs[0] = 0;
+    for (int r = 0; r < count; ++r) {
+        const fsp_pool_desc &p = pools[order[r]];
+        const fsp_instance *inst = p.inst;
+        LanesArgs &a = args[r];
+        a.grec = static_cast<const unsigned char *>(inst->t.grec);
+        a.gpairs = inst->t.gpairs;
+        a.hsort = reinterpret_cast<const int2 *>(inst->t.hsort);
+        a.tsort = reinterpret_cast<const int2 *>(inst->t.tsort);
+        a.ptot = inst->t.ptot;
+        a.pp = inst->t.pp;
+        a.nodes = p.nodes;
+        a.depths = p.depths;
+        a.out = p.out_lb;
+        a.status = inst->dev_status;
+        a.N = p.N;
+        a.n = inst->n;
+        a.m = inst->m;
+        a.G = inst->G;
+        a.npad = inst->npad;
+        a.mpad = inst->mpad;
+        a.rec_bytes = (uint32_t)inst->rec_bytes;
+        a.aq_stride = stride;
+        offs[r + 1] = offs[r] + (p.N + 31) / 32;
+    }
+    const int64_t nitems = offs[count];
+    if (nitems > INT32_MAX) return FSP_EINVAL;
+    if (nitems == 0) return FSP_OK;
+
+    // shared memory: flags [warps][n_max] words, rows [warps][32][stride] ints
+    const int optin = max_smem_per_block(dev);
+    int W = 16;
+    uint32_t off_aq = 0;
+    size_t smem = 0;
+    for (; W >= 1; --W) {
+        off_aq = (uint32_t)(((size_t)W * n_max * 4 + 127) / 128 * 128);
+        smem = ((size_t)off_aq + (size_t)W * 32 * stride * 4 + 127) / 128 * 128;
+        if (smem <= (size_t)optin) break;
+    }
+    if (W < 1) return FSP_EINVAL;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nitems + W - 1) / W, num_sms(dev)));
+
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // pageable sources: each copy has consumed its source when it returns
+    if (cudaMemcpyAsync(scratch, args, sizeof(LanesArgs) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(scratch + kArgsBytes, offs, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemsetAsync(scratch + kArgsBytes + kOffsBytes, 0, sizeof(int32_t), s) != cudaSuccess)
+        return FSP_ECUDA;
+    cudaError_t e;
+    switch (mp) {
+        case 8: e = launch_noalloc<8>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
+        case 12: e = launch_noalloc<12>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
+        case 16: e = launch_noalloc<16>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
+        case 20: e = launch_noalloc<20>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
+        case 24: e = launch_noalloc<24>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
+        default: e = launch_noalloc<32>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
+    }
+    return e == cudaSuccess ? FSP_OK : FSP_ECUDA;
+}

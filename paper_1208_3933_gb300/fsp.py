@@ -104,6 +104,7 @@ def load():
             "fsp_batch_launch_graph": ([vp, vp], i32),
             "fsp_batch_query": ([vp, i64p, i64p, i32p, i32p], i32),
             "fsp_batch_destroy": ([vp], None),
+            "fsp_bound_batch_noalloc": ([ctypes.POINTER(fsp_pool_desc), i32, vp], i32),
             "fsp_status_string": ([i32], ctypes.c_char_p),
             "fsp_version": ([], ctypes.c_char_p),
         }
@@ -335,3 +336,16 @@ class Batch:
 
 def fsp_batch_create(pools, warps_per_block: int = 0) -> Batch:
     return Batch(pools, warps_per_block)
+
+
+FSP_NOALLOC_MAX_POOLS = 64
+
+
+def fsp_bound_batch_noalloc(pools, stream=None):
+    """Batched bound with no allocation inside the library (see include/fsp.h):
+    pools are (instance, nodes, depths, out) with torch CUDA tensors."""
+    descs = (fsp_pool_desc * max(1, len(pools)))()
+    for i, (inst, nodes, depths, out) in enumerate(pools):
+        N = _check_pool(inst, nodes, depths, out)
+        descs[i] = fsp_pool_desc(inst.handle.value, nodes.data_ptr(), depths.data_ptr(), out.data_ptr(), N)
+    _check(load().fsp_bound_batch_noalloc(descs, len(pools), _stream_handle(stream)), "fsp_bound_batch_noalloc")
