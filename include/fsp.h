@@ -257,6 +257,100 @@ fsp_status fsp_batch_query(const fsp_batch *batch, int64_t *work_items, int64_t 
 /* Frees the plan; none of its launches may be in flight.  NULL is a no-op. */
 void fsp_batch_destroy(fsp_batch *batch);
 
+/* ---------------------------------------------------------------------
+ * Bounding server: continuous batching of many clients' pools.
+ * --------------------------------------------------------------------- */
+typedef struct fsp_server fsp_server;
+typedef struct fsp_request fsp_request;
+
+typedef struct fsp_server_config {
+    int64_t hbm_budget_bytes;  /* device arena for admitted pools (0 = 1 GiB) */
+    int32_t max_batch_pools;   /* pools gathered into one launch (0 = 256) */
+    int32_t slots;             /* batches in flight at once, 1..8 (0 = 2) */
+    int32_t warps_per_block;   /* batched kernel shape (0 = choose) */
+    int32_t reserved;
+} fsp_server_config;
+
+typedef struct fsp_server_stats {
+    int64_t pools_done, nodes_done, batches;
+    double mean_pools_per_batch;
+    double p50_us, p99_us, mean_us;  /* submission-to-completion latency */
+    double active_seconds;           /* first completed submission to last completion */
+    int64_t queued, in_flight;
+    int64_t arena_bytes, arena_bytes_used;
+} fsp_server_stats;
+
+/*
+ * fsp_server_create -- a bounding server on the current device (the paper's
+ * bounding operator, Section III-A, offered to many concurrent B&B searches
+ * or other clients).  A dispatcher thread admits queued pools in arrival
+ * order while their device footprint (nodes, depths, bounds) fits the
+ * arena, gathers the admitted pools into one batched launch per free slot
+ * (a CUDA stream), copies pools in and bounds out, and keeps admitting while
+ * earlier batches run, so later arrivals overlap them on the device.
+ * Instances stay resident; their tables are not copied per request.
+ * Errors: FSP_EINVAL, FSP_ENOMEM, FSP_ECUDA.
+ */
+fsp_status fsp_server_create(const fsp_server_config *cfg, fsp_server **out);
+
+/* Queues a pool of N nodes of `inst` (host buffers, pinned or pageable:
+ * nodes [N][n], depths [N], out_lb [N]); the buffers must stay valid until
+ * the request completes or is cancelled.  *req receives the request handle.
+ * Errors: FSP_EINVAL; FSP_EBUSY when the server no longer accepts work or the
+ * pool alone exceeds the whole arena (admission refused). */
+fsp_status fsp_server_submit(fsp_server *srv, const fsp_instance *inst, const int16_t *nodes,
+                             const int32_t *depths, int64_t N, int32_t *out_lb, fsp_request **req);
+
+/* Waits up to timeout_us microseconds (negative = no limit) for the request:
+ * FSP_OK when out_lb holds the bounds, FSP_ETIMEDOUT if it is still pending
+ * (the handle stays valid), FSP_EBUSY if it was cancelled, or the error that
+ * failed its batch. */
+fsp_status fsp_request_wait(fsp_request *req, int64_t timeout_us);
+
+/* Removes a request that is still queued (FSP_OK); admitted requests run to
+ * completion (FSP_EBUSY). */
+fsp_status fsp_request_cancel(fsp_request *req);
+
+/* Drops the handle; a request still running is freed when it completes. */
+void fsp_request_release(fsp_request *req);
+
+/* Counters and latency percentiles since creation or the last reset. */
+fsp_status fsp_server_get_stats(fsp_server *srv, fsp_server_stats *stats);
+fsp_status fsp_server_reset_stats(fsp_server *srv);
+
+/* Stops accepting requests (later submissions get FSP_EBUSY); queued and
+ * running requests complete. */
+fsp_status fsp_server_shutdown(fsp_server *srv);
+
+/* Shuts down, waits for every admitted and queued request, frees the server
+ * and every request handle it issued (released or not): no handle may be
+ * used afterwards. */
+void fsp_server_destroy(fsp_server *srv);
+
+/*
+ * fsp_server_search -- a depth-first B&B client of the server (Section II-A
+ * operators, Section II-B branching) that expands the top `expand` nodes of
+ * its stack at once and submits all their children as one pool, so that many
+ * searches keep the server's batches full.  UB starts at ub0 + 1; a child
+ * whose bound reaches UB is dropped; a bounded leaf (depth n) below UB
+ * becomes the incumbent at once.  The optimum equals fsp_branch_and_bound's;
+ * node counts differ (several nodes expanded per step).
+ *   expand  nodes expanded per request (>= 1);
+ *   node_limit  stop after this many bound evaluations (0 = no limit); the
+ *           search then returns FSP_ETIMEDOUT with its best incumbent so far;
+ *   best_perm (host int16 [n] or NULL), best_makespan, nodes_bounded (or NULL).
+ * Synchronous.  Errors: FSP_EINVAL, FSP_ENOMEM, FSP_EBUSY, FSP_EBADNODE,
+ * FSP_ENOTFOUND (no schedule of makespan <= ub0), FSP_ETIMEDOUT.
+ */
+
+/* NEH constructive heuristic (Nawaz, Enscore and Ham 1983; not part of the
+ * paper's method): a complete schedule whose makespan serves as ub0.
+ * perm: host int16 [n] or NULL.  Errors: FSP_EINVAL. */
+fsp_status fsp_neh(const fsp_instance *inst, int16_t *perm, int32_t *makespan);
+fsp_status fsp_server_search(fsp_server *srv, const fsp_instance *inst, int32_t ub0, int32_t expand,
+                             int64_t node_limit, int16_t *best_perm, int32_t *best_makespan,
+                             int64_t *nodes_bounded);
+
 /* Largest number of pools fsp_bound_batch_noalloc accepts in one call. */
 #define FSP_NOALLOC_MAX_POOLS 64
 

@@ -98,15 +98,11 @@ using namespace fspgb;
 
 struct fsp_batch {
     int device = 0;
-    int64_t nitems = 0;
-    int mp = 8, n_max = 1, stride = 1, warps = 16, grid = 1;
-    uint32_t off_aq = 0;
-    size_t smem = 0;
+    fspgb::PlanParams pp;
     void *dev_block = nullptr;  // pools, items and the work counter
     LanesArgs *d_pools = nullptr;
     int2 *d_items = nullptr;
     int32_t *d_counter = nullptr;
-    int64_t nodes = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::mutex mu;
@@ -114,66 +110,31 @@ struct fsp_batch {
 
 namespace {
 
-fsp_status enqueue(fsp_batch *b, cudaStream_t s) {
-    if (b->nitems == 0) return FSP_OK;
-    if (cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), s) != cudaSuccess) return FSP_ECUDA;
-    cudaError_t e;
-    switch (b->mp) {
-        case 8:
-            e = launch_batch_variant<8>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
-                                        b->off_aq, b->grid, 32 * b->warps, b->smem, s);
-            break;
-        case 12:
-            e = launch_batch_variant<12>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
-                                         b->off_aq, b->grid, 32 * b->warps, b->smem, s);
-            break;
-        case 16:
-            e = launch_batch_variant<16>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
-                                         b->off_aq, b->grid, 32 * b->warps, b->smem, s);
-            break;
-        case 20:
-            e = launch_batch_variant<20>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
-                                         b->off_aq, b->grid, 32 * b->warps, b->smem, s);
-            break;
-        case 24:
-            e = launch_batch_variant<24>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
-                                         b->off_aq, b->grid, 32 * b->warps, b->smem, s);
-            break;
-        default:
-            e = launch_batch_variant<32>(b->d_pools, b->d_items, b->nitems, b->d_counter, b->n_max, b->stride,
-                                         b->off_aq, b->grid, 32 * b->warps, b->smem, s);
-            break;
-    }
-    return e == cudaSuccess ? FSP_OK : FSP_ECUDA;
-}
+fsp_status enqueue(fsp_batch *b, cudaStream_t s) { return launch_plan(b->d_pools, b->d_items, b->d_counter, b->pp, s); }
 
 }  // namespace
 
-extern "C" fsp_status fsp_batch_create(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block,
-                                       fsp_batch **out) {
-    if (!out) return FSP_EINVAL;
-    *out = nullptr;
+namespace fspgb {
+
+fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block, int device,
+                      std::vector<LanesArgs> &args, std::vector<int2> &items, PlanParams &pp) {
     if (count < 0 || (count > 0 && !pools) || warps_per_block < 0 || warps_per_block > 16) return FSP_EINVAL;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
     int n_max = 1, m_max = 2, mp = 8;
     for (int32_t i = 0; i < count; ++i) {
         const fsp_pool_desc &p = pools[i];
         if (!p.inst || p.N < 0 || (p.N > 0 && (!p.nodes || !p.depths || !p.out_lb))) return FSP_EINVAL;
-        if (p.inst->device != dev || !p.inst->compact) return FSP_EINVAL;
+        if (p.inst->device != device || !p.inst->compact) return FSP_EINVAL;
         n_max = std::max(n_max, p.inst->n);
         m_max = std::max(m_max, p.inst->m);
         mp = std::max(mp, p.inst->mpad);
     }
-    fsp_batch *b = new (std::nothrow) fsp_batch();
-    if (!b) return FSP_ENOMEM;
-    b->device = dev;
-    b->mp = mp;
-    b->n_max = n_max;
-    b->stride = (m_max + (m_max + 1) / 2) | 1;
+    pp = PlanParams();
+    pp.mp = mp;
+    pp.n_max = n_max;
+    pp.stride = (m_max + (m_max + 1) / 2) | 1;
     // work items, longest first: couple groups x Johnson positions of the instance
-    std::vector<int2> items;
-    std::vector<LanesArgs> args((size_t)count);
+    items.clear();
+    args.assign((size_t)count, LanesArgs());
     for (int32_t i = 0; i < count; ++i) {
         const fsp_pool_desc &p = pools[i];
         const fsp_instance *inst = p.inst;
@@ -196,39 +157,82 @@ extern "C" fsp_status fsp_batch_create(const fsp_pool_desc *pools, int32_t count
         a.npad = inst->npad;
         a.mpad = inst->mpad;
         a.rec_bytes = (uint32_t)inst->rec_bytes;
-        a.aq_stride = b->stride;
+        a.aq_stride = pp.stride;
         a.wait_limit = 4000000000LL;
         const int64_t nb = (p.N + 31) / 32;
         for (int64_t k = 0; k < nb; ++k) items.push_back(make_int2(i, (int)k));
-        b->nodes += p.N;
+        pp.nodes += p.N;
     }
     std::stable_sort(items.begin(), items.end(), [&](const int2 &x, const int2 &y) {
         const int64_t cx = (int64_t)args[x.x].G * args[x.x].npad, cy = (int64_t)args[y.x].G * args[y.x].npad;
         return cx > cy;
     });
-    b->nitems = (int64_t)items.size();
+    pp.nitems = (int64_t)items.size();
+    if (pp.nitems > INT32_MAX) return FSP_EINVAL;
     // shared memory: flags [warps][n_max] words, rows [warps][32][stride] ints
-    const int smem_optin = max_smem_per_block(dev);
+    const int smem_optin = max_smem_per_block(device);
     int W = warps_per_block ? warps_per_block : 16;
     for (; W >= 1; --W) {
         const uint32_t off_aq = (uint32_t)align_up((size_t)W * n_max * 4, 128);
-        const size_t total = align_up(off_aq + (size_t)W * 32 * b->stride * 4, 128);
+        const size_t total = align_up(off_aq + (size_t)W * 32 * pp.stride * 4, 128);
         if (total <= (size_t)smem_optin) {
-            b->off_aq = off_aq;
-            b->smem = total;
+            pp.off_aq = off_aq;
+            pp.smem = total;
             break;
         }
         if (warps_per_block) break;
     }
-    if (!b->smem) {
-        delete b;
-        return FSP_EINVAL;
+    if (!pp.smem) return FSP_EINVAL;
+    pp.warps = W;
+    const int64_t blocks_needed = (pp.nitems + W - 1) / W;
+    pp.grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, num_sms(device)));
+    return FSP_OK;
+}
+
+fsp_status launch_plan(const LanesArgs *d_args, const int2 *d_items, int32_t *d_counter, const PlanParams &pp,
+                       cudaStream_t s) {
+    if (pp.nitems == 0) return FSP_OK;
+    if (cudaMemsetAsync(d_counter, 0, sizeof(int32_t), s) != cudaSuccess) return FSP_ECUDA;
+    cudaError_t e;
+    switch (pp.mp) {
+#define FSP_BATCH_CASE(MPV)                                                                                    \
+    case MPV:                                                                                                   \
+        e = launch_batch_variant<MPV>(d_args, d_items, pp.nitems, d_counter, pp.n_max, pp.stride, pp.off_aq, \
+                                      pp.grid, 32 * pp.warps, pp.smem, s);                                    \
+        break;
+        FSP_BATCH_CASE(8)
+        FSP_BATCH_CASE(12)
+        FSP_BATCH_CASE(16)
+        FSP_BATCH_CASE(20)
+        FSP_BATCH_CASE(24)
+#undef FSP_BATCH_CASE
+        default:
+            e = launch_batch_variant<32>(d_args, d_items, pp.nitems, d_counter, pp.n_max, pp.stride, pp.off_aq,
+                                         pp.grid, 32 * pp.warps, pp.smem, s);
+            break;
     }
-    b->warps = W;
-    const int64_t blocks_needed = (b->nitems + W - 1) / W;
-    b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, num_sms(dev)));
+    return e == cudaSuccess ? FSP_OK : FSP_ECUDA;
+}
+
+}  // namespace fspgb
+
+extern "C" fsp_status fsp_batch_create(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block,
+                                       fsp_batch **out) {
+    if (!out) return FSP_EINVAL;
+    *out = nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FSP_ECUDA;
+    std::vector<LanesArgs> args;
+    std::vector<int2> items;
+    PlanParams pp;
+    fsp_status st = build_plan(pools, count, warps_per_block, dev, args, items, pp);
+    if (st != FSP_OK) return st;
+    fsp_batch *b = new (std::nothrow) fsp_batch();
+    if (!b) return FSP_ENOMEM;
+    b->device = dev;
+    b->pp = pp;
     const size_t off_items = align_up(sizeof(LanesArgs) * std::max(1, count), 256);
-    const size_t off_ctr = align_up(off_items + sizeof(int2) * std::max<int64_t>(1, b->nitems), 256);
+    const size_t off_ctr = align_up(off_items + sizeof(int2) * std::max<int64_t>(1, pp.nitems), 256);
     const size_t bytes = off_ctr + 256;
     unsigned char *blk = nullptr;
     if (cudaMalloc((void **)&blk, bytes) != cudaSuccess) {
@@ -236,8 +240,8 @@ extern "C" fsp_status fsp_batch_create(const fsp_pool_desc *pools, int32_t count
         return FSP_ENOMEM;
     }
     if ((count && cudaMemcpy(blk, args.data(), sizeof(LanesArgs) * count, cudaMemcpyHostToDevice) != cudaSuccess) ||
-        (b->nitems &&
-         cudaMemcpy(blk + off_items, items.data(), sizeof(int2) * b->nitems, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (pp.nitems &&
+         cudaMemcpy(blk + off_items, items.data(), sizeof(int2) * pp.nitems, cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemset(blk + off_ctr, 0, 256) != cudaSuccess) {
         cudaFree(blk);
         delete b;
@@ -297,10 +301,10 @@ extern "C" fsp_status fsp_batch_launch_graph(fsp_batch *b, void *cuda_stream) {
 extern "C" fsp_status fsp_batch_query(const fsp_batch *b, int64_t *work_items, int64_t *nodes,
                                       int32_t *warps_per_block, int32_t *blocks) {
     if (!b) return FSP_EINVAL;
-    if (work_items) *work_items = b->nitems;
-    if (nodes) *nodes = b->nodes;
-    if (warps_per_block) *warps_per_block = b->warps;
-    if (blocks) *blocks = b->grid;
+    if (work_items) *work_items = b->pp.nitems;
+    if (nodes) *nodes = b->pp.nodes;
+    if (warps_per_block) *warps_per_block = b->pp.warps;
+    if (blocks) *blocks = b->pp.grid;
     return FSP_OK;
 }
 

@@ -146,3 +146,68 @@ extern "C" fsp_status fsp_branch_and_bound(const fsp_instance *inst, int32_t ub0
     if (best_perm) std::memcpy(best_perm, best.data(), sizeof(int16_t) * n);
     return FSP_OK;
 }
+
+// NEH constructive heuristic (Nawaz, Enscore and Ham, 1983): jobs by
+// decreasing total processing time, each inserted where the partial makespan
+// is smallest (first such position).  An initial upper bound for the B&B;
+// not part of the paper's method.  O(n^2 m) with the head/tail insertion
+// evaluation (Taillard 1990).
+extern "C" fsp_status fsp_neh(const fsp_instance *inst, int16_t *perm, int32_t *makespan) {
+    if (!inst || !makespan) return FSP_EINVAL;
+    const int n = inst->n, m = inst->m;
+    const int32_t *p = inst->p.data();
+    std::vector<int> order(n);
+    std::vector<int64_t> tot(n, 0);
+    for (int j = 0; j < n; ++j) {
+        order[j] = j;
+        for (int k = 0; k < m; ++k) tot[j] += p[j * m + k];
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tot[a] > tot[b]; });
+    std::vector<int> seq;
+    seq.reserve(n);
+    std::vector<int64_t> e((size_t)(n + 1) * m), q((size_t)(n + 2) * m), f(m);
+    for (int idx = 0; idx < n; ++idx) {
+        const int job = order[idx];
+        const int L = (int)seq.size();
+        // e[i][k]: completion of seq[0..i) on machine k; q[i][k]: tail from seq[i..L) starting at k
+        for (int k = 0; k < m; ++k) e[k] = 0;
+        for (int i = 1; i <= L; ++i)
+            for (int k = 0; k < m; ++k) {
+                const int64_t up = e[(size_t)(i - 1) * m + k], left = k ? e[(size_t)i * m + k - 1] : 0;
+                e[(size_t)i * m + k] = std::max(up, left) + p[seq[i - 1] * m + k];
+            }
+        for (int k = 0; k < m; ++k) q[(size_t)L * m + k] = 0;
+        for (int i = L - 1; i >= 0; --i)
+            for (int k = m - 1; k >= 0; --k) {
+                const int64_t down = q[(size_t)(i + 1) * m + k], right = k + 1 < m ? q[(size_t)i * m + k + 1] : 0;
+                q[(size_t)i * m + k] = std::max(down, right) + p[seq[i] * m + k];
+            }
+        int best_pos = 0;
+        int64_t best = -1;
+        for (int pos = 0; pos <= L; ++pos) {
+            int64_t mk = 0;
+            for (int k = 0; k < m; ++k) {
+                f[k] = std::max(e[(size_t)pos * m + k], k ? f[k - 1] : 0) + p[job * m + k];
+                mk = std::max(mk, f[k] + q[(size_t)pos * m + k]);
+            }
+            if (best < 0 || mk < best) {
+                best = mk;
+                best_pos = pos;
+            }
+        }
+        seq.insert(seq.begin() + best_pos, job);
+    }
+    // makespan of the final sequence
+    std::vector<int64_t> C(m, 0);
+    for (int j : seq) {
+        int64_t prev = 0;
+        for (int k = 0; k < m; ++k) {
+            C[k] = std::max(C[k], prev) + p[j * m + k];
+            prev = C[k];
+        }
+    }
+    *makespan = (int32_t)C[m - 1];
+    if (perm)
+        for (int i = 0; i < n; ++i) perm[i] = (int16_t)seq[i];
+    return FSP_OK;
+}

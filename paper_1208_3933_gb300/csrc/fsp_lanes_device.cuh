@@ -9,33 +9,11 @@
 #include <cstdint>
 
 #include "fsp_internal.h"
+#include "fsp_plan.h"
 
 namespace fspgb {
 
-struct LanesArgs {
-    const unsigned char *grec;
-    const uint8_t *gpairs;
-    const int2 *hsort, *tsort;
-    const int32_t *ptot;
-    const int32_t *pp;    // [n][mpad] processing times, rows padded with zeros
-    const int16_t *nodes;
-    const int32_t *depths;
-    int32_t *out;
-    int32_t *status;
-    int64_t N;
-    int64_t num_batches;  // streamed: block batches of 32 * warps nodes; resident: warp batches of 32
-    int32_t n, m, G, npad;
-    int32_t mpad;         // row stride of pp (<= the kernel's MP)
-    int32_t chunk;        // streamed: Johnson positions per tile (multiple of 4)
-    int32_t nchunks;      // streamed: tiles per couple group
-    int32_t ntiles;       // streamed: G * nchunks
-    uint32_t rec_bytes;
-    uint32_t off_tables;  // records (resident: all groups; streamed: two tile buffers)
-    uint32_t tile_stride;
-    uint32_t off_flags, off_aq;
-    int32_t aq_stride;    // ints per node row (odd): A as int32 [m], then q as int16 [m]
-    long long wait_limit;
-};
+
 
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -215,5 +193,7 @@ __device__ __forceinline__ int transpose_max(int (&lb)[32], int lane) {
     }
     return lb[0];
 }
+
+
 
 }  // namespace fspgb

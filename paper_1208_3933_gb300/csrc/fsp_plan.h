@@ -1,0 +1,57 @@
+// fsp_plan.h -- host-visible argument blocks of the couple-lanes kernels and
+// the batch-plan interface shared by fsp_batch.cu and fsp_server.cpp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "fsp_internal.h"
+
+namespace fspgb {
+
+// Arguments of one pool for the couple-lanes kernels (one per launch for the
+// single-pool kernels, one per pool in a batch plan).
+struct LanesArgs {
+    const unsigned char *grec;
+    const uint8_t *gpairs;
+    const int2 *hsort, *tsort;
+    const int32_t *ptot;
+    const int32_t *pp;    // [n][mpad] processing times, rows padded with zeros
+    const int16_t *nodes;
+    const int32_t *depths;
+    int32_t *out;
+    int32_t *status;
+    int64_t N;
+    int64_t num_batches;  // streamed: block batches of 32 * warps nodes; resident: warp batches of 32
+    int32_t n, m, G, npad;
+    int32_t mpad;         // row stride of pp (<= the kernel's MP)
+    int32_t chunk;        // streamed: Johnson positions per tile (multiple of 4)
+    int32_t nchunks;      // streamed: tiles per couple group
+    int32_t ntiles;       // streamed: G * nchunks
+    uint32_t rec_bytes;
+    uint32_t off_tables;  // records (resident: all groups; streamed: two tile buffers)
+    uint32_t tile_stride;
+    uint32_t off_flags, off_aq;
+    int32_t aq_stride;    // ints per node row (odd): A as int32 [m], then q as int16 [m]
+    long long wait_limit;
+};
+
+// A batch plan's launch parameters.
+struct PlanParams {
+    int64_t nitems = 0, nodes = 0;
+    int mp = 8, n_max = 1, stride = 1, warps = 16, grid = 1;
+    uint32_t off_aq = 0;
+    size_t smem = 0;
+};
+
+// Builds a batch plan on the host: per-pool arguments and the 32-node work
+// items ordered longest first (fsp_batch.cu).
+fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block, int device,
+                      std::vector<LanesArgs> &args, std::vector<int2> &items, PlanParams &pp);
+// Enqueues a plan already copied to the device: counter reset + kernel.
+fsp_status launch_plan(const LanesArgs *d_args, const int2 *d_items, int32_t *d_counter, const PlanParams &pp,
+                       cudaStream_t s);
+
+}  // namespace fspgb

@@ -1,0 +1,654 @@
+// fsp_server.cpp -- a device-resident bounding server with continuous batching.
+//
+// Clients (any number of host threads, e.g. concurrent branch-and-bound
+// searches) submit pools of sub-problems of already-created instances; the
+// instances' tables stay resident on the device.  One dispatcher thread:
+//   - admits queued requests in arrival order while their device footprint
+//     (nodes + depths + bounds) fits in a fixed device arena (the HBM budget);
+//     a request larger than the whole arena is refused at submission;
+//   - gathers the admitted requests into a batch for a free slot (a CUDA
+//     stream with its own plan buffers), copies their pools in, launches the
+//     batched bounding kernel over all of them, copies the bounds out, and
+//     marks the slot's completion with a host callback;
+//   - keeps admitting while earlier batches are in flight, so requests that
+//     arrive meanwhile run as the next batch on another slot and their work
+//     overlaps on the device.
+// Latency is measured from submission to the completion callback; p50/p99
+// are reported by fsp_server_get_stats.  Every wait a client does is bounded
+// by its own timeout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "fsp_internal.h"
+#include "fsp_plan.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// First-fit allocator over the device arena (offsets only), coalescing on free.
+class Arena {
+   public:
+    void reset(size_t size) {
+        free_.clear();
+        if (size) free_[0] = size;
+        used_ = 0;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+
+   private:
+    std::map<size_t, size_t> free_;
+    size_t used_ = 0;
+};
+
+enum ReqState { kQueued = 0, kAdmitted = 1, kDone = 2, kCancelled = 3 };
+
+}  // namespace
+
+struct fsp_request {
+    fsp_server *srv = nullptr;
+    const fsp_instance *inst = nullptr;
+    const int16_t *nodes = nullptr;
+    const int32_t *depths = nullptr;
+    int32_t *out = nullptr;
+    int64_t N = 0;
+    size_t bytes = 0, off = 0;
+    Clock::time_point t_submit;
+    int state = kQueued;          // guarded by the server mutex
+    fsp_status result = FSP_OK;
+    bool released = false;        // the client dropped its handle
+};
+
+namespace {
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    std::vector<fsp_request *> reqs;
+    bool busy = false;
+    bool done = false;  // set by the completion callback
+    // plan buffers: pinned host staging and device copies
+    fspgb::LanesArgs *h_args = nullptr, *d_args = nullptr;
+    int2 *h_items = nullptr, *d_items = nullptr;
+    int32_t *d_counter = nullptr;
+    size_t args_cap = 0, items_cap = 0;
+    fsp_server *srv = nullptr;
+};
+
+}  // namespace
+
+struct fsp_server {
+    fsp_server_config cfg{};
+    int device = 0;
+    unsigned char *arena_mem = nullptr;
+    size_t arena_size = 0;
+    Arena arena;
+    std::mutex mu;
+    std::condition_variable cv_dispatch;  // queue, slot completion, shutdown
+    std::condition_variable cv_client;    // request completion
+    std::deque<fsp_request *> queue;
+    std::vector<fsp_request *> live;      // every request not yet freed
+    std::vector<Slot> slots;
+    std::thread dispatcher;
+    bool accepting = true, stopping = false;
+    fsp_status fatal = FSP_OK;
+    // statistics
+    std::vector<double> lat_us;
+    int64_t pools_done = 0, nodes_done = 0, batches = 0, pools_batched = 0;
+    Clock::time_point t_first, t_last;
+    bool any_done = false;
+};
+
+namespace {
+
+void complete_slot_cb(void *p) {
+    Slot *s = static_cast<Slot *>(p);
+    fsp_server *srv = s->srv;
+    std::lock_guard<std::mutex> g(srv->mu);
+    s->done = true;
+    srv->cv_dispatch.notify_all();
+}
+
+bool grow(Slot &s, size_t nargs, size_t nitems) {
+    if (nargs > s.args_cap) {
+        if (s.h_args) cudaFreeHost(s.h_args);
+        if (s.d_args) cudaFree(s.d_args);
+        s.h_args = nullptr;
+        s.d_args = nullptr;
+        const size_t cap = std::max<size_t>(nargs, 64);
+        if (cudaMallocHost((void **)&s.h_args, sizeof(fspgb::LanesArgs) * cap) != cudaSuccess ||
+            cudaMalloc((void **)&s.d_args, sizeof(fspgb::LanesArgs) * cap) != cudaSuccess) {
+            s.args_cap = 0;
+            return false;
+        }
+        s.args_cap = cap;
+    }
+    if (nitems > s.items_cap) {
+        if (s.h_items) cudaFreeHost(s.h_items);
+        if (s.d_items) cudaFree(s.d_items);
+        s.h_items = nullptr;
+        s.d_items = nullptr;
+        const size_t cap = std::max<size_t>(nitems, 4096);
+        if (cudaMallocHost((void **)&s.h_items, sizeof(int2) * cap) != cudaSuccess ||
+            cudaMalloc((void **)&s.d_items, sizeof(int2) * cap) != cudaSuccess) {
+            s.items_cap = 0;
+            return false;
+        }
+        s.items_cap = cap;
+    }
+    return true;
+}
+
+// Enqueues one batch on slot s (dispatcher thread, server mutex NOT held).
+fsp_status launch_batch(fsp_server *srv, Slot &s) {
+    cudaStream_t st = s.stream;
+    std::vector<fsp_pool_desc> pools;
+    std::vector<fsp_request *> wide;
+    for (fsp_request *r : s.reqs) {
+        unsigned char *base = srv->arena_mem + r->off;
+        const int n = r->inst->n;
+        int16_t *d_nodes = reinterpret_cast<int16_t *>(base);
+        int32_t *d_dep = reinterpret_cast<int32_t *>(base + align_up(sizeof(int16_t) * r->N * n, 256));
+        int32_t *d_out =
+            reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(d_dep) + align_up(sizeof(int32_t) * r->N, 256));
+        if (r->N > 0 &&
+            (cudaMemcpyAsync(d_nodes, r->nodes, sizeof(int16_t) * r->N * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+             cudaMemcpyAsync(d_dep, r->depths, sizeof(int32_t) * r->N, cudaMemcpyHostToDevice, st) != cudaSuccess))
+            return FSP_ECUDA;
+        fsp_pool_desc d{r->inst, d_nodes, d_dep, d_out, r->N};
+        if (r->inst->compact)
+            pools.push_back(d);
+        else
+            wide.push_back(r);
+    }
+    std::vector<fspgb::LanesArgs> args;
+    std::vector<int2> items;
+    fspgb::PlanParams pp;
+    fsp_status rc = fspgb::build_plan(pools.data(), (int32_t)pools.size(), srv->cfg.warps_per_block, srv->device,
+                                      args, items, pp);
+    if (rc != FSP_OK) return rc;
+    if (!grow(s, args.size(), items.size())) return FSP_ENOMEM;
+    if (!args.empty()) std::memcpy(s.h_args, args.data(), sizeof(fspgb::LanesArgs) * args.size());
+    if (!items.empty()) std::memcpy(s.h_items, items.data(), sizeof(int2) * items.size());
+    if ((!args.empty() && cudaMemcpyAsync(s.d_args, s.h_args, sizeof(fspgb::LanesArgs) * args.size(),
+                                          cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+        (!items.empty() &&
+         cudaMemcpyAsync(s.d_items, s.h_items, sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st) != cudaSuccess))
+        return FSP_ECUDA;
+    rc = fspgb::launch_plan(s.d_args, s.d_items, s.d_counter, pp, st);
+    if (rc != FSP_OK) return rc;
+    // instances with 128-bit records: one plain launch each
+    for (fsp_request *r : wide) {
+        unsigned char *base = srv->arena_mem + r->off;
+        const int n = r->inst->n;
+        const int16_t *d_nodes = reinterpret_cast<const int16_t *>(base);
+        const int32_t *d_dep = reinterpret_cast<const int32_t *>(base + align_up(sizeof(int16_t) * r->N * n, 256));
+        int32_t *d_out = const_cast<int32_t *>(d_dep) + align_up(sizeof(int32_t) * r->N, 256) / sizeof(int32_t);
+        if (r->N > 0) {
+            rc = fspgb::launch_bound(r->inst, d_nodes, d_dep, r->N, d_out, st, nullptr);
+            if (rc != FSP_OK) return rc;
+        }
+    }
+    for (fsp_request *r : s.reqs) {
+        if (r->N == 0) continue;
+        const unsigned char *base = srv->arena_mem + r->off;
+        const int32_t *d_out = reinterpret_cast<const int32_t *>(
+            base + align_up(sizeof(int16_t) * r->N * r->inst->n, 256) + align_up(sizeof(int32_t) * r->N, 256));
+        if (cudaMemcpyAsync(r->out, d_out, sizeof(int32_t) * r->N, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return FSP_ECUDA;
+    }
+    if (cudaLaunchHostFunc(st, complete_slot_cb, &s) != cudaSuccess) return FSP_ECUDA;
+    return FSP_OK;
+}
+
+void free_request(fsp_server *srv, fsp_request *r) {
+    // server mutex held
+    auto it = std::find(srv->live.begin(), srv->live.end(), r);
+    if (it != srv->live.end()) {
+        *it = srv->live.back();
+        srv->live.pop_back();
+    }
+    delete r;
+}
+
+void finish_request(fsp_server *srv, fsp_request *r, fsp_status result, Clock::time_point now) {
+    // server mutex held
+    if (r->state == kAdmitted) srv->arena.release(r->off, r->bytes);
+    r->state = kDone;
+    r->result = result;
+    if (result == FSP_OK) {
+        srv->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r->t_submit).count());
+        srv->pools_done += 1;
+        srv->nodes_done += r->N;
+        if (!srv->any_done) srv->t_first = r->t_submit;
+        srv->any_done = true;
+        srv->t_last = now;
+    }
+    if (r->released) free_request(srv, r);
+}
+
+void dispatcher_main(fsp_server *srv) {
+    cudaSetDevice(srv->device);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    for (;;) {
+        // retire completed slots
+        const auto now = Clock::now();
+        bool retired = false;
+        for (Slot &s : srv->slots) {
+            if (s.busy && s.done) {
+                fsp_status st = FSP_OK;
+                for (fsp_request *r : s.reqs) {
+                    const fsp_status t = fspgb::take_device_status(r->inst);
+                    if (t != FSP_OK) st = t;
+                }
+                for (fsp_request *r : s.reqs) finish_request(srv, r, st, now);
+                s.reqs.clear();
+                s.busy = false;
+                s.done = false;
+                retired = true;
+            }
+        }
+        if (retired) srv->cv_client.notify_all();
+        bool in_flight = false;
+        for (Slot &s : srv->slots) in_flight |= s.busy;
+        if (srv->stopping && srv->queue.empty() && !in_flight) break;
+        // admit into a free slot
+        Slot *free_slot = nullptr;
+        for (Slot &s : srv->slots)
+            if (!s.busy) {
+                free_slot = &s;
+                break;
+            }
+        if (free_slot && !srv->queue.empty() && srv->fatal == FSP_OK) {
+            std::vector<fsp_request *> take;
+            while (!srv->queue.empty() && (int)take.size() < srv->cfg.max_batch_pools) {
+                fsp_request *r = srv->queue.front();
+                size_t off = 0;
+                if (!srv->arena.alloc(r->bytes, &off)) break;  // in order: wait for memory
+                r->off = off;
+                r->state = kAdmitted;
+                srv->queue.pop_front();
+                take.push_back(r);
+            }
+            if (!take.empty()) {
+                free_slot->reqs = take;
+                free_slot->busy = true;
+                free_slot->done = false;
+                lk.unlock();
+                const fsp_status st = launch_batch(srv, *free_slot);
+                lk.lock();
+                srv->batches += 1;
+                srv->pools_batched += (int64_t)take.size();
+                if (st != FSP_OK) {
+                    // nothing of this batch can be trusted; fail its requests
+                    lk.unlock();
+                    cudaStreamSynchronize(free_slot->stream);
+                    lk.lock();
+                    for (fsp_request *r : free_slot->reqs) finish_request(srv, r, st, Clock::now());
+                    free_slot->reqs.clear();
+                    free_slot->busy = false;
+                    srv->fatal = st;
+                    srv->cv_client.notify_all();
+                }
+                continue;
+            }
+        }
+        srv->cv_dispatch.wait(lk);
+    }
+}
+
+}  // namespace
+
+extern "C" fsp_status fsp_server_create(const fsp_server_config *cfg, fsp_server **out) {
+    if (!out) return FSP_EINVAL;
+    *out = nullptr;
+    fsp_server_config c = {};
+    if (cfg) c = *cfg;
+    if (c.hbm_budget_bytes < 0 || c.max_batch_pools < 0 || c.slots < 0 || c.slots > 8 || c.warps_per_block < 0 ||
+        c.warps_per_block > 16)
+        return FSP_EINVAL;
+    if (!c.hbm_budget_bytes) c.hbm_budget_bytes = (int64_t)1 << 30;
+    if (!c.max_batch_pools) c.max_batch_pools = 256;
+    if (!c.slots) c.slots = 2;
+    fsp_server *srv = new (std::nothrow) fsp_server();
+    if (!srv) return FSP_ENOMEM;
+    srv->cfg = c;
+    if (cudaGetDevice(&srv->device) != cudaSuccess) {
+        delete srv;
+        return FSP_ECUDA;
+    }
+    srv->arena_size = (size_t)c.hbm_budget_bytes;
+    if (cudaMalloc((void **)&srv->arena_mem, srv->arena_size) != cudaSuccess) {
+        delete srv;
+        return FSP_ENOMEM;
+    }
+    srv->arena.reset(srv->arena_size);
+    srv->slots.resize((size_t)c.slots);
+    for (Slot &s : srv->slots) {
+        s.srv = srv;
+        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMalloc((void **)&s.d_counter, 256) != cudaSuccess) {
+            for (Slot &t : srv->slots) {
+                if (t.stream) cudaStreamDestroy(t.stream);
+                if (t.d_counter) cudaFree(t.d_counter);
+            }
+            cudaFree(srv->arena_mem);
+            delete srv;
+            return FSP_ECUDA;
+        }
+    }
+    srv->dispatcher = std::thread(dispatcher_main, srv);
+    *out = srv;
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_server_submit(fsp_server *srv, const fsp_instance *inst, const int16_t *nodes,
+                                        const int32_t *depths, int64_t N, int32_t *out_lb, fsp_request **req) {
+    if (!req) return FSP_EINVAL;
+    *req = nullptr;
+    if (!srv || !inst || N < 0 || (N > 0 && (!nodes || !depths || !out_lb))) return FSP_EINVAL;
+    if (inst->device != srv->device) return FSP_EINVAL;
+    const size_t bytes = align_up(sizeof(int16_t) * N * inst->n, 256) + 2 * align_up(sizeof(int32_t) * N, 256) + 256;
+    if (bytes > srv->arena_size) return FSP_EBUSY;  // can never be admitted
+    fsp_request *r = new (std::nothrow) fsp_request();
+    if (!r) return FSP_ENOMEM;
+    r->srv = srv;
+    r->inst = inst;
+    r->nodes = nodes;
+    r->depths = depths;
+    r->out = out_lb;
+    r->N = N;
+    r->bytes = bytes;
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        if (!srv->accepting) {
+            delete r;
+            return FSP_EBUSY;
+        }
+        if (srv->fatal != FSP_OK) {
+            delete r;
+            return srv->fatal;
+        }
+        srv->queue.push_back(r);
+        srv->live.push_back(r);
+    }
+    srv->cv_dispatch.notify_all();
+    *req = r;
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_request_wait(fsp_request *r, int64_t timeout_us) {
+    if (!r) return FSP_EINVAL;
+    fsp_server *srv = r->srv;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto ready = [&] { return r->state == kDone || r->state == kCancelled; };
+    if (timeout_us < 0) {
+        srv->cv_client.wait(lk, ready);
+    } else if (!srv->cv_client.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+        return FSP_ETIMEDOUT;
+    }
+    return r->state == kCancelled ? FSP_EBUSY : r->result;
+}
+
+extern "C" fsp_status fsp_request_cancel(fsp_request *r) {
+    if (!r) return FSP_EINVAL;
+    fsp_server *srv = r->srv;
+    std::lock_guard<std::mutex> g(srv->mu);
+    if (r->state != kQueued) return FSP_EBUSY;  // admitted work runs to completion
+    auto it = std::find(srv->queue.begin(), srv->queue.end(), r);
+    if (it != srv->queue.end()) srv->queue.erase(it);
+    r->state = kCancelled;
+    srv->cv_client.notify_all();
+    return FSP_OK;
+}
+
+extern "C" void fsp_request_release(fsp_request *r) {
+    if (!r) return;
+    fsp_server *srv = r->srv;
+    std::lock_guard<std::mutex> g(srv->mu);
+    if (r->state == kDone || r->state == kCancelled)
+        free_request(srv, r);
+    else
+        r->released = true;  // freed by the dispatcher when it completes
+}
+
+extern "C" fsp_status fsp_server_get_stats(fsp_server *srv, fsp_server_stats *st) {
+    if (!srv || !st) return FSP_EINVAL;
+    std::lock_guard<std::mutex> g(srv->mu);
+    std::memset(st, 0, sizeof *st);
+    st->pools_done = srv->pools_done;
+    st->nodes_done = srv->nodes_done;
+    st->batches = srv->batches;
+    st->mean_pools_per_batch = srv->batches ? (double)srv->pools_batched / srv->batches : 0.0;
+    st->queued = (int64_t)srv->queue.size();
+    for (const Slot &s : srv->slots) st->in_flight += s.busy ? (int64_t)s.reqs.size() : 0;
+    st->arena_bytes = (int64_t)srv->arena_size;
+    st->arena_bytes_used = (int64_t)srv->arena.used();
+    if (!srv->lat_us.empty()) {
+        std::vector<double> v = srv->lat_us;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) {
+            const size_t i = std::min(v.size() - 1, (size_t)std::ceil(q * v.size()) - (q * v.size() >= 1 ? 1 : 0));
+            return v[i];
+        };
+        st->p50_us = pct(0.50);
+        st->p99_us = pct(0.99);
+        double sum = 0;
+        for (double x : v) sum += x;
+        st->mean_us = sum / v.size();
+    }
+    if (srv->any_done) st->active_seconds = std::chrono::duration<double>(srv->t_last - srv->t_first).count();
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_server_reset_stats(fsp_server *srv) {
+    if (!srv) return FSP_EINVAL;
+    std::lock_guard<std::mutex> g(srv->mu);
+    srv->lat_us.clear();
+    srv->pools_done = srv->nodes_done = srv->batches = srv->pools_batched = 0;
+    srv->any_done = false;
+    return FSP_OK;
+}
+
+extern "C" fsp_status fsp_server_shutdown(fsp_server *srv) {
+    if (!srv) return FSP_EINVAL;
+    std::lock_guard<std::mutex> g(srv->mu);
+    srv->accepting = false;
+    return FSP_OK;
+}
+
+extern "C" void fsp_server_destroy(fsp_server *srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->accepting = false;
+        srv->stopping = true;
+    }
+    srv->cv_dispatch.notify_all();
+    if (srv->dispatcher.joinable()) srv->dispatcher.join();
+    for (Slot &s : srv->slots) {
+        if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.d_counter) cudaFree(s.d_counter);
+        if (s.h_args) cudaFreeHost(s.h_args);
+        if (s.d_args) cudaFree(s.d_args);
+        if (s.h_items) cudaFreeHost(s.h_items);
+        if (s.d_items) cudaFree(s.d_items);
+    }
+    if (srv->arena_mem) cudaFree(srv->arena_mem);
+    for (fsp_request *r : srv->live) delete r;  // every handle dies with the server
+    delete srv;
+}
+
+// ---------------------------------------------------------------- a client
+namespace {
+
+struct SNode {
+    int32_t lb;
+    int32_t d;
+    std::vector<int16_t> row;  // prefix in row[0..d)
+};
+
+}  // namespace
+
+extern "C" fsp_status fsp_server_search(fsp_server *srv, const fsp_instance *inst, int32_t ub0, int32_t expand,
+                                        int64_t node_limit, int16_t *best_perm, int32_t *best_makespan,
+                                        int64_t *nodes_bounded) {
+    if (!srv || !inst || expand < 1 || node_limit < 0) return FSP_EINVAL;
+    const int n = inst->n;
+    const size_t cap = (size_t)expand * n;  // children of `expand` parents
+    int16_t *h_rows = nullptr;
+    int32_t *h_dep = nullptr, *h_out = nullptr;
+    if (cudaMallocHost((void **)&h_rows, sizeof(int16_t) * cap * n) != cudaSuccess ||
+        cudaMallocHost((void **)&h_dep, sizeof(int32_t) * cap) != cudaSuccess ||
+        cudaMallocHost((void **)&h_out, sizeof(int32_t) * cap) != cudaSuccess) {
+        if (h_rows) cudaFreeHost(h_rows);
+        if (h_dep) cudaFreeHost(h_dep);
+        return FSP_ENOMEM;
+    }
+    auto bound = [&](int64_t cnt) -> fsp_status {
+        fsp_request *req = nullptr;
+        fsp_status st = fsp_server_submit(srv, inst, h_rows, h_dep, cnt, h_out, &req);
+        if (st != FSP_OK) return st;
+        st = fsp_request_wait(req, 600000000LL);  // ten minutes: a stuck server ends the search
+        if (st == FSP_ETIMEDOUT) fsp_request_cancel(req);
+        fsp_request_release(req);
+        if (st != FSP_OK) return st;
+        for (int64_t i = 0; i < cnt; ++i)
+            if (h_out[i] == FSP_LB_INVALID) return FSP_EBADNODE;
+        return FSP_OK;
+    };
+    int64_t UB = (int64_t)ub0 + 1, count = 0;
+    bool found = false;
+    std::vector<int16_t> best(n, 0);
+    std::vector<SNode> stack;
+    fsp_status st;
+    // the root
+    std::memset(h_rows, 0, sizeof(int16_t) * n);
+    h_dep[0] = 0;
+    st = bound(1);
+    if (st == FSP_OK) {
+        ++count;
+        if (h_out[0] < UB) stack.push_back(SNode{h_out[0], 0, std::vector<int16_t>(n, 0)});
+    }
+    std::vector<SNode> parents;
+    std::vector<int> first(expand + 1);
+    std::vector<char> used(n);
+    struct Kid {
+        int32_t lb, job;
+    };
+    std::vector<Kid> kids;
+    bool cut = false;
+    while (st == FSP_OK && !stack.empty()) {
+        if (node_limit && count >= node_limit) {
+            cut = true;
+            break;
+        }
+        // selection: the top `expand` live nodes of the stack
+        parents.clear();
+        while (!stack.empty() && (int)parents.size() < expand) {
+            SNode nd = std::move(stack.back());
+            stack.pop_back();
+            if (nd.lb < UB) parents.push_back(std::move(nd));
+        }
+        if (parents.empty()) break;
+        // branching: all children of all selected parents form one pool
+        int64_t cnt = 0;
+        for (size_t p = 0; p < parents.size(); ++p) {
+            first[p] = (int)cnt;
+            const SNode &nd = parents[p];
+            std::fill(used.begin(), used.end(), 0);
+            for (int i = 0; i < nd.d; ++i) used[nd.row[i]] = 1;
+            for (int j = 0; j < n; ++j) {
+                if (used[j]) continue;
+                int16_t *r = h_rows + (size_t)cnt * n;
+                std::memcpy(r, nd.row.data(), sizeof(int16_t) * nd.d);
+                std::memset(r + nd.d, 0, sizeof(int16_t) * (n - nd.d));
+                r[nd.d] = (int16_t)j;
+                h_dep[cnt] = nd.d + 1;
+                ++cnt;
+            }
+        }
+        first[parents.size()] = (int)cnt;
+        st = bound(cnt);
+        if (st != FSP_OK) break;
+        count += cnt;
+        // leaves first: a bounded complete schedule is an incumbent at once
+        for (int64_t i = 0; i < cnt; ++i)
+            if (h_dep[i] == n && h_out[i] < UB) {
+                UB = h_out[i];
+                found = true;
+                std::memcpy(best.data(), h_rows + (size_t)i * n, sizeof(int16_t) * n);
+            }
+        // elimination and depth-first order: the first selected parent's
+        // children end on top, each parent's children by (LB, job)
+        for (int p = (int)parents.size() - 1; p >= 0; --p) {
+            const SNode &nd = parents[p];
+            if (nd.d + 1 == n) continue;
+            kids.clear();
+            for (int i = first[p]; i < first[p + 1]; ++i)
+                if (h_out[i] < UB) kids.push_back(Kid{h_out[i], h_rows[(size_t)i * n + nd.d]});
+            std::sort(kids.begin(), kids.end(),
+                      [](const Kid &x, const Kid &y) { return x.lb != y.lb ? x.lb < y.lb : x.job < y.job; });
+            for (int t = (int)kids.size() - 1; t >= 0; --t) {
+                SNode c{kids[t].lb, nd.d + 1, nd.row};
+                c.row[nd.d] = (int16_t)kids[t].job;
+                stack.push_back(std::move(c));
+            }
+        }
+    }
+    cudaFreeHost(h_rows);
+    cudaFreeHost(h_dep);
+    cudaFreeHost(h_out);
+    if (st != FSP_OK) return st;
+    if (nodes_bounded) *nodes_bounded = count;
+    if (found) {
+        if (best_makespan) *best_makespan = (int32_t)UB;
+        if (best_perm) std::memcpy(best_perm, best.data(), sizeof(int16_t) * n);
+    }
+    if (cut) return FSP_ETIMEDOUT;
+    return found ? FSP_OK : FSP_ENOTFOUND;
+}

@@ -67,6 +67,21 @@ class fsp_pool_desc(ctypes.Structure):
                 ("out_lb", ctypes.c_void_p), ("N", ctypes.c_int64)]
 
 
+class fsp_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_batch_pools", ctypes.c_int32),
+                ("slots", ctypes.c_int32), ("warps_per_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class fsp_server_stats(ctypes.Structure):
+    _fields_ = [("pools_done", ctypes.c_int64), ("nodes_done", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("mean_pools_per_batch", ctypes.c_double), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("mean_us", ctypes.c_double), ("active_seconds", ctypes.c_double), ("queued", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("arena_bytes", ctypes.c_int64), ("arena_bytes_used", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 def launch_config(**fields) -> fsp_launch_config:
     """fsp_launch_config from keyword fields (missing ones are 0 = choose)."""
     cfg = fsp_launch_config()
@@ -105,6 +120,17 @@ def load():
             "fsp_batch_query": ([vp, i64p, i64p, i32p, i32p], i32),
             "fsp_batch_destroy": ([vp], None),
             "fsp_bound_batch_noalloc": ([ctypes.POINTER(fsp_pool_desc), i32, vp], i32),
+            "fsp_server_create": ([ctypes.POINTER(fsp_server_config), ctypes.POINTER(vp)], i32),
+            "fsp_server_submit": ([vp, vp, vp, vp, i64, vp, ctypes.POINTER(vp)], i32),
+            "fsp_request_wait": ([vp, i64], i32),
+            "fsp_request_cancel": ([vp], i32),
+            "fsp_request_release": ([vp], None),
+            "fsp_server_get_stats": ([vp, ctypes.POINTER(fsp_server_stats)], i32),
+            "fsp_server_reset_stats": ([vp], i32),
+            "fsp_server_shutdown": ([vp], i32),
+            "fsp_server_destroy": ([vp], None),
+            "fsp_server_search": ([vp, vp, i32, i32, i64, i16p, i32p, i64p], i32),
+            "fsp_neh": ([vp, i16p, i32p], i32),
             "fsp_status_string": ([i32], ctypes.c_char_p),
             "fsp_version": ([], ctypes.c_char_p),
         }
@@ -349,3 +375,117 @@ def fsp_bound_batch_noalloc(pools, stream=None):
         N = _check_pool(inst, nodes, depths, out)
         descs[i] = fsp_pool_desc(inst.handle.value, nodes.data_ptr(), depths.data_ptr(), out.data_ptr(), N)
     _check(load().fsp_bound_batch_noalloc(descs, len(pools), _stream_handle(stream)), "fsp_bound_batch_noalloc")
+
+
+class Request:
+    """A pending fsp_server request; keeps its host buffers alive.  The
+    handle dies with its server (fsp_server_destroy frees it)."""
+
+    def __init__(self, handle, keep, server):
+        self._h = handle
+        self._keep = keep
+        self._server = server
+
+    @property
+    def out(self):
+        return self._keep[2]
+
+    def _handle(self):
+        if self._h is None or self._server._h is None:
+            raise RuntimeError("request handle is released or its server is destroyed")
+        return self._h
+
+    def wait(self, timeout_us: int = -1) -> int:
+        """fsp_request_wait: returns the status (FSP_OK, FSP_ETIMEDOUT, ...)."""
+        return load().fsp_request_wait(self._handle(), int(timeout_us))
+
+    def cancel(self) -> int:
+        return load().fsp_request_cancel(self._handle())
+
+    def release(self):
+        if self._h is not None and self._h.value and self._server._h is not None:
+            load().fsp_request_release(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owns an fsp_server (continuous-batching bounding server)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_batch_pools: int = 0, slots: int = 0,
+                 warps_per_block: int = 0):
+        cfg = fsp_server_config(int(hbm_budget_bytes), int(max_batch_pools), int(slots), int(warps_per_block), 0)
+        h = ctypes.c_void_p()
+        _check(load().fsp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fsp_server_create")
+        self._h = h
+
+    def submit(self, inst: Instance, nodes, depths, out=None) -> Request:
+        """Queues a host pool (numpy arrays, ideally in pinned memory)."""
+        nodes = np.ascontiguousarray(nodes, dtype=np.int16)
+        depths = np.ascontiguousarray(depths, dtype=np.int32)
+        N = int(depths.shape[0])
+        if nodes.shape != (N, inst.n):
+            raise ValueError("nodes must be [N][n]")
+        if out is None:
+            out = np.empty(N, np.int32)
+        req = ctypes.c_void_p()
+        st = load().fsp_server_submit(self._h, inst.handle, ctypes.c_void_p(nodes.ctypes.data),
+                                      ctypes.c_void_p(depths.ctypes.data), N, ctypes.c_void_p(out.ctypes.data),
+                                      ctypes.byref(req))
+        _check(st, "fsp_server_submit")
+        return Request(req, (nodes, depths, out), self)
+
+    def stats(self) -> dict:
+        st = fsp_server_stats()
+        _check(load().fsp_server_get_stats(self._h, ctypes.byref(st)), "fsp_server_get_stats")
+        return st.as_dict()
+
+    def reset_stats(self):
+        _check(load().fsp_server_reset_stats(self._h), "fsp_server_reset_stats")
+
+    def shutdown(self):
+        _check(load().fsp_server_shutdown(self._h), "fsp_server_shutdown")
+
+    def search(self, inst: Instance, ub0: int, expand: int = 64, node_limit: int = 0):
+        """fsp_server_search: (status, best_makespan, best_perm, nodes_bounded);
+        status FSP_OK, FSP_ENOTFOUND, or FSP_ETIMEDOUT when node_limit cut it."""
+        perm = np.zeros(inst.n, np.int16)
+        best = ctypes.c_int32(0)
+        nodes = ctypes.c_int64(0)
+        st = load().fsp_server_search(self._h, inst.handle, int(ub0), int(expand), int(node_limit),
+                                      perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), ctypes.byref(best),
+                                      ctypes.byref(nodes))
+        if st not in (FSP_OK, FSP_ENOTFOUND, FSP_ETIMEDOUT):
+            raise FspError(st, "fsp_server_search")
+        return st, int(best.value), perm, int(nodes.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().fsp_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fsp_neh(inst: Instance):
+    """NEH heuristic schedule: (makespan, perm)."""
+    perm = np.zeros(inst.n, np.int16)
+    mk = ctypes.c_int32(0)
+    _check(load().fsp_neh(inst.handle, perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), ctypes.byref(mk)),
+           "fsp_neh")
+    return int(mk.value), perm

@@ -272,3 +272,14 @@ def test_pins_detect_planted_mistakes(name, tmp_path):
             caught = True
             break
     assert caught, f"mutant '{name}' survived the enumeration pin"
+
+
+def test_neh_gives_a_valid_schedule_at_least_the_optimum():
+    from oracle.neh import neh
+    rng = np.random.default_rng(12)
+    for _ in range(10):
+        n = int(rng.integers(1, 8)); m = int(rng.integers(2, 5))
+        p = rand_instance(rng, n, m)
+        v, seq = neh(p)
+        assert sorted(seq) == list(range(n))
+        assert v == brute.makespan(p, seq) >= brute.optimum(p)[0]

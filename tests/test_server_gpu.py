@@ -1,0 +1,156 @@
+"""The continuous-batching bounding server: every request's bounds equal the
+same pool bounded alone (bit-exact), under concurrency, admission by device
+budget, cancellation, shutdown; and served DFS searches reach the oracle's
+optimum."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.neh import neh
+from paper_1208_3933_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def make_pools(fsp, specs, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for n, m, N in specs:
+        p = rng.integers(1, 100, (n, m), dtype=np.int32)
+        rows, depths = workloads.random_pool(rng, n, N, max_depth=n + 1)
+        out.append((fsp.Instance(p), rows, depths))
+    return out
+
+
+def alone(fsp, inst, rows, depths):
+    import torch
+    r = torch.from_numpy(rows).cuda()
+    d = torch.from_numpy(depths).cuda()
+    o = fsp.fsp_bound_pool(inst, r, d)
+    torch.cuda.synchronize()
+    return o.cpu().numpy()
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix(gpu_lib):
+    fsp = gpu_lib
+    specs = [(20, 5, 700), (50, 10, 3000), (200, 20, 2500), (20, 20, 33), (100, 12, 1500), (7, 3, 1)]
+    pools = make_pools(fsp, specs, 1)
+    ref = [alone(fsp, *p) for p in pools]
+    with fsp.Server(hbm_budget_bytes=64 << 20, slots=3) as srv:
+        errors = []
+
+        def client(cid):
+            rng = np.random.default_rng(100 + cid)
+            for _ in range(12):
+                k = int(rng.integers(0, len(pools)))
+                inst, rows, depths = pools[k]
+                req = srv.submit(inst, rows, depths)
+                st = req.wait(60_000_000)
+                if st != fsp.FSP_OK or not np.array_equal(req.out, ref[k]):
+                    errors.append((cid, k, st))
+                req.release()
+
+        threads = [threading.Thread(target=client, args=(c,)) for c in range(8)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join(120)
+        assert not errors, errors[:5]
+        st = srv.stats()
+        assert st["pools_done"] == 8 * 12
+        assert st["batches"] <= st["pools_done"]
+        assert st["p99_us"] >= st["p50_us"] > 0
+    for inst, _, _ in pools:
+        inst.close()
+
+
+def test_admission_by_budget(gpu_lib):
+    """A pool larger than the whole arena is refused at once; pools that fit
+    only one at a time are admitted in turn and all complete exactly."""
+    fsp = gpu_lib
+    (inst, rows, depths), = make_pools(fsp, [(200, 20, 6000)], 2)
+    per_pool = 6000 * 200 * 2 + 2 * 6000 * 4
+    with fsp.Server(hbm_budget_bytes=per_pool // 2) as small:
+        with pytest.raises(fsp.FspError) as e:
+            small.submit(inst, rows, depths)
+        assert e.value.status == fsp.FSP_EBUSY
+    want = alone(fsp, inst, rows, depths)
+    with fsp.Server(hbm_budget_bytes=int(per_pool * 1.5)) as one_at_a_time:
+        reqs = [one_at_a_time.submit(inst, rows, depths) for _ in range(4)]
+        for r in reqs:
+            assert r.wait(60_000_000) == fsp.FSP_OK
+            assert np.array_equal(r.out, want)
+        assert one_at_a_time.stats()["batches"] == 4
+    inst.close()
+
+
+def test_cancel_timeout_and_shutdown(gpu_lib):
+    fsp = gpu_lib
+    (inst, rows, depths), = make_pools(fsp, [(200, 20, 40000)], 3)
+    per_pool = 40000 * 200 * 2 + 2 * 40000 * 4
+    want = alone(fsp, inst, rows, depths)
+    with fsp.Server(hbm_budget_bytes=int(per_pool * 1.2)) as srv:
+        a = srv.submit(inst, rows, depths)
+        b = srv.submit(inst, rows, depths)  # waits for a's memory
+        c = b.cancel()
+        if c == fsp.FSP_OK:
+            assert b.wait(0) == fsp.FSP_EBUSY
+        else:  # b was admitted already and runs to completion
+            assert c == fsp.FSP_EBUSY and b.wait(60_000_000) == fsp.FSP_OK and np.array_equal(b.out, want)
+        assert a.wait(60_000_000) == fsp.FSP_OK and np.array_equal(a.out, want)
+        srv.shutdown()
+        with pytest.raises(fsp.FspError) as e:
+            srv.submit(inst, rows, depths)
+        assert e.value.status == fsp.FSP_EBUSY
+    with fsp.Server() as srv:
+        big = srv.submit(inst, rows, depths)
+        st = big.wait(0)
+        assert st in (fsp.FSP_ETIMEDOUT, fsp.FSP_OK)
+        assert big.wait(60_000_000) == fsp.FSP_OK and np.array_equal(big.out, want)
+    inst.close()
+
+
+@pytest.mark.parametrize("seed", [200, 203, 205, 206, 211, 213])
+def test_served_search_reaches_the_oracle_optimum(gpu_lib, seed):
+    """20-job searches of the serving loop (m=5), with the oracle's optimum
+    as ub0 so both sides explore small trees."""
+    fsp = gpu_lib
+    p = dict(workloads.serving_searches())[seed]
+    ost, opt, _, _ = oracle.branch_and_bound(p, neh(p)[0])
+    assert ost == oracle.FO_OK
+    from oracle import brute
+    with fsp.Instance(p) as inst, fsp.Server() as srv:
+        for expand in (1, 16, 256):
+            st, best, perm, nodes = srv.search(inst, opt, expand=expand)
+            assert st == fsp.FSP_OK and best == opt, (expand, best, opt)
+            assert brute.makespan(p, perm.tolist()) == opt
+            assert sorted(perm.tolist()) == list(range(20))
+        st, _, _, _ = srv.search(inst, opt - 1, expand=64)
+        assert st == fsp.FSP_ENOTFOUND
+
+
+def test_concurrent_served_searches(gpu_lib):
+    """Eight searches at once share one server; every optimum is right."""
+    fsp = gpu_lib
+    seeds = [200, 203, 205, 206, 211, 213, 201, 208]
+    probs = dict(workloads.serving_searches())
+    opts = {s: oracle.branch_and_bound(probs[s], neh(probs[s])[0])[1] for s in seeds}
+    insts = {s: fsp.Instance(probs[s]) for s in seeds}
+    results = {}
+    with fsp.Server(slots=2) as srv:
+        def run(s):
+            results[s] = srv.search(insts[s], opts[s], expand=32)
+
+        threads = [threading.Thread(target=run, args=(s,)) for s in seeds]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join(300)
+        for s in seeds:
+            st, best, _, _ = results[s]
+            assert st == fsp.FSP_OK and best == opts[s], s
+        assert srv.stats()["mean_pools_per_batch"] >= 1.0
+    for inst in insts.values():
+        inst.close()
