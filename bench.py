@@ -51,22 +51,30 @@ def algorithmic_int_ops(n: int, m: int, depths: np.ndarray) -> float:
     return float(np.sum(P * (n + 4 * nu) + 2 * m * n + 2 * m * d))
 
 
+LANES_SOURCES = ("fsp_bound_lanes.cu", "fsp_lanes_device.cuh", "fsp_ptx.cuh", "fsp_instance.cpp")
+
+
 def kernel_source_hash() -> str:
-    src = os.path.join(ROOT, "paper_1208_3933_gb300", "csrc", "fsp_bound.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the sources that make up the couple-lanes bounding kernel."""
+    h = hashlib.sha256()
+    for name in LANES_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1208_3933_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
 
 
-def read_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "fsp_bound_kernel_pool_200x20.json")
+def read_traffic(n_nodes: int):
+    """DRAM bytes per launch from the committed ncu capture, if it was taken
+    on the current kernel sources (else None).  The capture is a smaller pool
+    of the same instance; the bytes per node are scaled to this launch's nodes
+    (the kernel reads each node's row once and writes one bound)."""
+    path = os.path.join(ROOT, "profiles", "fsp_lanes_streamed_pool_200x20.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
     if d.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    return d["dram_bytes_per_launch"] / d["nodes_per_launch"] * n_nodes
 
 
 class ClockSampler:
@@ -161,6 +169,120 @@ def run_alu_peak():
         print(json.dumps({"pattern": name, "rc": rc, "ms": round(ms.value, 4), "sm_mhz": round(mhz.value),
                           "int_ops_per_s": rate, "ops_per_sm_per_clk": rate / sms / (mhz.value * 1e6),
                           "sms": sms}), flush=True)
+
+
+def run_batched_leg(dev, reps: int = 5):
+    """The batched uneven workload: 64 instances (seeds 100-163, n from
+    {20,50,100,200}, m from {5,10,20}, pools of 1,024 to 65,536 nodes).  One
+    graph-replayed persistent launch over all pools against one autotuned
+    plain launch per pool, same buffers, bit-exact."""
+    import torch
+    from paper_1208_3933_gb300 import fsp, workloads
+    ws = workloads.batched_instances()
+    insts = [fsp.Instance(w.p) for w in ws]
+    bufs = [(torch.from_numpy(w.rows).to(dev), torch.from_numpy(w.depths).to(dev)) for w in ws]
+    outs = [torch.empty(w.N, dtype=torch.int32, device=dev) for w in ws]
+    outs_b = [torch.empty(w.N, dtype=torch.int32, device=dev) for w in ws]
+    total = sum(w.N for w in ws)
+    for inst, (r, d), o in zip(insts, bufs, outs):
+        fsp.fsp_autotune(inst, r, d, o)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    def per_pool():
+        for inst, (r, d), o in zip(insts, bufs, outs):
+            fsp.fsp_bound_pool(inst, r, d, o)
+
+    plain_ms = timed(per_pool)
+    with fsp.Batch([(i, r, d, o) for i, (r, d), o in zip(insts, bufs, outs_b)]) as b:
+        batch_ms = timed(b.launch_graph)
+        q = b.query()
+    same = all(torch.equal(a, c) for a, c in zip(outs, outs_b))
+    for inst in insts:
+        inst.close()
+    return {"workload": "64 instances, seeds 100-163", "pools": len(ws), "nodes": total,
+            "batched_nodes_per_s": total / (batch_ms * 1e-3), "plain_nodes_per_s": total / (plain_ms * 1e-3),
+            "batched_ms": batch_ms, "plain_ms": plain_ms, "speedup": plain_ms / batch_ms,
+            "work_items": q["work_items"], "bit_exact_vs_plain": bool(same), "launch": "one CUDA-graph replay"}
+
+
+def run_served_leg(node_limit: int = 2_000_000, expand: int = 128, seconds: float = 40.0):
+    """The serving loop: 32 DFS searches (n=20, m=5 for seeds 200-215 and
+    m=10 for 216-231, NEH upper bound, node limit per search) plus 16 streams
+    of 200x20 pools (4,096-32,768 nodes, Poisson arrivals) share one server.
+    Served nodes/s and p50/p99 pool latency from the server; the plain rate
+    is the same stream pools bounded one by one through fsp_bound_pool_host."""
+    import threading
+
+    import torch
+    from paper_1208_3933_gb300 import fsp, workloads
+    golden = {}
+    gpath = os.path.join(ROOT, "tests", "golden", "serving_optima.json")
+    if os.path.exists(gpath):
+        golden = {int(k): v.get("opt") for k, v in json.load(open(gpath))["results"].items()}
+    searches = workloads.serving_searches()
+    streams = workloads.serving_streams(rate_hz=60.0)
+    s_insts = {s: fsp.Instance(p) for s, p in searches}
+    st_insts = [fsp.Instance(p) for p, _ in streams]
+    pools = [[(t, torch.from_numpy(r).pin_memory().numpy(), torch.from_numpy(d).pin_memory().numpy())
+              for t, r, d in pl] for _, pl in streams]
+    results = {}
+    with fsp.Server(hbm_budget_bytes=4 << 30, slots=3) as srv:
+        t_start = time.perf_counter()
+
+        def search(seed):
+            ub, _ = fsp.fsp_neh(s_insts[seed])
+            results[seed] = srv.search(s_insts[seed], ub, expand=expand, node_limit=node_limit)
+
+        def stream(i):
+            t0 = time.perf_counter()
+            reqs = []
+            for t, r, d in pools[i]:
+                delay = t - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                reqs.append(srv.submit(st_insts[i], r, d))
+            for q in reqs:
+                q.wait(int(seconds * 1e6))
+
+        threads = [threading.Thread(target=search, args=(s,)) for s, _ in searches]
+        threads += [threading.Thread(target=stream, args=(i,)) for i in range(len(streams))]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join(seconds * 4)
+        wall = time.perf_counter() - t_start
+        st = srv.stats()
+    finished = {s: r for s, r in results.items() if r[0] == fsp.FSP_OK}
+    verified = sum(1 for s, r in finished.items() if golden.get(s) is not None and golden[s] == r[1])
+    wrong = [s for s, r in finished.items() if golden.get(s) is not None and golden[s] != r[1]]
+    # plain: the stream pools bounded one by one, host buffers in and out
+    stream_nodes = 0
+    t0 = time.perf_counter()
+    for inst, pl in zip(st_insts, pools):
+        for _, r, d in pl:
+            fsp.fsp_bound_pool_host(inst, r, d)
+            stream_nodes += d.shape[0]
+    plain_s = time.perf_counter() - t0
+    for inst in list(s_insts.values()) + st_insts:
+        inst.close()
+    return {"workload": "32 DFS searches (20x5, 20x10; seeds 200-231) + 16 Poisson streams of 200x20 pools",
+            "served_nodes_per_s": st["nodes_done"] / st["active_seconds"] if st["active_seconds"] else None,
+            "plain_nodes_per_s": stream_nodes / plain_s, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
+            "pools": st["pools_done"], "nodes": st["nodes_done"], "batches": st["batches"],
+            "mean_pools_per_batch": st["mean_pools_per_batch"], "wall_s": wall,
+            "searches_finished": len(finished), "searches_cut_at_node_limit": len(results) - len(finished),
+            "node_limit_per_search": node_limit, "expand": expand,
+            "optima_verified_vs_oracle": verified, "optima_wrong": wrong}
 
 
 def dist_setup(args):
@@ -334,6 +456,8 @@ def run_gpu(args, world, rank, local):
     achieved = ops / mean_kernel_s
     cpu_rate, cpu_sample, cpu_s, cpu_threads = cpu_oracle_rate(w, seconds=2.0)
     info = inst.info()
+    batched = run_batched_leg(dev) if not (args.nodes or args.no_extra) else None
+    served = run_served_leg() if not (args.nodes or args.no_extra) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": region_ms_max / args.steps, "higher_is_better": True,
@@ -343,7 +467,7 @@ def run_gpu(args, world, rank, local):
                    "l2": "3 rotating pool copies of 105 MB (inputs larger than the 129 MB L2)",
                    "launch": launch, "autotune_ms": tuned_ms},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "int-ops/s",
-                     "frac": achieved / peak, "traffic": read_traffic(),
+                     "frac": achieved / peak, "traffic": read_traffic(w.N),
                      "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} int32 lanes x "
                                    f"{sm_max:.0f} MHz", "ops_per_launch": ops,
                      "kernel_ms_mean": mean_kernel_s * 1e3},
@@ -354,6 +478,8 @@ def run_gpu(args, world, rank, local):
                 "d2h_bytes_per_step": int(4 * w.N), "bit_exact_vs_device": ok_e2e},
         "gpu_launches": args.steps,
         "clocks": clocks,
+        "batched": batched,
+        "served": served,
     }
     print(json.dumps(line), flush=True)
     inst.close()
@@ -368,6 +494,7 @@ def main():
     ap.add_argument("--nodes", type=int, default=0,
                     help="bound only the first NODES nodes of the pool (small profiling cases)")
     ap.add_argument("--alu-peak", action="store_true", help="run the integer-pipe throughput probe and exit")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and served legs")
     ap.add_argument("--config", default="",
                     help="force a launch shape, e.g. kernel=2,warps_per_block=14 (profiling); default: autotuned")
     args = ap.parse_args()

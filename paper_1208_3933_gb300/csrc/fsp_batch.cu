@@ -53,13 +53,7 @@ __global__ void __launch_bounds__(512, 1)
             const uint32_t *R = reinterpret_cast<const uint32_t *>(a.grec) + (size_t)g * npad * 32 + lane;
 #pragma unroll 4
             for (int i = 0; i < npad; ++i) {
-                const uint32_t r = __ldg(R + i * 32);
-                const uint32_t fw = F[r & 1023u];
-                const float sf = __int_as_float(0x4B000000 | ((r >> 10) & 8191u)) - 8388608.0f;
-                const float df = __int_as_float(0x4B000000 | (uint32_t)(((int)r >> 23) + 256)) - 8388864.0f;
-#pragma unroll
-                for (int b = 0; b < 32; ++b)
-                    if ((fw >> b) & 1u) u[b] = fmaxf(u[b] + df, sf);
+                lanes_step(__ldg(R + i * 32), F, u);
             }
             couple_epilogue(AQ, aq_stride, m, kk, ll, u, lb);
         }

@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) 
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     int *ctr = reinterpret_cast<int *>(smem + 8);
     uint8_t *sgp = smem + 16;
+    int2 *hcache = reinterpret_cast<int2 *>(smem + a.off_cache);
+    int2 *tcache = hcache + a.m * 32;
     const unsigned char *tables = smem + a.off_tables;
     uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * a.n;
     int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
@@ -67,6 +69,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) 
         *ctr = 0;
     }
     for (int i = threadIdx.x; i < a.G * 64; i += blockDim.x) sgp[i] = a.gpairs[i];
+    load_sorted_heads(a, hcache, tcache);
     __syncthreads();
     const size_t group_bytes = (size_t)a.npad * 32 * a.rec_bytes;
     if (threadIdx.x == 0) {
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) 
         if (bt >= b1) break;
         const int64_t x = bt * 32 + lane;
         int bterm = 0;
-        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm);
+        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
         if (!ready) {
             if (!mbar_wait_bounded(bar, 0, a.wait_limit)) {
                 if (lane == 0) report_status(a.status, (int32_t)FSP_ETIMEDOUT);
@@ -126,6 +129,8 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
     const int W = blockDim.x >> 5;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     uint8_t *sgp = smem + 16;
+    int2 *hcache = reinterpret_cast<int2 *>(smem + a.off_cache);
+    int2 *tcache = hcache + a.m * 32;
     uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * a.n;
     int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
 
@@ -135,6 +140,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
         mbar_fence_init();
     }
     for (int i = threadIdx.x; i < a.G * 64; i += blockDim.x) sgp[i] = a.gpairs[i];
+    load_sorted_heads(a, hcache, tcache);
     __syncthreads();
 
     TilePipe tp{bar, smem + a.off_tables, a.tile_stride, a.ntiles <= 2};
@@ -152,7 +158,8 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
     for (int64_t bt = blockIdx.x; bt < a.num_batches; bt += gridDim.x) {
         const int64_t x = bt * (int64_t)(32 * W) + warp * 32 + lane;
         int bterm = 0;
-        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm);
+        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
+        prefetch_row(a, x + (int64_t)gridDim.x * (32 * W));  // this block's next batch
         int lb[32];
         float uf[32];
         int ui[32];
@@ -214,7 +221,7 @@ namespace {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct LanesLayout {
-    uint32_t off_tables, tile_stride, off_flags, off_aq;
+    uint32_t off_cache, off_tables, tile_stride, off_flags, off_aq;
     int32_t aq_stride;
     size_t total;
 };
@@ -223,7 +230,8 @@ int aq_stride_for(int m) { return (m + (m + 1) / 2) | 1; }
 
 LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident, int chunk) {
     LanesLayout L;
-    L.off_tables = (uint32_t)align_up(16 + (size_t)inst->G * 64, 128);
+    L.off_cache = (uint32_t)align_up(16 + (size_t)inst->G * 64, 128);
+    L.off_tables = (uint32_t)align_up(L.off_cache + (size_t)inst->m * 32 * 8 * 2, 128);
     const size_t group_bytes = (size_t)inst->npad * 32 * inst->rec_bytes;
     if (resident) {
         L.tile_stride = (uint32_t)group_bytes;
@@ -326,6 +334,7 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     a.nchunks = (inst->npad + chunk - 1) / chunk;
     a.ntiles = inst->G * a.nchunks;
     a.rec_bytes = (uint32_t)inst->rec_bytes;
+    a.off_cache = L.off_cache;
     a.off_tables = L.off_tables;
     a.tile_stride = L.tile_stride;
     a.off_flags = L.off_flags;

@@ -124,16 +124,23 @@ extern "C" fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m
     const int G = inst->G;
     std::vector<uint32_t> grec_c;
     std::vector<int32_t> grec_w;
+    // empty couples and padding positions hold the no-op record s = 0, delta = 0
+    const uint32_t kLanesNoop = 256u << 13;
     if (inst->compact)
-        grec_c.assign((size_t)G * npad * 32, 0u);
+        grec_c.assign((size_t)G * npad * 32, kLanesNoop);
     else
         grec_w.assign((size_t)G * npad * 32 * 4, 0);
     for (int c = 0; c < P; ++c) {
         const int g = c / 32, lane = c % 32;
         for (int i = 0; i < npad; ++i) {
             const size_t dst = ((size_t)g * npad + i) * 32 + lane;
-            if (inst->compact)
-                grec_c[dst] = rec_c[(size_t)c * npad + i];
+            if (inst->compact) {
+                // couple-lanes encoding: s bits 0..12, delta+256 bits 13..21, job bits 22..31
+                const uint32_t r = rec_c[(size_t)c * npad + i];
+                const uint32_t j = r & 1023u, sv = (r >> 10) & 8191u;
+                const int32_t dv = (int32_t)r >> 23;
+                grec_c[dst] = sv | ((uint32_t)(dv + 256) << 13) | (j << 22);
+            }
             else
                 for (int f = 0; f < 4; ++f) grec_w[dst * 4 + f] = rec_w[((size_t)c * npad + i) * 4 + f];
         }

@@ -31,6 +31,12 @@
 //   bits  0..9   j
 //   bits 10..22  s
 //   bits 23..31  delta (two's complement)
+// The couple-lanes copy (grec) packs the same fields so that each becomes an
+// fp32 value with one bitwise op and one add:
+//   bits  0..12  s            -> float(0x4B000000 | s) - 2^23
+//   bits 13..21  delta + 256  -> float(0x44800000 | those bits) - 1280
+//   bits 22..31  j
+// and its no-op record (padding, empty couples) is s = 0, delta = 0.
 // Wide record: int4 {j, s, delta, 0}.
 // Padding entries and empty couples are all-zero records: for any u >= 0,
 // max(u + 0, 0) = u, so they never change the result, and an empty couple

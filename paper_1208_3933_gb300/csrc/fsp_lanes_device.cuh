@@ -36,12 +36,11 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 // sum, so the answer is the sum of the first listed job whose flag bit is
 // set.  32 list entries are examined per step, one per lane; the transposed
 // flag words give every node the lanes that hit, and the first hit's sum is
-// shuffled in.  Nodes already `settled` get 0.
-__device__ __forceinline__ int first_unscheduled(const int2 *__restrict__ sorted, const uint32_t *F, int n, int lane,
-                                                 bool settled) {
-    int result = 0;
-    bool done = settled;
-    for (int base = 0; base < n && __any_sync(kFull, !done); base += 32) {
+// shuffled in.  Entries [0, 32) come from `first32` (a shared-memory copy) or
+// from `sorted`; later steps read `sorted`.  Nodes already `done` keep `res`.
+__device__ __forceinline__ void first_unscheduled_from(const int2 *__restrict__ sorted, int base, const uint32_t *F,
+                                                       int n, int lane, bool &done, int &res) {
+    for (; base < n && __any_sync(kFull, !done); base += 32) {
         const int pos = base + lane;
         int2 e = make_int2(0, 0);
         uint32_t w = 0;
@@ -53,11 +52,57 @@ __device__ __forceinline__ int first_unscheduled(const int2 *__restrict__ sorted
         const int first = __ffs(hits) - 1;
         const int val = __shfl_sync(kFull, e.y, first < 0 ? 0 : first);
         if (!done && first >= 0) {
-            result = val;
+            res = val;
             done = true;
         }
     }
-    return result;
+}
+
+// The head and the tail minima of one machine together (two independent
+// transposes in flight); first32_h / first32_t may be null (read `sorted`).
+__device__ __forceinline__ void machine_minima(const int2 *first32_h, const int2 *first32_t,
+                                               const int2 *__restrict__ sorted_h, const int2 *__restrict__ sorted_t,
+                                               bool want_h, bool want_t, const uint32_t *F, int n, int lane,
+                                               bool settled, int &mh, int &mt) {
+    mh = 0;
+    mt = 0;
+    bool done_h = settled || !want_h, done_t = settled || !want_t;
+    const bool in = lane < n;
+    int2 eh = make_int2(0, 0), et = make_int2(0, 0);
+    if (in && want_h) eh = first32_h ? first32_h[lane] : __ldg(sorted_h + lane);
+    if (in && want_t) et = first32_t ? first32_t[lane] : __ldg(sorted_t + lane);
+    const uint32_t wh = (in && want_h) ? F[eh.x] : 0u, wt = (in && want_t) ? F[et.x] : 0u;
+    const uint32_t hh = warp_transpose32(wh, lane), ht = warp_transpose32(wt, lane);
+    const int fh = __ffs(hh) - 1, ft = __ffs(ht) - 1;
+    const int vh = __shfl_sync(kFull, eh.y, fh < 0 ? 0 : fh), vt = __shfl_sync(kFull, et.y, ft < 0 ? 0 : ft);
+    if (!done_h && fh >= 0) {
+        mh = vh;
+        done_h = true;
+    }
+    if (!done_t && ft >= 0) {
+        mt = vt;
+        done_t = true;
+    }
+    if (want_h) first_unscheduled_from(sorted_h, 32, F, n, lane, done_h, mh);
+    if (want_t) first_unscheduled_from(sorted_t, 32, F, n, lane, done_t, mt);
+}
+
+// Copies the first 32 entries of every machine's head- and tail-sorted job
+// lists into shared memory ([m][32] each; entries past n read (0,0)).
+__device__ __forceinline__ void load_sorted_heads(const LanesArgs &a, int2 *hcache, int2 *tcache) {
+    for (int i = threadIdx.x; i < a.m * 32; i += blockDim.x) {
+        const int k = i >> 5, pos = i & 31;
+        hcache[i] = pos < a.n ? a.hsort[(size_t)k * a.n + pos] : make_int2(0, 0);
+        tcache[i] = pos < a.n ? a.tsort[(size_t)k * a.n + pos] : make_int2(0, 0);
+    }
+}
+
+// L2 prefetch of a node row (the next batch's, issued during this batch's scan).
+__device__ __forceinline__ void prefetch_row(const LanesArgs &a, int64_t x) {
+    if (x >= a.N) return;
+    const char *row = reinterpret_cast<const char *>(a.nodes + x * (int64_t)a.n);
+    for (int off = 0; off < 2 * a.n; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.depths + x));
 }
 
 // Setup of node x (lane = node) for the warp's 32 nodes: the flag words F[j]
@@ -66,7 +111,8 @@ __device__ __forceinline__ int first_unscheduled(const int2 *__restrict__ sorted
 // max_{l>=1} (A_l + q_l).  Returns whether the row is valid.
 template <int MP>
 __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int lane, uint32_t *F, int32_t *myrow,
-                                            int &bterm) {
+                                            int &bterm, const int2 *hcache = nullptr,
+                                            const int2 *tcache = nullptr) {
     const int n = a.n, m = a.m;
     bool valid = false;
     int d = 0;
@@ -108,8 +154,8 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
             int c = 0;
 #pragma unroll
             for (int q = 0; q < MP / 4; ++q) {
-                if (4 * q >= a.mpad) break;
-                const int4 v = __ldg(pj + q);
+                // columns past the instance's own padding read as zeros (no branch)
+                const int4 v = 4 * q < a.mpad ? __ldg(pj + q) : make_int4(0, 0, 0, 0);
                 const int pv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -122,39 +168,72 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
         }
     }
     __syncwarp();
-    // (3) A_k = max(C_k, min_U head) + (ptot_k - prefix sum), q_l = min_U tail
+    // (3) A_k = max(C_k, min_U head) + (ptot_k - prefix sum), q_l = min_U tail.
+    // First the 32 cheapest list entries of every machine, all independent;
+    // then, for the rare nodes whose first 32 entries are all scheduled, the
+    // rest of the list machine by machine.
     const bool settled = !valid || d == n;  // nothing to search for
     int16_t *qrow = reinterpret_cast<int16_t *>(myrow + m);
-    bterm = 0;
+    uint32_t open_h = 0, open_t = 0;  // machines still searching (bit k)
+    const bool in = lane < n;
 #pragma unroll
     for (int k = 0; k < MP; ++k) {
         if (k < m) {
-            const int mh = k > 0 ? first_unscheduled(a.hsort + (size_t)k * n, F, n, lane, settled) : 0;
-            const int Ak = max(C[k], mh) + (__ldg(a.ptot + k) - Ps[k]);
-            const int ql = k < m - 1 ? first_unscheduled(a.tsort + (size_t)k * n, F, n, lane, settled) : 0;
-            myrow[k] = Ak;
+            const bool want_h = k > 0, want_t = k < m - 1;  // heads are 0 on machine 0, tails on m-1
+            int2 eh = make_int2(0, 0), et = make_int2(0, 0);
+            if (in && want_h) eh = hcache ? hcache[k * 32 + lane] : __ldg(a.hsort + (size_t)k * n + lane);
+            if (in && want_t) et = tcache ? tcache[k * 32 + lane] : __ldg(a.tsort + (size_t)k * n + lane);
+            const uint32_t wh = (in && want_h) ? F[eh.x] : 0u, wt = (in && want_t) ? F[et.x] : 0u;
+            const uint32_t hh = warp_transpose32(wh, lane), ht = warp_transpose32(wt, lane);
+            const int fh = __ffs(hh) - 1, ft = __ffs(ht) - 1;
+            const int vh = __shfl_sync(kFull, eh.y, fh < 0 ? 0 : fh);
+            const int vt = __shfl_sync(kFull, et.y, ft < 0 ? 0 : ft);
+            const int mh = (!settled && fh >= 0) ? vh : 0;
+            const int ql = (!settled && ft >= 0) ? vt : 0;
+            if (want_h && !settled && fh < 0) open_h |= 1u << k;
+            if (want_t && !settled && ft < 0) open_t |= 1u << k;
+            myrow[k] = max(C[k], mh) + (__ldg(a.ptot + k) - Ps[k]);
             qrow[k] = (int16_t)ql;
-            if (k >= 1) bterm = max(bterm, Ak + ql);
         }
     }
+    if (__any_sync(kFull, (open_h | open_t) != 0)) {
+#pragma unroll
+        for (int k = 0; k < MP; ++k) {
+            if (k < m && __any_sync(kFull, ((open_h | open_t) >> k) & 1u)) {
+                bool done_h = !((open_h >> k) & 1u), done_t = !((open_t >> k) & 1u);
+                int mh = 0, ql = 0;
+                first_unscheduled_from(a.hsort + (size_t)k * n, 32, F, n, lane, done_h, mh);
+                first_unscheduled_from(a.tsort + (size_t)k * n, 32, F, n, lane, done_t, ql);
+                if ((open_h >> k) & 1u) myrow[k] = max(C[k], mh) + (__ldg(a.ptot + k) - Ps[k]);
+                if ((open_t >> k) & 1u) qrow[k] = (int16_t)ql;
+            }
+        }
+    }
+    bterm = 0;
+    for (int l = 1; l < m; ++l) bterm = max(bterm, myrow[l] + qrow[l]);
     __syncwarp();
     return valid;
+}
+
+// One slack update of the 32 nodes for a couple-lanes record r (32-bit
+// encoding of fsp_internal.h): s and delta become exact floats by OR-ing an
+// exponent into their bit fields (s < 2^13 below the 2^23 exponent, delta+256
+// < 2^9 below the 2^10 exponent), then u_b = max(u_b + delta, s) for every
+// node b whose flag bit for job r>>22 is set.
+__device__ __forceinline__ void lanes_step(uint32_t r, const uint32_t *F, float (&u)[32]) {
+    const uint32_t fw = F[r >> 22];
+    const float sf = __int_as_float((r & 0x1FFFu) | 0x4B000000u) - 8388608.0f;
+    const float df = __int_as_float((r & 0x3FE000u) | 0x44800000u) - 1280.0f;
+#pragma unroll
+    for (int b = 0; b < 32; ++b)
+        if ((fw >> b) & 1u) u[b] = fmaxf(u[b] + df, sf);
 }
 
 // One couple group's scan over positions [0, npos) of a record tile (lane =
 // couple): fp32 slack for 32-bit records, int32 for 128-bit records.
 __device__ __forceinline__ void scan_compact(const uint32_t *R, int npos, const uint32_t *F, float (&u)[32]) {
 #pragma unroll 2
-    for (int i = 0; i < npos; ++i) {
-        const uint32_t r = R[i * 32];
-        const uint32_t fw = F[r & 1023u];
-        // exact int -> float for 0 <= v < 2^23 via the exponent of 2^23
-        const float sf = __int_as_float(0x4B000000 | ((r >> 10) & 8191u)) - 8388608.0f;
-        const float df = __int_as_float(0x4B000000 | (uint32_t)(((int)r >> 23) + 256)) - 8388864.0f;
-#pragma unroll
-        for (int b = 0; b < 32; ++b)
-            if ((fw >> b) & 1u) u[b] = fmaxf(u[b] + df, sf);
-    }
+    for (int i = 0; i < npos; ++i) lanes_step(R[i * 32], F, u);
 }
 
 __device__ __forceinline__ void scan_wide(const int4 *R, int npos, const uint32_t *F, int (&u)[32]) {

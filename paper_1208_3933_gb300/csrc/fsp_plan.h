@@ -34,6 +34,7 @@ struct LanesArgs {
     uint32_t off_tables;  // records (resident: all groups; streamed: two tile buffers)
     uint32_t tile_stride;
     uint32_t off_flags, off_aq;
+    uint32_t off_cache;   // first 32 entries of each machine's head/tail-sorted list (0 = none)
     int32_t aq_stride;    // ints per node row (odd): A as int32 [m], then q as int16 [m]
     long long wait_limit;
 };
