@@ -155,11 +155,31 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
         if (a.ntiles == 2) tile_issue(1, 1);
     }
 
+    int *okey = reinterpret_cast<int *>(smem + a.off_order);  // [32W] sort keys
+    int *operm = okey + 32 * W;                                // [32W] batch offsets by rank
     for (int64_t bt = blockIdx.x; bt < a.num_batches; bt += gridDim.x) {
-        const int64_t x = bt * (int64_t)(32 * W) + warp * 32 + lane;
+        const int64_t base = bt * (int64_t)(32 * W);
+        // The batch's nodes in order of depth (ties by index): warp w takes
+        // ranks [32w, 32w+32), so the depth-long loops of a warp's setup run
+        // about as long as its own deepest node instead of the batch's.
+        {
+            const int64_t xi = base + threadIdx.x;
+            const int dep = xi < a.N ? __ldg(a.depths + xi) : -1;
+            const int key = ((min(max(dep, -1), a.n + 1) + 1) << 10) | (int)threadIdx.x;  // distinct keys
+            okey[threadIdx.x] = key;
+            __syncthreads();
+            int rank = 0;
+            for (int i = 0; i < 32 * W; i += 4) {
+                const int4 k4 = *reinterpret_cast<const int4 *>(okey + i);
+                rank += (k4.x < key) + (k4.y < key) + (k4.z < key) + (k4.w < key);
+            }
+            operm[rank] = threadIdx.x;
+            __syncthreads();
+        }
+        const int64_t x = base + operm[threadIdx.x];
         int bterm = 0;
         const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
-        prefetch_row(a, x + (int64_t)gridDim.x * (32 * W));  // this block's next batch
+        prefetch_row(a, x + (int64_t)gridDim.x * (32 * W));  // a node of this block's next batch
         int lb[32];
         float uf[32];
         int ui[32];
@@ -221,7 +241,7 @@ namespace {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct LanesLayout {
-    uint32_t off_cache, off_tables, tile_stride, off_flags, off_aq;
+    uint32_t off_cache, off_tables, tile_stride, off_flags, off_aq, off_order;
     int32_t aq_stride;
     size_t total;
 };
@@ -242,7 +262,8 @@ LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident,
     }
     L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)warps * inst->n * 4, 128);
     L.aq_stride = aq_stride_for(inst->m);
-    L.total = align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
+    L.off_order = (uint32_t)align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
+    L.total = align_up(L.off_order + (size_t)warps * 32 * 4 * 2, 128);
     return L;
 }
 
@@ -339,6 +360,7 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     a.tile_stride = L.tile_stride;
     a.off_flags = L.off_flags;
     a.off_aq = L.off_aq;
+    a.off_order = L.off_order;
     a.aq_stride = L.aq_stride;
     a.wait_limit = 4000000000LL;
     int grid;

@@ -58,35 +58,6 @@ __device__ __forceinline__ void first_unscheduled_from(const int2 *__restrict__ 
     }
 }
 
-// The head and the tail minima of one machine together (two independent
-// transposes in flight); first32_h / first32_t may be null (read `sorted`).
-__device__ __forceinline__ void machine_minima(const int2 *first32_h, const int2 *first32_t,
-                                               const int2 *__restrict__ sorted_h, const int2 *__restrict__ sorted_t,
-                                               bool want_h, bool want_t, const uint32_t *F, int n, int lane,
-                                               bool settled, int &mh, int &mt) {
-    mh = 0;
-    mt = 0;
-    bool done_h = settled || !want_h, done_t = settled || !want_t;
-    const bool in = lane < n;
-    int2 eh = make_int2(0, 0), et = make_int2(0, 0);
-    if (in && want_h) eh = first32_h ? first32_h[lane] : __ldg(sorted_h + lane);
-    if (in && want_t) et = first32_t ? first32_t[lane] : __ldg(sorted_t + lane);
-    const uint32_t wh = (in && want_h) ? F[eh.x] : 0u, wt = (in && want_t) ? F[et.x] : 0u;
-    const uint32_t hh = warp_transpose32(wh, lane), ht = warp_transpose32(wt, lane);
-    const int fh = __ffs(hh) - 1, ft = __ffs(ht) - 1;
-    const int vh = __shfl_sync(kFull, eh.y, fh < 0 ? 0 : fh), vt = __shfl_sync(kFull, et.y, ft < 0 ? 0 : ft);
-    if (!done_h && fh >= 0) {
-        mh = vh;
-        done_h = true;
-    }
-    if (!done_t && ft >= 0) {
-        mt = vt;
-        done_t = true;
-    }
-    if (want_h) first_unscheduled_from(sorted_h, 32, F, n, lane, done_h, mh);
-    if (want_t) first_unscheduled_from(sorted_t, 32, F, n, lane, done_t, mt);
-}
-
 // Copies the first 32 entries of every machine's head- and tail-sorted job
 // lists into shared memory ([m][32] each; entries past n read (0,0)).
 __device__ __forceinline__ void load_sorted_heads(const LanesArgs &a, int2 *hcache, int2 *tcache) {

@@ -35,6 +35,7 @@ struct LanesArgs {
     uint32_t tile_stride;
     uint32_t off_flags, off_aq;
     uint32_t off_cache;   // first 32 entries of each machine's head/tail-sorted list (0 = none)
+    uint32_t off_order;   // streamed kernel: a batch's depth keys and node order
     int32_t aq_stride;    // ints per node row (odd): A as int32 [m], then q as int16 [m]
     long long wait_limit;
 };
