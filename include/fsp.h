@@ -85,17 +85,25 @@ typedef struct fsp_instance_info {
 #define FSP_KERNEL_LOCKSTEP 1
 #define FSP_KERNEL_LANES 2
 /* Lanes kernel staging: all records resident in shared memory (warps then
- * work independently), or streamed through two tile buffers. */
+ * work independently); streamed through two tile buffers, each block setting
+ * up its nodes and scanning in one kernel; or split: a prep kernel sets up
+ * every 32-node batch into stream-ordered scratch (from a per-device memory
+ * pool the library keeps; about (n + 48 m + 64) * 4 bytes per 32 nodes, at
+ * most 2^20 nodes' worth per call) and a scan kernel streams the tiles; or
+ * warp: every warp streams the tiles through its own ring of buffers and the
+ * warps of a block work independently. */
 #define FSP_STAGING_AUTO 0
 #define FSP_STAGING_RESIDENT 1
 #define FSP_STAGING_STREAMED 2
+#define FSP_STAGING_SPLIT 3
+#define FSP_STAGING_WARP 4
 typedef struct fsp_launch_config {
     int32_t kernel;              /* FSP_KERNEL_* */
     int32_t nodes_per_thread;    /* lockstep: K in {1,2,4,8} */
-    int32_t blocks_per_sm;       /* resident blocks per SM (1 or 2; lanes: streamed staging only) */
+    int32_t blocks_per_sm;       /* resident blocks per SM (1 or 2; lanes: streamed/split/warp staging) */
     int32_t pairs_per_tile;      /* lockstep: couples staged in shared memory at a time */
     int32_t warps_per_block;     /* lanes: 1..16 warps of 32 nodes */
-    int32_t positions_per_tile;  /* lanes, streamed: Johnson positions per tile (multiple of 4) */
+    int32_t positions_per_tile;  /* lanes, streamed/split/warp: Johnson positions per tile (multiple of 4) */
     int32_t staging;             /* lanes: FSP_STAGING_* */
     int32_t reserved;
 } fsp_launch_config;
@@ -183,6 +191,34 @@ fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_t *nodes,
  */
 fsp_status fsp_branch_and_bound(const fsp_instance *inst, int32_t ub0, int16_t *best_perm,
                                 int32_t *best_makespan, int64_t *nodes_bounded);
+
+/*
+ * fsp_branch_and_bound_device -- the same depth-first B&B with branching and
+ * elimination on the device as well (the steps on either side of the bound,
+ * which the paper runs on the CPU in Section III-A).  The open nodes live in
+ * a device stack; each round pops up to `expand` nodes from its top (a node
+ * whose LB reached UB is eliminated), generates their children on the device
+ * (one per unscheduled job, forward branching of Section II-B), bounds them
+ * as one pool, takes the best leaf as the incumbent when it lowers UB, drops
+ * children with LB >= UB and pushes the rest where the parents were -- the
+ * children of the topmost parent on top, each parent's children in
+ * decreasing (LB, job) order so the smallest is popped first.  Node rows
+ * never leave the device; the host reads a few counters per round.
+ *   ub0, best_perm, best_makespan, nodes_bounded  as fsp_branch_and_bound
+ *                  (with expand = 1 the exploration order is the same, up to
+ *                  when a leaf updates UB: at generation, not when popped);
+ *   expand         parents per round, 0..65536 (0 = 256);
+ *   node_limit     0 = none; otherwise the search stops with FSP_ETIMEDOUT
+ *                  once that many bounds were evaluated (nodes_bounded is
+ *                  still written).
+ * Synchronous; uses its own CUDA stream; device memory grows with the stack
+ * (at least expand * n children of n int16 jobs, plus the stack).
+ * Errors: FSP_EINVAL, FSP_ENOMEM, FSP_ECUDA, FSP_EBADNODE, FSP_ENOTFOUND,
+ * FSP_ETIMEDOUT.
+ */
+fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int32_t ub0, int32_t expand,
+                                       int64_t node_limit, int16_t *best_perm,
+                                       int32_t *best_makespan, int64_t *nodes_bounded);
 
 /*
  * fsp_autotune -- picks the launch shape for pools of N nodes of this

@@ -124,7 +124,7 @@ fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_p
     }
     pp = PlanParams();
     pp.mp = mp;
-    pp.n_max = n_max;
+    pp.n_max = flag_words(n_max);  // flag words per warp
     pp.stride = (m_max + (m_max + 1) / 2) | 1;
     // work items, longest first: couple groups x Johnson positions of the instance
     items.clear();
@@ -167,7 +167,7 @@ fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_p
     const int smem_optin = max_smem_per_block(device);
     int W = warps_per_block ? warps_per_block : 16;
     for (; W >= 1; --W) {
-        const uint32_t off_aq = (uint32_t)align_up((size_t)W * n_max * 4, 128);
+        const uint32_t off_aq = (uint32_t)align_up((size_t)W * pp.n_max * 4, 128);
         const size_t total = align_up(off_aq + (size_t)W * 32 * pp.stride * 4, 128);
         if (total <= (size_t)smem_optin) {
             pp.off_aq = off_aq;

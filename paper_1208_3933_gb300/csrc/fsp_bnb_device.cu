@@ -1,0 +1,360 @@
+// fsp_bnb_device.cu -- depth-first branch-and-bound with branching and
+// elimination on the device.
+//
+// The paper keeps selection, branching and elimination on the CPU and ships
+// each pool of children to the GPU for bounding (Section III-A).  Here the
+// open nodes live in a device stack and never leave the device; one round
+//   1. pops up to `expand` nodes from the top of the stack (a parent whose
+//      bound reached the incumbent is dropped: elimination),
+//   2. branches each parent into one child per unscheduled job (forward
+//      branching, Section II-B: the job is appended to the prefix), children
+//      of a parent in job order,
+//   3. bounds all children as one pool (the couple-lanes kernels),
+//   4. takes the best leaf (a leaf's bound is its makespan) as the new
+//      incumbent when it improves, drops children whose bound reaches the
+//      incumbent, and pushes the survivors back where the parents were, the
+//      children of the topmost parent on top and, within a parent, in
+//      decreasing (bound, job) order so that the smallest is popped first.
+// The host reads two counters per round (children generated, new stack size)
+// to size the next launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <vector>
+
+#include "fsp_internal.h"
+
+namespace fspgb {
+namespace {
+
+constexpr int kScanThreads = 1024;
+
+// Round state kept on the device.
+struct DevState {
+    int32_t best;          // incumbent makespan, or ub0 + 1 before any
+    int32_t found;         // an incumbent exists
+    int32_t total;         // children generated this round
+    int32_t survivors;     // children pushed this round
+    unsigned long long round_key;  // (makespan << 32) | child of this round's best leaf
+};
+
+// Block-wide exclusive scan of `count(i)` over i in [0, k): out[i] and the
+// total in out[k].  One block of kScanThreads threads.
+template <typename CountF>
+__device__ void block_exclusive_scan(int k, CountF count, int32_t *out) {
+    __shared__ int32_t part[kScanThreads];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < k; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int v = i < k ? count(i) : 0;
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < kScanThreads; off <<= 1) {
+            const int t = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+            __syncthreads();
+            part[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < k) out[i] = carry + part[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) carry += part[kScanThreads - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = carry;
+}
+
+// (1)+(2a) children per popped parent: n - d for a parent still below the
+// incumbent, else 0; offsets of each parent's children.
+__global__ void __launch_bounds__(kScanThreads) bnb_count_children(const int32_t *sdep, const int32_t *slb,
+                                                                     int64_t top0, int k, int n, DevState *st,
+                                                                     int32_t *offs) {
+    const int32_t best = st->best;
+    block_exclusive_scan(
+        k, [&](int i) { return slb[top0 + i] < best ? n - sdep[top0 + i] : 0; }, offs);
+    if (threadIdx.x == 0) {
+        st->total = offs[k];
+        st->round_key = ~0ull;
+    }
+}
+
+// (2b) one warp per parent writes its children: the parent's prefix plus one
+// unscheduled job, in job order.
+__global__ void bnb_make_children(const int16_t *srows, const int32_t *sdep, int64_t top0, int k, int n,
+                                  const int32_t *offs, int16_t *crows, int32_t *cdep, int32_t *cparent) {
+    const int lane = threadIdx.x & 31;
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= k) return;
+    const int c0 = offs[p], cnt = offs[p + 1] - c0;
+    if (cnt == 0) return;
+    const int d = sdep[top0 + p];
+    const int16_t *prow = srows + (top0 + p) * (int64_t)n;
+    // scheduled-job bitmap of the prefix, built by the warp in shared memory
+    extern __shared__ uint32_t sched[];
+    const int nw = (n + 31) >> 5;
+    uint32_t *bm = sched + (threadIdx.x >> 5) * nw;
+    for (int w = lane; w < nw; w += 32) bm[w] = 0u;
+    __syncwarp();
+    for (int i = lane; i < d; i += 32) {
+        const int j = prow[i];
+        atomicOr(&bm[j >> 5], 1u << (j & 31));
+    }
+    __syncwarp();
+    // the r-th unscheduled job (in job order) becomes child c0 + r
+    int r = 0;
+    for (int w = 0; w < nw; ++w) {
+        const uint32_t un = ~bm[w] & (w == nw - 1 && (n & 31) ? ((1u << (n & 31)) - 1u) : 0xffffffffu);
+        const int j = w * 32 + lane;
+        const bool mine = (un >> lane) & 1u;
+        const int rank = r + __popc(un & ((1u << lane) - 1u));
+        if (mine) {
+            const int c = c0 + rank;
+            int16_t *crow = crows + (int64_t)c * n;
+            for (int i = 0; i < d; ++i) crow[i] = prow[i];
+            crow[d] = (int16_t)j;
+            for (int i = d + 1; i < n; ++i) crow[i] = 0;
+            cdep[c] = d + 1;
+            cparent[c] = p;
+        }
+        r += __popc(un);
+    }
+}
+
+// (4a) leaves update the round's best; other children survive while their
+// bound is below the incumbent.
+__global__ void bnb_filter(const int32_t *clb, const int32_t *cdep, int total, int n, DevState *st,
+                           int32_t *keep) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= total) return;
+    const int32_t best = st->best, lb = clb[c];
+    int kv = 0;
+    if (lb >= 0 && lb < best) {
+        if (cdep[c] == n)
+            atomicMin(&st->round_key, ((unsigned long long)(uint32_t)lb << 32) | (uint32_t)c);
+        else
+            kv = 1;
+    }
+    keep[c] = kv;
+}
+
+// (4b) the incumbent from this round's best leaf.
+__global__ void bnb_incumbent(const int16_t *crows, int n, DevState *st, int16_t *best_row) {
+    const unsigned long long key = st->round_key;
+    if (key == ~0ull) return;
+    const int32_t ms = (int32_t)(key >> 32);
+    if (ms >= st->best) return;
+    const int c = (int)(key & 0xffffffffu);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) best_row[i] = crows[(int64_t)c * n + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->best = ms;
+        st->found = 1;
+    }
+}
+
+// (4c) survivors per parent and their offsets in the stack.
+__global__ void __launch_bounds__(kScanThreads) bnb_count_survivors(const int32_t *offs, const int32_t *keep, int k,
+                                                                      DevState *st, int32_t *soffs) {
+    block_exclusive_scan(
+        k,
+        [&](int p) {
+            int s = 0;
+            for (int c = offs[p]; c < offs[p + 1]; ++c) s += keep[c];
+            return s;
+        },
+        soffs);
+    if (threadIdx.x == 0) st->survivors = soffs[k];
+}
+
+// (4d) push: survivor c of parent p goes to top0 + soffs[p] + (number of
+// surviving siblings with a larger (bound, job)).
+__global__ void bnb_push(const int16_t *crows, const int32_t *cdep, const int32_t *clb, const int32_t *cparent,
+                         const int32_t *offs, const int32_t *keep, const int32_t *soffs, int total, int n, int64_t top0,
+                         int16_t *srows, int32_t *sdep, int32_t *slb) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= total || !keep[c]) return;
+    const int p = cparent[c];
+    const int32_t lb = clb[c];
+    const int d = cdep[c];
+    const int job = crows[(int64_t)c * n + d - 1];
+    int r = 0;
+    for (int s = offs[p]; s < offs[p + 1]; ++s) {
+        if (s == c || !keep[s]) continue;
+        const int32_t lbs = clb[s];
+        const int jobs = crows[(int64_t)s * n + d - 1];
+        r += (lbs > lb) || (lbs == lb && jobs > job);
+    }
+    const int64_t dst = top0 + soffs[p] + r;
+    for (int i = 0; i < n; ++i) srows[dst * n + i] = crows[(int64_t)c * n + i];
+    sdep[dst] = d;
+    slb[dst] = lb;
+}
+
+struct DevBuffers {
+    int16_t *srows = nullptr, *crows = nullptr, *best_row = nullptr;
+    int32_t *sdep = nullptr, *slb = nullptr, *cdep = nullptr, *clb = nullptr, *cparent = nullptr;
+    int32_t *offs = nullptr, *keep = nullptr, *soffs = nullptr;
+    DevState *st = nullptr;
+    int64_t cap = 0;
+    void release() {
+        for (void *p : {(void *)srows, (void *)crows, (void *)best_row, (void *)sdep, (void *)slb, (void *)cdep,
+                        (void *)clb, (void *)cparent, (void *)offs, (void *)keep, (void *)soffs, (void *)st})
+            if (p) cudaFree(p);
+    }
+};
+
+// Grows the stack to hold `need` nodes, keeping its first `keep_nodes`.
+fsp_status grow_stack(DevBuffers &b, int n, int64_t need, int64_t keep_nodes) {
+    if (need <= b.cap) return FSP_OK;
+    const int64_t cap = std::max<int64_t>(need, b.cap * 2);
+    int16_t *r = nullptr;
+    int32_t *d = nullptr, *l = nullptr;
+    if (cudaMalloc((void **)&r, sizeof(int16_t) * cap * n) != cudaSuccess ||
+        cudaMalloc((void **)&d, sizeof(int32_t) * cap) != cudaSuccess ||
+        cudaMalloc((void **)&l, sizeof(int32_t) * cap) != cudaSuccess) {
+        if (r) cudaFree(r);
+        if (d) cudaFree(d);
+        return FSP_ENOMEM;
+    }
+    if (keep_nodes > 0 &&
+        (cudaMemcpy(r, b.srows, sizeof(int16_t) * keep_nodes * n, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+         cudaMemcpy(d, b.sdep, sizeof(int32_t) * keep_nodes, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+         cudaMemcpy(l, b.slb, sizeof(int32_t) * keep_nodes, cudaMemcpyDeviceToDevice) != cudaSuccess)) {
+        cudaFree(r);
+        cudaFree(d);
+        cudaFree(l);
+        return FSP_ECUDA;
+    }
+    if (b.srows) cudaFree(b.srows);
+    if (b.sdep) cudaFree(b.sdep);
+    if (b.slb) cudaFree(b.slb);
+    b.srows = r;
+    b.sdep = d;
+    b.slb = l;
+    b.cap = cap;
+    return FSP_OK;
+}
+
+}  // namespace
+}  // namespace fspgb
+
+using namespace fspgb;
+
+extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int32_t ub0, int32_t expand,
+                                                  int64_t node_limit, int16_t *best_perm, int32_t *best_makespan,
+                                                  int64_t *nodes_bounded) {
+    if (!inst || expand < 0 || expand > 65536 || node_limit < 0) return FSP_EINVAL;
+    fsp_status st = check_device(inst);
+    if (st != FSP_OK) return st;
+    st = take_device_status(inst);
+    if (st != FSP_OK) return st;
+    const int n = inst->n;
+    const int K = expand ? expand : 256;
+    const int64_t max_children = (int64_t)K * n;
+    if (max_children > INT32_MAX) return FSP_EINVAL;
+
+    DevBuffers b;
+    cudaStream_t s = nullptr;
+    DevState *hst = nullptr;
+    auto fail = [&](fsp_status e) {
+        if (s) cudaStreamSynchronize(s);
+        b.release();
+        if (hst) cudaFreeHost(hst);
+        if (s) cudaStreamDestroy(s);
+        return e;
+    };
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(FSP_ECUDA);
+    if (cudaMallocHost((void **)&hst, sizeof(DevState)) != cudaSuccess) return fail(FSP_ENOMEM);
+    if (cudaMalloc((void **)&b.crows, sizeof(int16_t) * max_children * n) != cudaSuccess ||
+        cudaMalloc((void **)&b.best_row, sizeof(int16_t) * n) != cudaSuccess ||
+        cudaMalloc((void **)&b.cdep, sizeof(int32_t) * max_children) != cudaSuccess ||
+        cudaMalloc((void **)&b.clb, sizeof(int32_t) * max_children) != cudaSuccess ||
+        cudaMalloc((void **)&b.cparent, sizeof(int32_t) * max_children) != cudaSuccess ||
+        cudaMalloc((void **)&b.keep, sizeof(int32_t) * max_children) != cudaSuccess ||
+        cudaMalloc((void **)&b.offs, sizeof(int32_t) * (K + 1)) != cudaSuccess ||
+        cudaMalloc((void **)&b.soffs, sizeof(int32_t) * (K + 1)) != cudaSuccess ||
+        cudaMalloc((void **)&b.st, sizeof(DevState)) != cudaSuccess)
+        return fail(FSP_ENOMEM);
+    st = grow_stack(b, n, std::max<int64_t>(4096, max_children), 0);
+    if (st != FSP_OK) return fail(st);
+
+    // the root: empty prefix, bounded like any node
+    int64_t count = 0;
+    {
+        if (cudaMemsetAsync(b.srows, 0, sizeof(int16_t) * n, s) != cudaSuccess ||
+            cudaMemsetAsync(b.sdep, 0, sizeof(int32_t), s) != cudaSuccess)
+            return fail(FSP_ECUDA);
+        st = launch_bound(inst, b.srows, b.sdep, 1, b.slb, s, nullptr);
+        if (st != FSP_OK) return fail(st);
+        count = 1;
+        DevState init = {};
+        init.best = (int32_t)std::min<int64_t>((int64_t)ub0 + 1, INT32_MAX);
+        init.found = 0;
+        init.round_key = ~0ull;
+        *hst = init;
+        if (cudaMemcpyAsync(b.st, hst, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(FSP_ECUDA);
+    }
+    int64_t S = 1;  // stack size
+    const int make_warps = 8;
+    const size_t make_smem = (size_t)make_warps * ((n + 31) / 32) * 4;
+    while (S > 0) {
+        if (node_limit && count >= node_limit) {
+            cudaStreamSynchronize(s);
+            if (nodes_bounded) *nodes_bounded = count;
+            b.release();
+            cudaFreeHost(hst);
+            cudaStreamDestroy(s);
+            return FSP_ETIMEDOUT;
+        }
+        const int k = (int)std::min<int64_t>(K, S);
+        const int64_t top0 = S - k;
+        bnb_count_children<<<1, kScanThreads, 0, s>>>(b.sdep, b.slb, top0, k, n, b.st, b.offs);
+        bnb_make_children<<<(k + make_warps - 1) / make_warps, 32 * make_warps, make_smem, s>>>(
+            b.srows, b.sdep, top0, k, n, b.offs, b.crows, b.cdep, b.cparent);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(hst, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(FSP_ECUDA);
+        const int total = hst->total;
+        if (total == 0) {
+            S = top0;
+            continue;
+        }
+        st = launch_bound(inst, b.crows, b.cdep, total, b.clb, s, nullptr);
+        if (st != FSP_OK) return fail(st);
+        count += total;
+        // every child could survive: the stack must hold top0 + total nodes
+        st = grow_stack(b, n, top0 + total, top0);
+        if (st != FSP_OK) return fail(st);
+        const int tb = 256, gb = (total + tb - 1) / tb;
+        bnb_filter<<<gb, tb, 0, s>>>(b.clb, b.cdep, total, n, b.st, b.keep);
+        bnb_incumbent<<<1, 128, 0, s>>>(b.crows, n, b.st, b.best_row);
+        bnb_count_survivors<<<1, kScanThreads, 0, s>>>(b.offs, b.keep, k, b.st, b.soffs);
+        bnb_push<<<gb, tb, 0, s>>>(b.crows, b.cdep, b.clb, b.cparent, b.offs, b.keep, b.soffs, total, n, top0,
+                                   b.srows, b.sdep, b.slb);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(hst, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(FSP_ECUDA);
+        st = take_device_status(inst);
+        if (st != FSP_OK) return fail(st);
+        S = top0 + hst->survivors;
+    }
+    const bool found = hst->found != 0;
+    const int32_t best = hst->best;
+    if (found && best_perm &&
+        cudaMemcpy(best_perm, b.best_row, sizeof(int16_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(FSP_ECUDA);
+    if (nodes_bounded) *nodes_bounded = count;
+    b.release();
+    cudaFreeHost(hst);
+    cudaStreamDestroy(s);
+    if (!found) return FSP_ENOTFOUND;
+    if (best_makespan) *best_makespan = best;
+    return FSP_OK;
+}

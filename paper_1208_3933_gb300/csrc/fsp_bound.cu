@@ -403,7 +403,7 @@ fsp_status resolve_lockstep(const fsp_instance *inst, int64_t N, const DeviceLim
 
 fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits &d, fsp_launch_config &c) {
     if (c.warps_per_block < 0 || c.warps_per_block > 16 || c.positions_per_tile < 0 ||
-        (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 2 || c.blocks_per_sm < 0 || c.blocks_per_sm > 2)
+        (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 4 || c.blocks_per_sm < 0 || c.blocks_per_sm > 2)
         return FSP_EINVAL;
     if (!c.blocks_per_sm) c.blocks_per_sm = 1;
     const int npad = inst->npad;
@@ -415,10 +415,14 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
         size_t smem = 0;
         return lanes_layout(inst, t, &smem) == FSP_OK;
     };
-    // largest streamed tile (multiple of 4, at most npad) for W warps; 0 if none
+    // tiled modes: streamed (block-wide tile pipeline), split (prep + scan
+    // kernels) or warp (a tile pipeline per warp)
+    const int tiled = (c.staging == FSP_STAGING_SPLIT || c.staging == FSP_STAGING_WARP) ? c.staging
+                                                                                        : FSP_STAGING_STREAMED;
+    // largest record tile (multiple of 4, at most npad) for W warps; 0 if none
     auto best_chunk = [&](int W) {
         for (int ch = npad; ch >= 4; ch -= 4)
-            if (fits(W, FSP_STAGING_STREAMED, ch)) return ch;
+            if (fits(W, tiled, ch)) return ch;
         return 0;
     };
     // resident staging only on request: holding every record in shared memory
@@ -442,13 +446,13 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
         }
         return FSP_EINVAL;
     }
-    c.staging = FSP_STAGING_STREAMED;
+    c.staging = tiled;
     if (!c.warps_per_block) {
         double best = -1.0;
         int bW = 0;
         for (int W = 16 / c.blocks_per_sm; W >= 1; --W) {
             const int ch = c.positions_per_tile ? c.positions_per_tile : best_chunk(W);
-            if (ch < 4 || !fits(W, FSP_STAGING_STREAMED, ch)) continue;
+            if (ch < 4 || !fits(W, tiled, ch)) continue;
             if (!c.positions_per_tile && ch < std::min(npad, 64)) continue;
             const double batches = std::ceil((double)std::max<int64_t>(N, 1) / (32.0 * W));
             const double score = wave_efficiency(batches, (double)d.num_sms * c.blocks_per_sm) *
@@ -463,7 +467,7 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     }
     if (!c.positions_per_tile) c.positions_per_tile = best_chunk(c.warps_per_block);
     if (c.positions_per_tile < 4) return FSP_EINVAL;
-    return fits(c.warps_per_block, FSP_STAGING_STREAMED, c.positions_per_tile) ? FSP_OK : FSP_EINVAL;
+    return fits(c.warps_per_block, tiled, c.positions_per_tile) ? FSP_OK : FSP_EINVAL;
 }
 
 }  // namespace

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) 
     int2 *hcache = reinterpret_cast<int2 *>(smem + a.off_cache);
     int2 *tcache = hcache + a.m * 32;
     const unsigned char *tables = smem + a.off_tables;
-    uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * a.n;
+    uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * flag_words(a.n);
     int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
 
     // this block's share of the warp batches
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) 
         if (lane == 0) claim = atomicAdd(ctr, 1);
         const int64_t bt = b0 + __shfl_sync(kFull, claim, 0);
         if (bt >= b1) break;
-        const int64_t x = bt * 32 + lane;
+        const int64_t x = node_at(a, bt * 32 + lane);
         int bterm = 0;
         const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
         if (!ready) {
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
     uint8_t *sgp = smem + 16;
     int2 *hcache = reinterpret_cast<int2 *>(smem + a.off_cache);
     int2 *tcache = hcache + a.m * 32;
-    uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * a.n;
+    uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * flag_words(a.n);
     int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
 
     if (threadIdx.x == 0) {
@@ -155,31 +155,10 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
         if (a.ntiles == 2) tile_issue(1, 1);
     }
 
-    int *okey = reinterpret_cast<int *>(smem + a.off_order);  // [32W] sort keys
-    int *operm = okey + 32 * W;                                // [32W] batch offsets by rank
     for (int64_t bt = blockIdx.x; bt < a.num_batches; bt += gridDim.x) {
-        const int64_t base = bt * (int64_t)(32 * W);
-        // The batch's nodes in order of depth (ties by index): warp w takes
-        // ranks [32w, 32w+32), so the depth-long loops of a warp's setup run
-        // about as long as its own deepest node instead of the batch's.
-        {
-            const int64_t xi = base + threadIdx.x;
-            const int dep = xi < a.N ? __ldg(a.depths + xi) : -1;
-            const int key = ((min(max(dep, -1), a.n + 1) + 1) << 10) | (int)threadIdx.x;  // distinct keys
-            okey[threadIdx.x] = key;
-            __syncthreads();
-            int rank = 0;
-            for (int i = 0; i < 32 * W; i += 4) {
-                const int4 k4 = *reinterpret_cast<const int4 *>(okey + i);
-                rank += (k4.x < key) + (k4.y < key) + (k4.z < key) + (k4.w < key);
-            }
-            operm[rank] = threadIdx.x;
-            __syncthreads();
-        }
-        const int64_t x = base + operm[threadIdx.x];
+        const int64_t x = node_at(a, bt * (int64_t)(32 * W) + warp * 32 + lane);
         int bterm = 0;
         const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
-        prefetch_row(a, x + (int64_t)gridDim.x * (32 * W));  // a node of this block's next batch
         int lb[32];
         float uf[32];
         int ui[32];
@@ -241,7 +220,7 @@ namespace {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct LanesLayout {
-    uint32_t off_cache, off_tables, tile_stride, off_flags, off_aq, off_order;
+    uint32_t off_cache, off_tables, tile_stride, off_flags, off_aq;
     int32_t aq_stride;
     size_t total;
 };
@@ -260,10 +239,9 @@ LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident,
         L.tile_stride = (uint32_t)align_up((size_t)chunk * 32 * inst->rec_bytes, 128);
         L.off_flags = L.off_tables + 2 * L.tile_stride;
     }
-    L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)warps * inst->n * 4, 128);
+    L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)warps * flag_words(inst->n) * 4, 128);
     L.aq_stride = aq_stride_for(inst->m);
-    L.off_order = (uint32_t)align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
-    L.total = align_up(L.off_order + (size_t)warps * 32 * 4 * 2, 128);
+    L.total = align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
     return L;
 }
 
@@ -308,6 +286,8 @@ cudaError_t launch_lanes_mp(const LanesArgs &a, int mp, bool resident, int grid,
 }  // namespace
 
 fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, size_t *smem_bytes) {
+    if (c.staging == FSP_STAGING_SPLIT) return split_layout(inst, c, smem_bytes);
+    if (c.staging == FSP_STAGING_WARP) return warp_layout(inst, c, smem_bytes);
     const int W = c.warps_per_block;
     const int bps = c.blocks_per_sm ? c.blocks_per_sm : 1;
     if (W < 1 || W > 16 || bps < 1 || bps > 2 || W * bps > 16) return FSP_EINVAL;
@@ -327,6 +307,8 @@ fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, si
 
 fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
                         int32_t *out_lb, void *stream, const fsp_launch_config &cfg) {
+    if (cfg.staging == FSP_STAGING_SPLIT) return launch_split(inst, nodes, depths, N, out_lb, stream, cfg);
+    if (cfg.staging == FSP_STAGING_WARP) return launch_warp(inst, nodes, depths, N, out_lb, stream, cfg);
     size_t smem = 0;
     fsp_status st = lanes_layout(inst, cfg, &smem);
     if (st != FSP_OK) return st;
@@ -334,7 +316,7 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     const bool resident = cfg.staging == FSP_STAGING_RESIDENT;
     const int chunk = resident ? inst->npad : std::min(cfg.positions_per_tile, inst->npad);
     const LanesLayout L = lanes_layout_for(inst, W, resident, chunk);
-    LanesArgs a;
+    LanesArgs a = {};
     a.grec = static_cast<const unsigned char *>(inst->t.grec);
     a.gpairs = inst->t.gpairs;
     a.hsort = reinterpret_cast<const int2 *>(inst->t.hsort);
@@ -360,7 +342,6 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     a.tile_stride = L.tile_stride;
     a.off_flags = L.off_flags;
     a.off_aq = L.off_aq;
-    a.off_order = L.off_order;
     a.aq_stride = L.aq_stride;
     a.wait_limit = 4000000000LL;
     int grid;
@@ -376,9 +357,14 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     }
     grid = std::max(grid, 1);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t *order = nullptr;
+    st = depth_order(inst, depths, N, s, &order);
+    if (st != FSP_OK) return st;
+    a.order = order;
     const cudaError_t e = inst->compact ? launch_lanes_mp<false>(a, inst->mpad, resident, grid, 32 * W, smem, s)
                                         : launch_lanes_mp<true>(a, inst->mpad, resident, grid, 32 * W, smem, s);
-    return e == cudaSuccess ? FSP_OK : FSP_ECUDA;
+    const cudaError_t ef = order ? cudaFreeAsync(order, s) : cudaSuccess;
+    return (e == cudaSuccess && ef == cudaSuccess) ? FSP_OK : FSP_ECUDA;
 }
 
 }  // namespace fspgb

@@ -44,6 +44,8 @@
 // own value.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstddef>
 #include <cstdint>
 #include <mutex>
@@ -103,6 +105,23 @@ fsp_status launch_bound(const fsp_instance *inst, const int16_t *nodes, const in
 fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &cfg, size_t *smem_bytes);
 fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
                         int32_t *out_lb, void *stream, const fsp_launch_config &cfg);
+// The same bound as a prep kernel and a scan kernel (fsp_bound_split.cu).
+fsp_status split_layout(const fsp_instance *inst, const fsp_launch_config &cfg, size_t *smem_bytes);
+fsp_status launch_split(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
+                        int32_t *out_lb, void *stream, const fsp_launch_config &cfg);
+// The same bound with a record-tile pipeline per warp (fsp_bound_warp.cu).
+fsp_status warp_layout(const fsp_instance *inst, const fsp_launch_config &cfg, size_t *smem_bytes);
+fsp_status launch_warp(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
+                       int32_t *out_lb, void *stream, const fsp_launch_config &cfg);
+// Depth order of a pool (fsp_order.cu): *order = a device permutation slot ->
+// node, allocated from the scratch pool on stream s (free it with
+// cudaFreeAsync on s after the launch that reads it), or null (identity) for
+// pools below kDepthOrderMin nodes or instances below kDepthOrderMinJobs jobs.
+constexpr int64_t kDepthOrderMin = 8192;
+constexpr int kDepthOrderMinJobs = 64;
+fsp_status depth_order(const fsp_instance *inst, const int32_t *depths, int64_t N, cudaStream_t s, int32_t **order);
+// Per-device stream-ordered memory pool for launch scratch (keeps its memory).
+fsp_status scratch_pool(int dev, cudaMemPool_t *out);
 int max_smem_per_block(int device);
 int max_smem_per_sm(int device);
 int num_sms(int device);

@@ -17,6 +17,11 @@ namespace fspgb {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// The node bounded in slot i of a launch (slots past N map to themselves).
+__device__ __forceinline__ int64_t node_at(const LanesArgs &a, int64_t i) {
+    return (a.order && i < a.N) ? (int64_t)__ldg(a.order + i) : i;
+}
+
 // 32x32 bit-matrix transpose across a warp: on entry lane L holds row L
 // (bit b = M[L][b]); on exit lane b holds column b (bit L = M[L][b]).  Five
 // butterfly stages, each swapping the off-diagonal halves of every block.
@@ -31,33 +36,6 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
     return x;
 }
 
-// Minimum over the unscheduled jobs of one machine's head (or tail) sums for
-// the warp's 32 nodes (lane = node): `sorted` lists (job, sum) by ascending
-// sum, so the answer is the sum of the first listed job whose flag bit is
-// set.  32 list entries are examined per step, one per lane; the transposed
-// flag words give every node the lanes that hit, and the first hit's sum is
-// shuffled in.  Entries [0, 32) come from `first32` (a shared-memory copy) or
-// from `sorted`; later steps read `sorted`.  Nodes already `done` keep `res`.
-__device__ __forceinline__ void first_unscheduled_from(const int2 *__restrict__ sorted, int base, const uint32_t *F,
-                                                       int n, int lane, bool &done, int &res) {
-    for (; base < n && __any_sync(kFull, !done); base += 32) {
-        const int pos = base + lane;
-        int2 e = make_int2(0, 0);
-        uint32_t w = 0;
-        if (pos < n) {
-            e = __ldg(sorted + pos);
-            w = F[e.x];
-        }
-        const uint32_t hits = warp_transpose32(w, lane);
-        const int first = __ffs(hits) - 1;
-        const int val = __shfl_sync(kFull, e.y, first < 0 ? 0 : first);
-        if (!done && first >= 0) {
-            res = val;
-            done = true;
-        }
-    }
-}
-
 // Copies the first 32 entries of every machine's head- and tail-sorted job
 // lists into shared memory ([m][32] each; entries past n read (0,0)).
 __device__ __forceinline__ void load_sorted_heads(const LanesArgs &a, int2 *hcache, int2 *tcache) {
@@ -68,81 +46,95 @@ __device__ __forceinline__ void load_sorted_heads(const LanesArgs &a, int2 *hcac
     }
 }
 
-// L2 prefetch of a node row (the next batch's, issued during this batch's scan).
-__device__ __forceinline__ void prefetch_row(const LanesArgs &a, int64_t x) {
-    if (x >= a.N) return;
-    const char *row = reinterpret_cast<const char *>(a.nodes + x * (int64_t)a.n);
-    for (int off = 0; off < 2 * a.n; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.depths + x));
-}
-
 // Setup of node x (lane = node) for the warp's 32 nodes: the flag words F[j]
-// (bit b: job j unscheduled in the warp's node b), the lane's row
+// (bit b: job j unscheduled in the warp's node b; F holds 32 * ceil(n / 32)
+// words, which first hold the lanes' membership bitmaps), the lane's row
 // (A_k = r_k + S_k as int32, q_l as int16) and the one-machine term
 // max_{l>=1} (A_l + q_l).  Returns whether the row is valid.
 template <int MP>
 __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int lane, uint32_t *F, int32_t *myrow,
                                             int &bterm, const int2 *hcache = nullptr,
                                             const int2 *tcache = nullptr) {
-    const int n = a.n, m = a.m;
+    const int n = a.n, m = a.m, nw = (n + 31) >> 5;
     bool valid = false;
     int d = 0;
     if (x < a.N) {
         d = __ldg(a.depths + x);
         valid = (d >= 0 && d <= n);
     }
-    const uint32_t vmask = __ballot_sync(kFull, valid);
-    for (int j = lane; j < n; j += 32) F[j] = vmask;
-    __syncwarp();
-    const int16_t *row = a.nodes + x * (int64_t)n;
-    // (1) clear the prefix jobs' flag bits; a job outside [0,n) or seen twice
-    // invalidates the row (no branch on the loop's critical path)
-    {
-        const int dv = valid ? d : 0;
-        bool bad = false;
-#pragma unroll 4
-        for (int i = 0; i < dv; ++i) {
-            const int j = __ldg(row + i);
-            const bool inr = (unsigned)j < (unsigned)n;
-            const uint32_t old = atomicAnd(&F[inr ? j : 0], inr ? ~(1u << lane) : kFull);
-            bad |= !inr || !((old >> lane) & 1u);
-        }
-        valid = valid && !bad;
-    }
-    // (2) C(sigma,k) by the flow-shop recurrence, and the prefix column sums;
-    // one step is max(c + p, C_k + p), a single fused add-max
+    // (1) one pass over the prefix.  Membership: each lane marks its node's
+    // jobs in a private bitmap (word w of lane L at F[32 w + L], so the 32
+    // lanes never share a word); a job outside [0,n) or marked twice
+    // invalidates the row.  Recurrence: C(sigma,k) by the flow-shop recurrence
+    // and the prefix column sums, one step max(c + p, C_k + p) = a single
+    // fused add-max.  An invalid row still runs the loop on clamped jobs; its
+    // result is discarded.
+    for (int w = 0; w < nw; ++w) F[w * 32 + lane] = 0u;
     int C[MP], Ps[MP];
 #pragma unroll
     for (int k = 0; k < MP; ++k) {
         C[k] = 0;
         Ps[k] = 0;
     }
-    if (valid) {
-#pragma unroll 4
-        for (int i = 0; i < d; ++i) {
-            const int j = __ldg(row + i);
-            const int4 *pj = reinterpret_cast<const int4 *>(a.pp + (size_t)j * a.mpad);
-            int c = 0;
+    const int16_t *row = a.nodes + x * (int64_t)n;
+    const int dv = valid ? d : 0;
+    bool bad = false;
+    auto take = [&](int j) {
+        const bool inr = (unsigned)j < (unsigned)n;
+        const int jj = inr ? j : 0;
+        uint32_t *wp = F + (jj >> 5) * 32 + lane;
+        const uint32_t bit = 1u << (jj & 31), old = *wp;
+        bad |= !inr || (old & bit) != 0u;
+        *wp = old | bit;
+        const int4 *pj = reinterpret_cast<const int4 *>(a.pp + (size_t)jj * a.mpad);
+        int c = 0;
 #pragma unroll
-            for (int q = 0; q < MP / 4; ++q) {
-                // columns past the instance's own padding read as zeros (no branch)
-                const int4 v = 4 * q < a.mpad ? __ldg(pj + q) : make_int4(0, 0, 0, 0);
-                const int pv[4] = {v.x, v.y, v.z, v.w};
+        for (int q = 0; q < MP / 4; ++q) {
+            // columns past the instance's own padding read as zeros (no branch)
+            const int4 v = 4 * q < a.mpad ? __ldg(pj + q) : make_int4(0, 0, 0, 0);
+            const int pv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int k = 4 * q + e;
-                    c = __viaddmax_s32(c, pv[e], C[k] + pv[e]);
-                    C[k] = c;
-                    Ps[k] += pv[e];
-                }
+            for (int e = 0; e < 4; ++e) {
+                const int k = 4 * q + e;
+                c = __viaddmax_s32(c, pv[e], C[k] + pv[e]);
+                C[k] = c;
+                Ps[k] += pv[e];
             }
         }
+    };
+    int i = 0;
+    if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(a.nodes) & 7) == 0) {  // 8-byte aligned rows: four jobs per load
+        const int2 *row4 = reinterpret_cast<const int2 *>(row);
+#pragma unroll 1
+        for (; i + 4 <= dv; i += 4) {
+            const int2 v = __ldg(row4 + (i >> 2));
+            take((int)(int16_t)(v.x & 0xFFFF));
+            take(v.x >> 16);
+            take((int)(int16_t)(v.y & 0xFFFF));
+            take(v.y >> 16);
+        }
+    }
+#pragma unroll 1
+    for (; i < dv; ++i) take(__ldg(row + i));
+    valid = valid && !bad;
+    __syncwarp();
+    // (2) the flag words: transposing lane L's bitmap word w gives lane i the
+    // bits over nodes of job 32 w + i; F[j] bit b = job j unscheduled in the
+    // warp's node b (valid nodes only)
+    const uint32_t vmask = __ballot_sync(kFull, valid);
+    for (int w = 0; w < nw; ++w) {
+        const uint32_t t = warp_transpose32(F[w * 32 + lane], lane);
+        F[w * 32 + lane] = ~t & vmask;
     }
     __syncwarp();
     // (3) A_k = max(C_k, min_U head) + (ptot_k - prefix sum), q_l = min_U tail.
-    // First the 32 cheapest list entries of every machine, all independent;
-    // then, for the rare nodes whose first 32 entries are all scheduled, the
-    // rest of the list machine by machine.
+    // Each machine's (job, head) and (job, tail) lists are sorted by sum, so
+    // a minimum over U is the sum of the first listed job that is unscheduled
+    // in the node.  A round examines 32 list entries per machine, one per
+    // lane: the transposed flag words give every node the lanes that hit, and
+    // the first hit's sum is shuffled in.  Round 0 covers the 32 cheapest
+    // entries (from the shared-memory copy when given); nodes whose entries
+    // were all scheduled go on round by round.
     const bool settled = !valid || d == n;  // nothing to search for
     int16_t *qrow = reinterpret_cast<int16_t *>(myrow + m);
     uint32_t open_h = 0, open_t = 0;  // machines still searching (bit k)
@@ -167,16 +159,34 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
             qrow[k] = (int16_t)ql;
         }
     }
-    if (__any_sync(kFull, (open_h | open_t) != 0)) {
+    // later rounds: list entries [base, base + 32) of every machine some node
+    // still searches, all machines at once so their loads and transposes
+    // overlap
+    for (int base = 32; base < n; base += 32) {
+        const uint32_t any_h = __reduce_or_sync(kFull, open_h), any_t = __reduce_or_sync(kFull, open_t);
+        if ((any_h | any_t) == 0u) break;
+        const int pos = base + lane;
+        const bool inr = pos < n;
 #pragma unroll
         for (int k = 0; k < MP; ++k) {
-            if (k < m && __any_sync(kFull, ((open_h | open_t) >> k) & 1u)) {
-                bool done_h = !((open_h >> k) & 1u), done_t = !((open_t >> k) & 1u);
-                int mh = 0, ql = 0;
-                first_unscheduled_from(a.hsort + (size_t)k * n, 32, F, n, lane, done_h, mh);
-                first_unscheduled_from(a.tsort + (size_t)k * n, 32, F, n, lane, done_t, ql);
-                if ((open_h >> k) & 1u) myrow[k] = max(C[k], mh) + (__ldg(a.ptot + k) - Ps[k]);
-                if ((open_t >> k) & 1u) qrow[k] = (int16_t)ql;
+            if (k < m) {
+                const bool lh = inr && ((any_h >> k) & 1u), lt = inr && ((any_t >> k) & 1u);
+                int2 eh = make_int2(0, 0), et = make_int2(0, 0);
+                if (lh) eh = __ldg(a.hsort + (size_t)k * n + pos);
+                if (lt) et = __ldg(a.tsort + (size_t)k * n + pos);
+                const uint32_t wh = lh ? F[eh.x] : 0u, wt = lt ? F[et.x] : 0u;
+                const uint32_t hh = warp_transpose32(wh, lane), ht = warp_transpose32(wt, lane);
+                const int fh = __ffs(hh) - 1, ft = __ffs(ht) - 1;
+                const int vh = __shfl_sync(kFull, eh.y, fh < 0 ? 0 : fh);
+                const int vt = __shfl_sync(kFull, et.y, ft < 0 ? 0 : ft);
+                if (((open_h >> k) & 1u) && fh >= 0) {
+                    myrow[k] = max(C[k], vh) + (__ldg(a.ptot + k) - Ps[k]);
+                    open_h &= ~(1u << k);
+                }
+                if (((open_t >> k) & 1u) && ft >= 0) {
+                    qrow[k] = (int16_t)vt;
+                    open_t &= ~(1u << k);
+                }
             }
         }
     }

@@ -139,6 +139,7 @@ extern "C" fsp_status fsp_bound_batch_noalloc(const fsp_pool_desc *pools, int32_
         m_max = std::max(m_max, p.inst->m);
         mp = std::max(mp, p.inst->mpad);
     }
+    n_max = flag_words(n_max);  // flag words per warp
     unsigned char *scratch = nullptr;
     fsp_status st = scratch_address(dev, &scratch);
     if (st != FSP_OK) return st;

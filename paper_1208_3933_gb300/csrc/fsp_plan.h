@@ -11,6 +11,10 @@
 
 namespace fspgb {
 
+// Shared-memory words of one warp's flag array: one per job, rounded up to
+// whole 32-word blocks (the setup's membership bitmaps use them all).
+__host__ __device__ inline int flag_words(int n) { return (n + 31) & ~31; }
+
 // Arguments of one pool for the couple-lanes kernels (one per launch for the
 // single-pool kernels, one per pool in a batch plan).
 struct LanesArgs {
@@ -33,9 +37,11 @@ struct LanesArgs {
     uint32_t rec_bytes;
     uint32_t off_tables;  // records (resident: all groups; streamed: two tile buffers)
     uint32_t tile_stride;
-    uint32_t off_flags, off_aq;
+    uint32_t off_flags, off_aq;  // split scan: off_flags = the prepared-state region
     uint32_t off_cache;   // first 32 entries of each machine's head/tail-sorted list (0 = none)
-    uint32_t off_order;   // streamed kernel: a batch's depth keys and node order
+    const int32_t *order; // slot -> node (depth order), or null: slot i bounds node i
+    uint32_t *scratch;    // split kernels: prepared state, [32-node batch][sb_words]
+    int32_t sb_words;
     int32_t aq_stride;    // ints per node row (odd): A as int32 [m], then q as int16 [m]
     long long wait_limit;
 };

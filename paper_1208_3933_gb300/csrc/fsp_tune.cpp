@@ -88,16 +88,17 @@ std::vector<fsp_launch_config> candidates(const fsp_instance *inst, int64_t N) {
         c.warps_per_block = W;
         c.staging = FSP_STAGING_RESIDENT;
         add(c);
-        for (int pos : {0, 256, 128, 64}) {
-            c.staging = FSP_STAGING_STREAMED;
-            c.positions_per_tile = pos;
-            add(c);
-            if (W <= 8) {
-                fsp_launch_config c2 = c;
-                c2.blocks_per_sm = 2;
-                add(c2);
+        for (int staging : {FSP_STAGING_STREAMED, FSP_STAGING_SPLIT, FSP_STAGING_WARP})
+            for (int pos : {0, 256, 128, 64}) {
+                c.staging = staging;
+                c.positions_per_tile = pos;
+                add(c);
+                if (W <= 8) {
+                    fsp_launch_config c2 = c;
+                    c2.blocks_per_sm = 2;
+                    add(c2);
+                }
             }
-        }
     }
     for (int K : {8, 4, 2, 1})
         for (int bps : {1, 2}) {

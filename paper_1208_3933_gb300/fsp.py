@@ -50,6 +50,8 @@ FSP_KERNEL_LANES = 2
 FSP_STAGING_AUTO = 0
 FSP_STAGING_RESIDENT = 1
 FSP_STAGING_STREAMED = 2
+FSP_STAGING_SPLIT = 3
+FSP_STAGING_WARP = 4
 
 
 class fsp_launch_config(ctypes.Structure):
@@ -111,6 +113,7 @@ def load():
             "fsp_bound_pool_ex": ([vp, vp, vp, i64, vp, vp, ctypes.POINTER(fsp_launch_config)], i32),
             "fsp_bound_pool_host": ([vp, vp, vp, i64, vp, vp], i32),
             "fsp_branch_and_bound": ([vp, i32, i16p, i32p, i64p], i32),
+            "fsp_branch_and_bound_device": ([vp, i32, i32, i64, i16p, i32p, i64p], i32),
             "fsp_autotune": ([vp, vp, vp, i64, vp, vp, ctypes.c_char_p, ctypes.POINTER(fsp_launch_config),
                               ctypes.POINTER(ctypes.c_float)], i32),
             "fsp_tuned_config": ([vp, i64, ctypes.POINTER(fsp_launch_config)], i32),
@@ -311,6 +314,21 @@ def fsp_branch_and_bound(inst: Instance, ub0: int):
                                      ctypes.byref(best), ctypes.byref(nodes))
     if st not in (FSP_OK, FSP_ENOTFOUND):
         raise FspError(st, "fsp_branch_and_bound")
+    return st, int(best.value), perm, int(nodes.value)
+
+
+def fsp_branch_and_bound_device(inst: Instance, ub0: int, expand: int = 0, node_limit: int = 0):
+    """B&B with branching and elimination on the device.  Returns (status,
+    best_makespan, best_perm, nodes_bounded); status is FSP_OK,
+    FSP_ENOTFOUND or FSP_ETIMEDOUT (other failures raise)."""
+    perm = np.zeros(inst.n, np.int16)
+    best = ctypes.c_int32(0)
+    nodes = ctypes.c_int64(0)
+    st = load().fsp_branch_and_bound_device(inst.handle, int(ub0), int(expand), int(node_limit),
+                                            perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)),
+                                            ctypes.byref(best), ctypes.byref(nodes))
+    if st not in (FSP_OK, FSP_ENOTFOUND, FSP_ETIMEDOUT):
+        raise FspError(st, "fsp_branch_and_bound_device")
     return st, int(best.value), perm, int(nodes.value)
 
 

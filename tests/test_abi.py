@@ -66,6 +66,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.fsp_bound_pool_host(None, None, None, 0, None, None) == fsp.FSP_EINVAL
     assert lib.fsp_instance_query(None, None) == fsp.FSP_EINVAL
     assert lib.fsp_branch_and_bound(None, 0, None, None, None) == fsp.FSP_EINVAL
+    assert lib.fsp_branch_and_bound_device(None, 0, 0, 0, None, None, None) == fsp.FSP_EINVAL
     lib.fsp_instance_destroy(None)  # no-op
 
 

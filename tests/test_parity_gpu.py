@@ -65,13 +65,15 @@ def test_every_lockstep_shape_matches_oracle(gpu_lib, K, bps, ppt):
 
 
 @pytest.mark.parametrize("W", [1, 3, 16])
-@pytest.mark.parametrize("staging,positions", [(1, 0), (2, 0), (2, 4), (2, 12), (2, 64)])
+@pytest.mark.parametrize("staging,positions", [(1, 0), (2, 0), (2, 4), (2, 12), (2, 64), (3, 0), (3, 4), (3, 64),
+                                               (4, 0), (4, 4), (4, 12)])
 @pytest.mark.parametrize("nm", [(40, 20), (23, 9), (17, 5), (70, 12), (33, 27)])
 def test_every_lanes_shape_matches_oracle(gpu_lib, W, staging, positions, nm):
     """Couple-lanes kernel, explicit shapes: 1 to 16 warps per block; records
-    resident (warps claim batches independently) or streamed with Johnson
-    positions staged 4, 12 or 64 at a time (re-staging, ragged last chunk);
-    couple counts below, at and above one warp of 32 (m = 5, 9, 12, 20, 27)."""
+    resident (warps claim batches independently), streamed with Johnson
+    positions staged 4, 12 or 64 at a time (re-staging, ragged last chunk),
+    split into prep and scan kernels, or streamed per warp; couple counts
+    below, at and above one warp of 32 (m = 5, 9, 12, 20, 27)."""
     fsp = gpu_lib
     n, m = nm
     p, rows, depths = pool(78 + n, n, m, 2 * 32 * W * 3 + 19)
@@ -93,11 +95,17 @@ def test_wide_records_match_oracle(gpu_lib):
         got_lanes = gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=2, warps_per_block=4,
                                                                       positions_per_tile=16, staging=2))
         got_res = gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=2, warps_per_block=4, staging=1))
+        got_split = gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=2, warps_per_block=4,
+                                                                      positions_per_tile=16, staging=3))
+        got_warp = gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=2, warps_per_block=4,
+                                                                     positions_per_tile=8, staging=4))
     want = oracle_bounds(p, rows, depths)
     assert np.array_equal(got, want)
     assert np.array_equal(got_k1, want)
     assert np.array_equal(got_lanes, want)
     assert np.array_equal(got_res, want)
+    assert np.array_equal(got_split, want)
+    assert np.array_equal(got_warp, want)
 
 
 def test_pair_tiled_500x20_matches_oracle(gpu_lib):
@@ -113,14 +121,14 @@ def test_pair_tiled_500x20_matches_oracle(gpu_lib):
 def test_maximum_sizes(gpu_lib):
     """n = 1024 jobs (the largest instance) and m = 32 machines."""
     fsp = gpu_lib
-    p, rows, depths = pool(11, 1024, 4, 300)
-    with fsp.Instance(p) as inst:
-        got = gpu_bounds(fsp, inst, rows, depths)
-    assert np.array_equal(got, oracle_bounds(p, rows, depths))
-    p, rows, depths = pool(12, 30, 32, 400)
-    with fsp.Instance(p) as inst:
-        got = gpu_bounds(fsp, inst, rows, depths)
-    assert np.array_equal(got, oracle_bounds(p, rows, depths))
+    for seed, n, m, N in ((11, 1024, 4, 300), (12, 30, 32, 400)):
+        p, rows, depths = pool(seed, n, m, N)
+        with fsp.Instance(p) as inst:
+            got = gpu_bounds(fsp, inst, rows, depths)
+            others = [gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=2, staging=st)) for st in (3, 4)]
+        assert np.array_equal(got, oracle_bounds(p, rows, depths))
+        for o in others:
+            assert np.array_equal(o, got)
 
 
 def test_edge_rows(gpu_lib):
@@ -140,6 +148,9 @@ def test_edge_rows(gpu_lib):
         rows[11, :4] = [0, 1, 9, 2]      # job out of range
         with fsp.Instance(p) as inst:
             got = gpu_bounds(fsp, inst, rows, depths)
+            for staging in (2, 3, 4):
+                cfg = dict(kernel=2, warps_per_block=2, positions_per_tile=4, staging=staging)
+                assert np.array_equal(gpu_bounds(fsp, inst, rows, depths, config=cfg), got)
         want = oracle_bounds(p, rows, depths)
         assert np.array_equal(got, want)
         assert got[1] == brute.makespan(p, rows[1].tolist())
@@ -155,6 +166,11 @@ def test_empty_and_single_pools(gpu_lib):
         e = torch.empty((0, 10), dtype=torch.int16, device="cuda")
         out = fsp.fsp_bound_pool(inst, e, torch.empty(0, dtype=torch.int32, device="cuda"))
         assert out.numel() == 0
+        for staging in (3, 4):
+            cfg = dict(kernel=2, warps_per_block=4, positions_per_tile=8, staging=staging)
+            out = fsp.fsp_bound_pool(inst, e, torch.empty(0, dtype=torch.int32, device="cuda"), config=cfg)
+            assert out.numel() == 0
+            assert gpu_bounds(fsp, inst, rows, depths, config=cfg).tolist() == oracle_bounds(p, rows, depths).tolist()
 
 
 def test_host_buffer_entry_point(gpu_lib):
@@ -209,9 +225,29 @@ def test_full_size_pools_sampled(gpu_lib, name, sample):
         got = gpu_bounds(fsp, inst, w.rows, w.depths)
         other = dict(kernel=fsp.FSP_KERNEL_LOCKSTEP)
         got_other = gpu_bounds(fsp, inst, w.rows, w.depths, config=other)
+        for staging in (2, 3, 4):
+            shape = dict(kernel=2, staging=staging, warps_per_block=8, blocks_per_sm=2,
+                         positions_per_tile=16 if staging == 4 else 128)
+            assert np.array_equal(gpu_bounds(fsp, inst, w.rows, w.depths, config=shape), got)
     assert np.array_equal(got, got_other)
     idx = np.sort(np.random.default_rng(123).choice(w.N, sample, replace=False))
     idx = np.unique(np.concatenate([idx, [0, w.N - 1]]))
     want = oracle_bounds(w.p, w.rows[idx], w.depths[idx])
     assert np.array_equal(got[idx], want)
     assert (got > 0).all()
+
+
+def test_split_pool_larger_than_one_chunk(gpu_lib):
+    """The split kernels bound pools above 2^20 nodes chunk by chunk through
+    one scratch allocation: same bounds as the fused kernel, a sample checked
+    against the oracle, the ragged last chunk included."""
+    fsp = gpu_lib
+    N = (1 << 20) + 4133
+    p, rows, depths = pool(31, 12, 6, N)
+    with fsp.Instance(p) as inst:
+        split = gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=2, staging=3, warps_per_block=6))
+        fused = gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=2, staging=2, warps_per_block=6))
+    assert np.array_equal(split, fused)
+    idx = np.unique(np.concatenate([np.random.default_rng(5).choice(N, 4000, replace=False),
+                                    np.arange((1 << 20) - 40, (1 << 20) + 40), [0, N - 1]]))
+    assert np.array_equal(split[idx], oracle_bounds(p, rows[idx], depths[idx]))
