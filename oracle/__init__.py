@@ -32,6 +32,8 @@ FO_EINVAL = -1
 FO_ENOMEM = -2
 FO_EBADNODE = -4
 FO_ENOTFOUND = -6
+RELEASE_HEADS = 0  # release of k: max(C(sigma,k), min_U sum_{h<k} p_jh)
+RELEASE_EST = 1    # release of k: min_U earliest start of j on k after the prefix
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +63,12 @@ def _load():
             lib.fo_lb_pool.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i32p, i16p,
                                        i32p, ctypes.c_int64, i32p]
             lib.fo_lb_pool.restype = ctypes.c_int64
+            lib.fo_lb_ex.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i32p, i16p,
+                                     ctypes.c_int32, ctypes.c_int, i64p, i32p]
+            lib.fo_lb_ex.restype = ctypes.c_int
+            lib.fo_lb_pool_ex.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i32p, i16p,
+                                          i32p, ctypes.c_int64, ctypes.c_int, i32p]
+            lib.fo_lb_pool_ex.restype = ctypes.c_int64
             lib.fo_bnb.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int32, i16p, i32p, i64p]
             lib.fo_bnb.restype = ctypes.c_int
             _lib = lib
@@ -91,9 +99,10 @@ class Tables:
         if rc != FO_OK:
             raise RuntimeError(f"fo_tables failed: {rc}")
 
-    def lb(self, prefix, return_pairs: bool = False):
+    def lb(self, prefix, return_pairs: bool = False, release: int = 0):
         """LB of the node whose scheduled prefix is ``prefix`` (a sequence of
-        job indices).  Returns None for an invalid prefix."""
+        job indices).  Returns None for an invalid prefix.  ``release`` picks
+        the reading of RM: RELEASE_HEADS (default) or RELEASE_EST."""
         lib = _load()
         row = np.zeros(self.n, np.int16)
         d = len(prefix)
@@ -102,16 +111,17 @@ class Tables:
         row[:d] = np.asarray(prefix, dtype=np.int16)
         pairs = np.zeros(self.P, np.int64)
         out = ctypes.c_int32(0)
-        rc = lib.fo_lb(self.n, self.m, _ptr(self.p, ctypes.c_int32), _ptr(self.mm, ctypes.c_int32),
-                       _ptr(self.lag, ctypes.c_int32), _ptr(self.jm, ctypes.c_int32),
-                       _ptr(row, ctypes.c_int16), d, _ptr(pairs, ctypes.c_int64), ctypes.byref(out))
+        rc = lib.fo_lb_ex(self.n, self.m, _ptr(self.p, ctypes.c_int32), _ptr(self.mm, ctypes.c_int32),
+                          _ptr(self.lag, ctypes.c_int32), _ptr(self.jm, ctypes.c_int32),
+                          _ptr(row, ctypes.c_int16), d, int(release), _ptr(pairs, ctypes.c_int64),
+                          ctypes.byref(out))
         if rc == FO_EBADNODE:
             return None
         if rc != FO_OK:
             raise RuntimeError(f"fo_lb failed: {rc}")
         return (int(out.value), pairs) if return_pairs else int(out.value)
 
-    def lb_pool(self, rows: np.ndarray, depths: np.ndarray, threads: int = 1) -> np.ndarray:
+    def lb_pool(self, rows: np.ndarray, depths: np.ndarray, threads: int = 1, release: int = 0) -> np.ndarray:
         """Bounds a pool (rows int16 [N][n], depths int32 [N]); invalid rows
         give -1.  ``threads`` > 1 runs the single-threaded C routine on
         disjoint chunks from a thread pool (ctypes drops the GIL)."""
@@ -126,11 +136,11 @@ class Tables:
             return out
 
         def run(lo, hi):
-            rc = lib.fo_lb_pool(self.n, self.m, _ptr(self.p, ctypes.c_int32),
-                                _ptr(self.mm, ctypes.c_int32), _ptr(self.lag, ctypes.c_int32),
-                                _ptr(self.jm, ctypes.c_int32),
-                                _ptr(rows[lo:hi], ctypes.c_int16), _ptr(depths[lo:hi], ctypes.c_int32),
-                                hi - lo, _ptr(out[lo:hi], ctypes.c_int32))
+            rc = lib.fo_lb_pool_ex(self.n, self.m, _ptr(self.p, ctypes.c_int32),
+                                   _ptr(self.mm, ctypes.c_int32), _ptr(self.lag, ctypes.c_int32),
+                                   _ptr(self.jm, ctypes.c_int32),
+                                   _ptr(rows[lo:hi], ctypes.c_int16), _ptr(depths[lo:hi], ctypes.c_int32),
+                                   hi - lo, int(release), _ptr(out[lo:hi], ctypes.c_int32))
             if rc < 0:
                 raise RuntimeError(f"fo_lb_pool failed: {rc}")
 

@@ -67,6 +67,22 @@ def release_and_latency(p, prefix):
     return r, q
 
 
+def release_by_appending(p, prefix):
+    """The per-job reading of the release times: r_k = min over unscheduled j
+    of the time job j would start on machine k if it were scheduled right
+    after the prefix, C(prefix + [j], k) - p_jk; r_k = C(prefix, k) when no
+    job is left.  Written from the flow-shop recurrence, not from a formula
+    for earliest starts."""
+    n, m = len(p), len(p[0])
+    U = [j for j in range(n) if j not in set(prefix)]
+    if not U:
+        return completion_times(p, prefix, m)
+    r = []
+    for k in range(m):
+        r.append(min(completion_times(p, list(prefix) + [j], m)[k] - int(p[j][k]) for j in U))
+    return r
+
+
 def two_machine_value(p, order, k, l, rk, rl, ql):
     """The relaxed problem on couple (M_k, M_l): machines between k and l
     become a lag (sum of the job's times strictly between them); machine k is
@@ -79,16 +95,19 @@ def two_machine_value(p, order, k, l, rk, rl, ql):
     return t2 + ql
 
 
-def pair_minimum(p, prefix, k, l):
-    """Minimum of two_machine_value over every order of the unscheduled jobs."""
+def pair_minimum(p, prefix, k, l, release="heads"):
+    """Minimum of two_machine_value over every order of the unscheduled jobs;
+    release = "heads" (the default reading) or "est" (release_by_appending)."""
     n = len(p)
     r, q = release_and_latency(p, prefix)
+    if release == "est":
+        r = release_by_appending(p, prefix)
     U = [j for j in range(n) if j not in set(prefix)]
     return min(two_machine_value(p, o, k, l, r[k], r[l], q[l]) for o in itertools.permutations(U))
 
 
-def lb_by_enumeration(p, prefix):
+def lb_by_enumeration(p, prefix, release="heads"):
     """max over couples k<l of pair_minimum: the bound computed with no
     Johnson order at all."""
     m = len(p[0])
-    return max(pair_minimum(p, prefix, k, l) for k in range(m) for l in range(k + 1, m))
+    return max(pair_minimum(p, prefix, k, l, release) for k in range(m) for l in range(k + 1, m))

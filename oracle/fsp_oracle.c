@@ -25,6 +25,8 @@
  *     of sum_{h<k} p_jh) and the latency of machine l is min over unscheduled
  *     j of sum_{h>l} p_jh, both minima over the empty set being 0 (the RM and
  *     QM rows of the pseudo-code; the paper computes these minima on the CPU);
+ *     fo_lb_ex also offers the tighter per-job reading of RM, the minimum over
+ *     unscheduled j of the earliest start of j on machine k after the prefix;
  *   - LB starts at 0 (the pseudo-code's maxInteger start cannot be meant);
  *   - the couple loop, the filtered Johnson scan and the two-machine update
  *     follow the pseudo-code in its order, lines (03) to (19).
@@ -40,6 +42,10 @@
 #define FO_ENOMEM (-2)
 #define FO_EBADNODE (-4)
 #define FO_ENOTFOUND (-6)
+
+/* Release-time readings of RM (see fo_lb_ex). */
+#define FO_RELEASE_HEADS 0 /* max(C(sigma,k), min_U sum_{h<k} p_jh) */
+#define FO_RELEASE_EST 1   /* min_U earliest start of j on k after the prefix */
 
 /* Number of machine couples (k,l), k<l: m(m-1)/2 (Section II-D). */
 int fo_num_pairs(int m) { return m * (m - 1) / 2; }
@@ -106,9 +112,9 @@ int fo_tables(int n, int m, const int32_t *p, int32_t *mm, int32_t *lag, int32_t
  * appears twice.  pair_out, if not NULL, receives the value of every couple
  * (timeOnM2 after line (18) of the pseudo-code).
  */
-int fo_lb(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *lag,
-          const int32_t *jm, const int16_t *row, int32_t d, int64_t *pair_out,
-          int32_t *lb_out) {
+int fo_lb_ex(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *lag,
+             const int32_t *jm, const int16_t *row, int32_t d, int release,
+             int64_t *pair_out, int32_t *lb_out) {
     if (d < 0 || d > n) return FO_EBADNODE;
     char *sched = (char *)calloc((size_t)n, 1);
     int64_t *C = (int64_t *)calloc((size_t)m, sizeof(int64_t));
@@ -137,6 +143,27 @@ int fo_lb(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *lag,
         /* RM: release of machine k = max(C(sigma,k), min_{j in U} sum_{h<k} p_jh).
            QM: latency of machine l = min_{j in U} sum_{h>l} p_jh.  Empty U: 0. */
         int nu = n - d;
+        if (release == FO_RELEASE_EST && nu > 0) {
+            /* RM read as the earliest starting time of each unscheduled job j
+               on each machine k after the prefix (Section II-D names RM "the
+               matrix of the earliest starting times of jobs", indexed by
+               machine and job, and the pseudo-code takes its minimum over j,
+               lines (06)-(07)): est_j0 = C(sigma,0),
+               est_jk = max(C(sigma,k), est_j,k-1 + p_j,k-1);
+               release of machine k = min over U of est_jk. */
+            for (int k = 0; k < m; ++k) R[k] = -1;
+            for (int j = 0; j < n; ++j) {
+                if (sched[j]) continue;
+                int64_t est = C[0];
+                for (int k = 0; k < m; ++k) {
+                    if (k > 0) {
+                        int64_t ready = est + p[j * m + k - 1];
+                        est = C[k] > ready ? C[k] : ready;
+                    }
+                    if (R[k] < 0 || est < R[k]) R[k] = est;
+                }
+            }
+        }
         for (int k = 0; k < m; ++k) {
             int64_t mh = 0, mq = 0;
             int first = 1;
@@ -150,7 +177,7 @@ int fo_lb(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *lag,
                 first = 0;
             }
             if (nu == 0) { mh = 0; mq = 0; }
-            R[k] = C[k] > mh ? C[k] : mh;
+            if (release != FO_RELEASE_EST || nu == 0) R[k] = C[k] > mh ? C[k] : mh;
             Q[k] = mq;
         }
         /* The couple loop of the pseudo-code, lines (03)-(19). */
@@ -180,21 +207,34 @@ int fo_lb(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *lag,
     return rc;
 }
 
+/* fo_lb_ex with the release times of the default reading. */
+int fo_lb(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *lag,
+          const int32_t *jm, const int16_t *row, int32_t d, int64_t *pair_out,
+          int32_t *lb_out) {
+    return fo_lb_ex(n, m, p, mm, lag, jm, row, d, FO_RELEASE_HEADS, pair_out, lb_out);
+}
+
 /* Bounds a pool of N nodes stored as int16 rows [N][n] plus depths [N];
    invalid rows get -1.  Returns the number of invalid rows, or a negative
    error code. */
-int64_t fo_lb_pool(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *lag,
-                   const int32_t *jm, const int16_t *rows, const int32_t *depths,
-                   int64_t N, int32_t *out) {
+int64_t fo_lb_pool_ex(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *lag,
+                      const int32_t *jm, const int16_t *rows, const int32_t *depths,
+                      int64_t N, int release, int32_t *out) {
     int64_t bad = 0;
     for (int64_t x = 0; x < N; ++x) {
         int32_t v = -1;
-        int rc = fo_lb(n, m, p, mm, lag, jm, rows + (size_t)x * n, depths[x], NULL, &v);
+        int rc = fo_lb_ex(n, m, p, mm, lag, jm, rows + (size_t)x * n, depths[x], release, NULL, &v);
         if (rc == FO_ENOMEM) return FO_ENOMEM;
         if (rc != FO_OK) { v = -1; ++bad; }
         out[x] = v;
     }
     return bad;
+}
+
+int64_t fo_lb_pool(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *lag,
+                   const int32_t *jm, const int16_t *rows, const int32_t *depths,
+                   int64_t N, int32_t *out) {
+    return fo_lb_pool_ex(n, m, p, mm, lag, jm, rows, depths, N, FO_RELEASE_HEADS, out);
 }
 
 /*

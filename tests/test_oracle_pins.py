@@ -219,6 +219,54 @@ def test_trivial_ub_formula_is_not_always_valid():
     assert rc == oracle.FO_ENOTFOUND
 
 
+# ----------------------------- the per-job reading of the release times (RM)
+@pytest.mark.parametrize("seed", range(10))
+def test_est_pair_values_equal_enumerated_minimum(seed):
+    """With RM read as the earliest start of each unscheduled job on each
+    machine, every couple's value is still the minimum over all orders of the
+    relaxed two-machine problem, now released at min_j (C(prefix + [j], k) -
+    p_jk) -- the start times found by appending each job to the prefix."""
+    rng = np.random.default_rng(3000 + seed)
+    n = int(rng.integers(2, 7))
+    m = int(rng.integers(2, 6))
+    p = rand_instance(rng, n, m, [3, 9, 99][seed % 3])
+    t = oracle.Tables(p)
+    for _ in range(4):
+        prefix = rand_prefix(rng, n, int(rng.integers(0, n + 1)))
+        lb, pairs = t.lb(prefix, return_pairs=True, release=oracle.RELEASE_EST)
+        for c, (k, l) in enumerate(t.mm.tolist()):
+            assert pairs[c] == brute.pair_minimum(p, prefix, k, l, "est"), (p.tolist(), prefix, k, l)
+        assert lb == max(int(v) for v in pairs)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_est_bound_is_valid_and_at_least_the_default(seed):
+    """The per-job release times are never earlier than the default ones, so
+    the bound is at least the default bound, and it stays below the best
+    completion of the node (a valid bound); at leaves it is the makespan."""
+    rng = np.random.default_rng(4000 + seed)
+    n = int(rng.integers(2, 8))
+    m = int(rng.integers(2, 6))
+    p = rand_instance(rng, n, m)
+    t = oracle.Tables(p)
+    for d in range(n + 1):
+        prefix = rand_prefix(rng, n, d)
+        est = t.lb(prefix, release=oracle.RELEASE_EST)
+        assert t.lb(prefix) <= est <= brute.best_completion(p, prefix)
+        if d == n:
+            assert est == brute.makespan(p, prefix)
+
+
+def test_est_pool_matches_single_nodes():
+    rng = np.random.default_rng(4100)
+    p = rand_instance(rng, 9, 6)
+    rows, depths = workloads.random_pool(rng, 9, 300, max_depth=10)
+    t = oracle.Tables(p)
+    got = t.lb_pool(rows, depths, threads=3, release=oracle.RELEASE_EST)
+    want = [t.lb(rows[i, :depths[i]].tolist(), release=oracle.RELEASE_EST) for i in range(300)]
+    assert got.tolist() == [(-1 if w is None else w) for w in want]
+
+
 # ------------------------------------------------- the pins catch mistakes
 MUTANTS = {
     "dropped lag": ("for (int h = k + 1; h < l; ++h) lg += p[j * m + h];", ""),
@@ -228,6 +276,9 @@ MUTANTS = {
     "release without heads": ("R[k] = C[k] > mh ? C[k] : mh;", "R[k] = C[k];"),
     "machines swapped in update": ("t2 += p[job * m + M2];", "t2 += p[job * m + M1];"),
     "scheduled jobs not filtered": ("if (sched[job]) continue; /* line (10): only unscheduled jobs */", ""),
+    "est: machine availability ignored": ("est = C[k] > ready ? C[k] : ready;", "est = ready;"),
+    "est: time of the wrong machine": ("int64_t ready = est + p[j * m + k - 1];", "int64_t ready = est + p[j * m + k];"),
+    "est: largest start kept": ("if (R[k] < 0 || est < R[k]) R[k] = est;", "if (R[k] < 0 || est > R[k]) R[k] = est;"),
 }
 
 
@@ -240,6 +291,7 @@ def test_pins_detect_planted_mistakes(name, tmp_path):
 
     src = open(os.path.join(os.path.dirname(oracle.__file__), "fsp_oracle.c")).read()
     old, new = MUTANTS[name]
+    release = oracle.RELEASE_EST if name.startswith("est:") else oracle.RELEASE_HEADS
     assert src.count(old) == 1, name
     mut = tmp_path / "mut.c"
     mut.write_text(src.replace(old, new))
@@ -257,9 +309,9 @@ def test_pins_detect_planted_mistakes(name, tmp_path):
                       jm.ctypes.data_as(I32))
         row = np.zeros(n, np.int16); row[: len(prefix)] = prefix
         out = ctypes.c_int32(0)
-        lib.fo_lb(n, m, pc.ctypes.data_as(I32), mm.ctypes.data_as(I32), lag.ctypes.data_as(I32),
-                  jm.ctypes.data_as(I32), row.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)),
-                  len(prefix), None, ctypes.byref(out))
+        lib.fo_lb_ex(n, m, pc.ctypes.data_as(I32), mm.ctypes.data_as(I32), lag.ctypes.data_as(I32),
+                     jm.ctypes.data_as(I32), row.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)),
+                     len(prefix), release, None, ctypes.byref(out))
         return out.value
 
     rng = np.random.default_rng(99)
@@ -268,7 +320,7 @@ def test_pins_detect_planted_mistakes(name, tmp_path):
         n = int(rng.integers(2, 6)); m = int(rng.integers(2, 6))
         p = rand_instance(rng, n, m)
         prefix = rand_prefix(rng, n, int(rng.integers(0, n)))
-        if mutant_lb(p, prefix) != brute.lb_by_enumeration(p, prefix):
+        if mutant_lb(p, prefix) != brute.lb_by_enumeration(p, prefix, "est" if release else "heads"):
             caught = True
             break
     assert caught, f"mutant '{name}' survived the enumeration pin"
