@@ -62,6 +62,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def kernel_name(cfg) -> str:
+    """The dominant kernel of a launch shape (its name in ncu launch lists)."""
+    if not cfg or cfg.get("kernel") == 1:
+        return "fsp_bound_kernel (node-lockstep)"
+    return {1: "fsp_lanes_resident", 2: "fsp_lanes_streamed", 3: "fsp_lanes_scan (after fsp_lanes_prep)",
+            4: "fsp_lanes_warp"}.get(cfg.get("staging"), "fsp_lanes_streamed")
+
+
 def read_traffic(n_nodes: int):
     """DRAM bytes per launch from the committed ncu capture, if it was taken
     on the current kernel sources (else None).  The capture is a smaller pool
@@ -326,6 +334,20 @@ def rank_pool(rank: int):
     return workloads.PoolWorkload(w.name, w.n, w.m, w.seed, w.p, rows, depths)
 
 
+def host_cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, else the Arm part),
+    with the core count."""
+    name = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part") and not name:
+                name = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return f"{name or 'unknown'} x {os.cpu_count()}"
+
+
 def cpu_oracle_rate(w, seconds: float = 2.0, threads: int | None = None):
     """Times the oracle as it stands on a bounded sample of the pool, on all
     host cores (the single-threaded C routine on disjoint chunks)."""
@@ -414,6 +436,7 @@ def run_gpu(args, world, rank, local):
         time.sleep(0.3)
         barrier(world)
         torch.cuda.synchronize(dev)
+        launches0 = fsp.fsp_kernel_launches()
         region0.record(stream)
         for i in range(args.steps):
             ev[i][0].record(stream)
@@ -421,6 +444,7 @@ def run_gpu(args, world, rank, local):
                                config=cfg)
             ev[i][1].record(stream)
         region1.record(stream)
+        launches = fsp.fsp_kernel_launches() - launches0
         torch.cuda.synchronize(dev)
         barrier(world)
     region_ms = region0.elapsed_time(region1)
@@ -455,6 +479,7 @@ def run_gpu(args, world, rank, local):
     peak = alu_peak_ops(props.multi_processor_count, sm_max, ALU_LANES_PER_SM)
     achieved = ops / mean_kernel_s
     cpu_rate, cpu_sample, cpu_s, cpu_threads = cpu_oracle_rate(w, seconds=2.0)
+    cpu1_rate, cpu1_sample, cpu1_s, _ = cpu_oracle_rate(w, seconds=1.0, threads=1)
     info = inst.info()
     batched = run_batched_leg(dev) if not (args.nodes or args.no_extra) else None
     served = run_served_leg() if not (args.nodes or args.no_extra) else None
@@ -470,13 +495,19 @@ def run_gpu(args, world, rank, local):
                      "frac": achieved / peak, "traffic": read_traffic(w.N),
                      "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} int32 lanes x "
                                    f"{sm_max:.0f} MHz", "ops_per_launch": ops,
-                     "kernel_ms_mean": mean_kernel_s * 1e3},
+                     "kernel_ms_mean": mean_kernel_s * 1e3, "kernel": kernel_name(launch),
+                     "timed": "CUDA events around each step's fsp_bound_pool on its stream: the bounding "
+                              "kernel(s) of the launch shape plus, for pools of >= 8192 nodes and >= 64 jobs, the "
+                              "three small depth-order kernels"},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                          "sample": f"first {cpu_sample} nodes of the pool, plain C oracle on {cpu_threads} threads, "
-                                   f"{cpu_s:.1f} s"},
+                                   f"{cpu_s:.1f} s",
+                         "single_thread": {"value": cpu1_rate, "sample": f"first {cpu1_sample} nodes, 1 thread, "
+                                                                         f"{cpu1_s:.1f} s"},
+                         "host_cpu": host_cpu_model()},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(w.rows.nbytes + w.depths.nbytes),
                 "d2h_bytes_per_step": int(4 * w.N), "bit_exact_vs_device": ok_e2e},
-        "gpu_launches": args.steps,
+        "gpu_launches": launches,
         "clocks": clocks,
         "batched": batched,
         "served": served,

@@ -70,7 +70,7 @@ typedef struct fsp_instance_info {
     int32_t compact;        /* 1: 32-bit Johnson records, 0: 128-bit records */
     int64_t device_bytes;   /* device memory held by the instance */
     int32_t device;         /* CUDA ordinal the tables live on */
-    int32_t reserved;
+    int32_t flags;          /* FSP_INSTANCE_* options given at creation */
 } fsp_instance_info;
 
 /* Launch shape of the bounding kernel.  Zero in any field means "choose":
@@ -121,6 +121,24 @@ typedef struct fsp_launch_config {
  * FSP_ENOMEM, FSP_ECUDA.
  */
 fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m, fsp_instance **out);
+
+/* Options of fsp_instance_create_ex.
+ *   FSP_INSTANCE_RELEASE_PER_JOB  the release time of machine k (the RM row
+ *     of the figure "Pseudo-code implementing the LB function", lines
+ *     (06)-(07)) is read per job, as Section II-D names RM "the matrix of the
+ *     earliest starting times of jobs": r_k = min over unscheduled j of
+ *     est_jk, with est_j0 = C(sigma,0) and est_jk = max(C(sigma,k),
+ *     est_j,k-1 + p_j,k-1); r_k = C(sigma,k) when no job is left.  It is
+ *     never earlier than the default max(C(sigma,k), min_U sum_{h<k} p_jh),
+ *     so the bound is at least as tight, at about n' m more operations per
+ *     node.  Bounded by the couple-lanes kernels only (a node-lockstep shape
+ *     is refused with FSP_EINVAL). */
+#define FSP_INSTANCE_RELEASE_PER_JOB 0x1u
+
+/* fsp_instance_create with options (flags: FSP_INSTANCE_* bits; other bits
+ * give FSP_EINVAL).  fsp_instance_create(p, n, m, out) is flags = 0. */
+fsp_status fsp_instance_create_ex(const int32_t *p, int32_t n, int32_t m, uint32_t flags,
+                                  fsp_instance **out);
 
 /* Frees the instance and its device tables.  NULL is a no-op.  No bounding
  * call on this instance may be in flight. */
@@ -418,6 +436,12 @@ const char *fsp_status_string(fsp_status s);
 
 /* Library version as "major.minor.patch" (static string). */
 const char *fsp_version(void);
+
+/* fsp_kernel_launches -- number of CUDA kernels this library has enqueued in
+ * the process so far (every entry point counts its own launches; no compute
+ * of the method, the paper has no counterpart).  For launch accounting around
+ * a timed region. */
+int64_t fsp_kernel_launches(void);
 
 #ifdef __cplusplus
 }

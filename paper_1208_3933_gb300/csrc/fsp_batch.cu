@@ -81,6 +81,7 @@ cudaError_t launch_batch_variant(const LanesArgs *pools, const int2 *items, int6
     });
     if (attr_err != cudaSuccess) return attr_err;
     fsp_lanes_batch<MP><<<grid, threads, smem, s>>>(pools, items, nitems, counter, n_max, stride, off_aq);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -152,6 +153,7 @@ fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_p
         a.mpad = inst->mpad;
         a.rec_bytes = (uint32_t)inst->rec_bytes;
         a.aq_stride = pp.stride;
+        a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
         a.wait_limit = 4000000000LL;
         const int64_t nb = (p.N + 31) / 32;
         for (int64_t k = 0; k < nb; ++k) items.push_back(make_int2(i, (int)k));

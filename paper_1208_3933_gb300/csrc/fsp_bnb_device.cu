@@ -313,6 +313,7 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
         }
         const int k = (int)std::min<int64_t>(K, S);
         const int64_t top0 = S - k;
+        note_launches(2);
         bnb_count_children<<<1, kScanThreads, 0, s>>>(b.sdep, b.slb, top0, k, n, b.st, b.offs);
         bnb_make_children<<<(k + make_warps - 1) / make_warps, 32 * make_warps, make_smem, s>>>(
             b.srows, b.sdep, top0, k, n, b.offs, b.crows, b.cdep, b.cparent);
@@ -332,6 +333,7 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
         st = grow_stack(b, n, top0 + total, top0);
         if (st != FSP_OK) return fail(st);
         const int tb = 256, gb = (total + tb - 1) / tb;
+        note_launches(4);
         bnb_filter<<<gb, tb, 0, s>>>(b.clb, b.cdep, total, n, b.st, b.keep);
         bnb_incumbent<<<1, 128, 0, s>>>(b.crows, n, b.st, b.best_row);
         bnb_count_survivors<<<1, kScanThreads, 0, s>>>(b.offs, b.keep, k, b.st, b.soffs);

@@ -507,7 +507,10 @@ fsp_status resolve_config(const fsp_instance *inst, int64_t N, const fsp_launch_
         for (auto &e : inst->tuned)
             if (e.first == N) c = e.second;
     }
-    if (c.kernel == 0) c.kernel = inst->P >= 32 ? FSP_KERNEL_LANES : FSP_KERNEL_LOCKSTEP;
+    // per-job release times are computed by the couple-lanes setup only
+    const bool per_job = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) != 0;
+    if (per_job && c.kernel == FSP_KERNEL_LOCKSTEP) return FSP_EINVAL;
+    if (c.kernel == 0) c.kernel = (inst->P >= 32 || per_job) ? FSP_KERNEL_LANES : FSP_KERNEL_LOCKSTEP;
     fsp_status st = c.kernel == FSP_KERNEL_LANES ? resolve_lanes(inst, N, d, c) : resolve_lockstep(inst, N, d, c);
     if (st != FSP_OK) return st;
     if (c.kernel == FSP_KERNEL_LANES) {
@@ -534,6 +537,7 @@ cudaError_t launch_variant(const BoundArgs &a, int grid, size_t smem, cudaStream
     });
     if (attr_err != cudaSuccess) return attr_err;
     fsp_bound_kernel<K, WIDE><<<grid, kThreads, smem, s>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 

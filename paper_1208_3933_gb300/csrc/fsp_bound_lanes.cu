@@ -263,6 +263,7 @@ cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int grid, in
         if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP>);
     });
     if (attr_err != cudaSuccess) return attr_err;
+    note_launches(1);
     if (resident)
         fsp_lanes_resident<WIDE, MP><<<grid, threads, smem, s>>>(a);
     else
@@ -343,6 +344,7 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     a.off_flags = L.off_flags;
     a.off_aq = L.off_aq;
     a.aq_stride = L.aq_stride;
+    a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
     a.wait_limit = 4000000000LL;
     int grid;
     if (resident) {

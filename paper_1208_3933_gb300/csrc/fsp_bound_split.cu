@@ -246,6 +246,7 @@ cudaError_t launch_pair(const LanesArgs &ap, int64_t nbatch32, size_t prep_smem,
         per_sm = 1;
     }
     const int prep_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ap.num_batches, (int64_t)sms * per_sm));
+    note_launches(2);
     fsp_lanes_prep<MP><<<prep_grid, 32 * kPrepWarps, prep_smem, s>>>(ap, nbatch32);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -328,6 +329,7 @@ fsp_status launch_split(const fsp_instance *inst, const int16_t *nodes, const in
     a.ntiles = inst->G * a.nchunks;
     a.rec_bytes = (uint32_t)inst->rec_bytes;
     a.aq_stride = aq_stride_for(inst->m);
+    a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
     a.scratch = scratch;
     a.sb_words = sb;
     a.wait_limit = 4000000000LL;

@@ -184,6 +184,7 @@ cudaError_t launch_warp_variant(const LanesArgs &a, const WarpLayout &L, int gri
     std::call_once(once, [] { attr_err = set_smem_attr(fsp_lanes_warp<WIDE, MP>); });
     if (attr_err != cudaSuccess) return attr_err;
     fsp_lanes_warp<WIDE, MP><<<grid, threads, L.total, s>>>(a, L.warp_stride, L.w_off_aq, L.w_off_tiles);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -251,6 +252,7 @@ fsp_status launch_warp(const fsp_instance *inst, const int16_t *nodes, const int
     a.off_flags = L.off_warps;
     a.tile_stride = L.tile_stride;
     a.aq_stride = aq_stride_for(inst->m);
+    a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
     a.wait_limit = 4000000000LL;
     // whole blocks' worth of warps per SM; at least one batch per warp of the grid
     const int64_t per_block = W;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 
@@ -48,9 +49,15 @@ void johnson_order(int n, int m, const int32_t *p, int k, int l, std::vector<int
 }  // namespace
 
 extern "C" fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m, fsp_instance **out) {
+    return fsp_instance_create_ex(p, n, m, 0u, out);
+}
+
+extern "C" fsp_status fsp_instance_create_ex(const int32_t *p, int32_t n, int32_t m, uint32_t flags,
+                                             fsp_instance **out) {
     if (!out) return FSP_EINVAL;
     *out = nullptr;
     if (!p || n < 1 || n > FSP_MAX_JOBS || m < 2 || m > FSP_MAX_MACHINES) return FSP_EINVAL;
+    if (flags & ~(uint32_t)FSP_INSTANCE_RELEASE_PER_JOB) return FSP_EINVAL;
     int64_t total = 0;
     int32_t maxp = 0;
     for (int64_t i = 0; i < (int64_t)n * m; ++i) {
@@ -64,6 +71,7 @@ extern "C" fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m
     if (!inst) return FSP_ENOMEM;
     inst->n = n;
     inst->m = m;
+    inst->flags = flags;
     inst->P = m * (m - 1) / 2;
     inst->npad = (int32_t)align_up((size_t)n, fspgb::kRecAlign);
     inst->p.assign(p, p + (size_t)n * m);
@@ -298,7 +306,7 @@ extern "C" fsp_status fsp_instance_query(const fsp_instance *inst, fsp_instance_
     info->compact = inst->compact;
     info->device_bytes = (int64_t)inst->dev_bytes;
     info->device = inst->device;
-    info->reserved = 0;
+    info->flags = (int32_t)inst->flags;
     return FSP_OK;
 }
 
@@ -315,5 +323,13 @@ extern "C" const char *fsp_status_string(fsp_status s) {
     }
     return "unknown status";
 }
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}  // namespace
+
+void fspgb::note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+extern "C" int64_t fsp_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 extern "C" const char *fsp_version(void) { return "0.1.0"; }

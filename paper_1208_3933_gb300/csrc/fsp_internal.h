@@ -82,6 +82,7 @@ struct fsp_instance {
     int32_t compact = 1;
     int32_t device = 0;
     int32_t rec_bytes = 4;          // bytes per Johnson record
+    uint32_t flags = 0;             // FSP_INSTANCE_* options of fsp_instance_create_ex
     std::vector<int32_t> p;         // host copy [n][m]
     std::vector<uint8_t> pairs;     // host copy [P][2]
     void *dev_block = nullptr;      // owns every device table
@@ -122,6 +123,8 @@ constexpr int kDepthOrderMinJobs = 64;
 fsp_status depth_order(const fsp_instance *inst, const int32_t *depths, int64_t N, cudaStream_t s, int32_t **order);
 // Per-device stream-ordered memory pool for launch scratch (keeps its memory).
 fsp_status scratch_pool(int dev, cudaMemPool_t *out);
+// Counts kernels the library enqueues (fsp_kernel_launches).
+void note_launches(int k);
 int max_smem_per_block(int device);
 int max_smem_per_sm(int device);
 int num_sms(int device);

@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 
 #include "fsp_internal.h"
@@ -104,20 +105,66 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     };
     int i = 0;
     if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(a.nodes) & 7) == 0) {  // 8-byte aligned rows: four jobs per load
+        // the next four jobs are loaded while these four are taken
         const int2 *row4 = reinterpret_cast<const int2 *>(row);
+        int2 v = i + 4 <= dv ? __ldg(row4) : make_int2(0, 0);
 #pragma unroll 1
         for (; i + 4 <= dv; i += 4) {
-            const int2 v = __ldg(row4 + (i >> 2));
+            const int2 nv = i + 8 <= dv ? __ldg(row4 + (i >> 2) + 1) : make_int2(0, 0);
             take((int)(int16_t)(v.x & 0xFFFF));
             take(v.x >> 16);
             take((int)(int16_t)(v.y & 0xFFFF));
             take(v.y >> 16);
+            v = nv;
         }
     }
 #pragma unroll 1
     for (; i < dv; ++i) take(__ldg(row + i));
     valid = valid && !bad;
     __syncwarp();
+    // S_k = ptot_k - prefix sum of machine k, kept in the lane's row until
+    // A_k = r_k + S_k replaces it
+#pragma unroll
+    for (int k = 0; k < MP; ++k)
+        if (k < m) myrow[k] = __ldg(a.ptot + k) - Ps[k];
+    // Per-job release times (when the instance asks for them): RM of
+    // Section II-D read as the earliest start of every unscheduled job j on
+    // every machine k after the prefix, est_j0 = C_0 and
+    // est_jk = max(est_j,k-1 + p_j,k-1, C_k) (one fused add-max), and
+    // r_k = min over U of est_jk (r_k = C_k once U is empty).  The lane walks
+    // its node's unscheduled jobs in its own membership bitmap.
+    const bool per_job = a.release != 0;
+    int R[MP];
+    if (per_job) {
+#pragma unroll
+        for (int k = 0; k < MP; ++k) R[k] = C[k];
+        if (valid && d < n) {
+#pragma unroll
+            for (int k = 0; k < MP; ++k) R[k] = INT_MAX;
+            for (int w = 0; w < nw; ++w) {
+                uint32_t un = ~F[w * 32 + lane];
+                if (w == nw - 1 && (n & 31)) un &= (1u << (n & 31)) - 1u;
+                while (un) {
+                    const int j = w * 32 + __ffs(un) - 1;
+                    un &= un - 1u;
+                    const int4 *pj = reinterpret_cast<const int4 *>(a.pp + (size_t)j * a.mpad);
+                    int est = C[0], prev = 0;
+#pragma unroll
+                    for (int q = 0; q < MP / 4; ++q) {
+                        const int4 v = 4 * q < a.mpad ? __ldg(pj + q) : make_int4(0, 0, 0, 0);
+                        const int pv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int k = 4 * q + e;
+                            if (k > 0) est = __viaddmax_s32(est, prev, C[k]);
+                            R[k] = min(R[k], est);
+                            prev = pv[e];
+                        }
+                    }
+                }
+            }
+        }
+    }
     // (2) the flag words: transposing lane L's bitmap word w gives lane i the
     // bits over nodes of job 32 w + i; F[j] bit b = job j unscheduled in the
     // warp's node b (valid nodes only)
@@ -127,7 +174,8 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
         F[w * 32 + lane] = ~t & vmask;
     }
     __syncwarp();
-    // (3) A_k = max(C_k, min_U head) + (ptot_k - prefix sum), q_l = min_U tail.
+    // (3) A_k = max(C_k, min_U head) + S_k (per-job release times: r_k + S_k),
+    // q_l = min_U tail.
     // Each machine's (job, head) and (job, tail) lists are sorted by sum, so
     // a minimum over U is the sum of the first listed job that is unscheduled
     // in the node.  A round examines 32 list entries per machine, one per
@@ -142,7 +190,9 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
 #pragma unroll
     for (int k = 0; k < MP; ++k) {
         if (k < m) {
-            const bool want_h = k > 0, want_t = k < m - 1;  // heads are 0 on machine 0, tails on m-1
+            // heads are 0 on machine 0 and not needed with per-job release
+            // times; tails are 0 on machine m-1
+            const bool want_h = k > 0 && !per_job, want_t = k < m - 1;
             int2 eh = make_int2(0, 0), et = make_int2(0, 0);
             if (in && want_h) eh = hcache ? hcache[k * 32 + lane] : __ldg(a.hsort + (size_t)k * n + lane);
             if (in && want_t) et = tcache ? tcache[k * 32 + lane] : __ldg(a.tsort + (size_t)k * n + lane);
@@ -153,9 +203,11 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
             const int vt = __shfl_sync(kFull, et.y, ft < 0 ? 0 : ft);
             const int mh = (!settled && fh >= 0) ? vh : 0;
             const int ql = (!settled && ft >= 0) ? vt : 0;
-            if (want_h && !settled && fh < 0) open_h |= 1u << k;
+            if (want_h && !settled && fh < 0)
+                open_h |= 1u << k;  // A_k once a later round finds the minimum
+            else
+                myrow[k] = (per_job ? R[k] : max(C[k], mh)) + myrow[k];
             if (want_t && !settled && ft < 0) open_t |= 1u << k;
-            myrow[k] = max(C[k], mh) + (__ldg(a.ptot + k) - Ps[k]);
             qrow[k] = (int16_t)ql;
         }
     }
@@ -180,7 +232,7 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
                 const int vh = __shfl_sync(kFull, eh.y, fh < 0 ? 0 : fh);
                 const int vt = __shfl_sync(kFull, et.y, ft < 0 ? 0 : ft);
                 if (((open_h >> k) & 1u) && fh >= 0) {
-                    myrow[k] = max(C[k], vh) + (__ldg(a.ptot + k) - Ps[k]);
+                    myrow[k] = max(C[k], vh) + myrow[k];
                     open_h &= ~(1u << k);
                 }
                 if (((open_t >> k) & 1u) && ft >= 0) {

@@ -116,6 +116,7 @@ cudaError_t launch_noalloc(const unsigned char *scratch, int count, int64_t nite
         cudaFuncSetAttribute(fsp_lanes_batch_noalloc<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fsp_lanes_batch_noalloc<MP><<<grid, threads, smem, s>>>(scratch, count, nitems, n_max, stride, off_aq);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -180,6 +181,7 @@ extern "C" fsp_status fsp_bound_batch_noalloc(const fsp_pool_desc *pools, int32_
         a.mpad = inst->mpad;
         a.rec_bytes = (uint32_t)inst->rec_bytes;
         a.aq_stride = stride;
+        a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
         offs[r + 1] = offs[r] + (p.N + 31) / 32;
     }
     const int64_t nitems = offs[count];

@@ -20,7 +20,8 @@ namespace fspgb {
 namespace {
 
 constexpr int kOrderThreads = 256;
-constexpr int kOrderBlocks = 128;  // blocks of the histogram and scatter passes
+constexpr int kOrderBlocks = 48;     // blocks of the histogram and scatter passes
+constexpr int kOrderScanMax = 12000;  // bins x blocks scanned in shared memory (< 48 KB)
 
 __device__ __forceinline__ int depth_bin(int d, int n) { return min(max(d, -1), n + 1) + 1; }  // [0, n + 2]
 
@@ -40,15 +41,19 @@ __global__ void __launch_bounds__(kOrderThreads) order_hist(const int32_t *depth
 
 // Exclusive scan of hist in place, bin-major: block k's nodes of bin b start
 // after all nodes of smaller bins and of bin b in blocks before k.  One block:
-// each thread sums a contiguous segment, the 1024 sums are scanned with warp
+// hist is staged in shared memory (at most kOrderScanMax entries), each
+// thread sums a contiguous segment, the 1024 sums are scanned with warp
 // shuffles, and each thread rewrites its segment.
 __global__ void __launch_bounds__(1024) order_scan(int32_t *hist, int total) {
+    extern __shared__ int32_t sh[];
     __shared__ int32_t wsum[32];
+    for (int i = threadIdx.x; i < total; i += blockDim.x) sh[i] = hist[i];
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int seg = (total + 1023) / 1024;
     const int i0 = min(total, (int)threadIdx.x * seg), i1 = min(total, i0 + seg);
     int sum = 0;
-    for (int i = i0; i < i1; ++i) sum += hist[i];
+    for (int i = i0; i < i1; ++i) sum += sh[i];
     int incl = sum;  // inclusive scan across the warp
     for (int off = 1; off < 32; off <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, incl, off);
@@ -57,7 +62,8 @@ __global__ void __launch_bounds__(1024) order_scan(int32_t *hist, int total) {
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int w = wsum[lane], wi = w;
+        const int w = wsum[lane];
+        int wi = w;
         for (int off = 1; off < 32; off <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, wi, off);
             if (lane >= off) wi += t;
@@ -67,10 +73,12 @@ __global__ void __launch_bounds__(1024) order_scan(int32_t *hist, int total) {
     __syncthreads();
     int run = wsum[warp] + incl - sum;
     for (int i = i0; i < i1; ++i) {
-        const int v = hist[i];
-        hist[i] = run;
+        const int v = sh[i];
+        sh[i] = run;
         run += v;
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < total; i += blockDim.x) hist[i] = sh[i];
 }
 
 // Block k writes its nodes at its offsets, counting within a bin in shared
@@ -123,7 +131,8 @@ fsp_status depth_order(const fsp_instance *inst, const int32_t *depths, int64_t 
     fsp_status st = scratch_pool(inst->device, &pool);
     if (st != FSP_OK) return st;
     const int nb = inst->n + 3;
-    const int blocks = (int)std::min<int64_t>(kOrderBlocks, (N + kOrderThreads - 1) / kOrderThreads);
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>({(int64_t)kOrderBlocks, (int64_t)(kOrderScanMax / nb), (N + kOrderThreads - 1) / kOrderThreads}));
     const int64_t per = (N + blocks - 1) / blocks;
     const int total = nb * blocks;
     int32_t *buf = nullptr;
@@ -133,8 +142,9 @@ fsp_status depth_order(const fsp_instance *inst, const int32_t *depths, int64_t 
     }
     int32_t *hist = buf + N;
     const size_t hsmem = sizeof(int32_t) * nb;
+    note_launches(3);
     order_hist<<<blocks, kOrderThreads, hsmem, s>>>(depths, N, inst->n, per, hist);
-    order_scan<<<1, 1024, 0, s>>>(hist, total);
+    order_scan<<<1, 1024, sizeof(int32_t) * total, s>>>(hist, total);
     order_scatter<<<blocks, kOrderThreads, hsmem, s>>>(depths, N, inst->n, per, hist, buf);
     if (cudaGetLastError() != cudaSuccess) {
         cudaFreeAsync(buf, s);

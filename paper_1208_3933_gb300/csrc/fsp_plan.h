@@ -43,6 +43,7 @@ struct LanesArgs {
     uint32_t *scratch;    // split kernels: prepared state, [32-node batch][sb_words]
     int32_t sb_words;
     int32_t aq_stride;    // ints per node row (odd): A as int32 [m], then q as int16 [m]
+    int32_t release;      // 0: release times from the head minima; 1: per-job earliest starts
     long long wait_limit;
 };
 

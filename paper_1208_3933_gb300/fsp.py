@@ -41,8 +41,10 @@ class FspError(RuntimeError):
 class fsp_instance_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("pairs", ctypes.c_int32),
                 ("compact", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
+
+FSP_INSTANCE_RELEASE_PER_JOB = 0x1  # release times read per job (fsp_instance_create_ex)
 
 FSP_KERNEL_AUTO = 0
 FSP_KERNEL_LOCKSTEP = 1
@@ -107,6 +109,7 @@ def load():
         i64p = ctypes.POINTER(ctypes.c_int64)
         sig = {
             "fsp_instance_create": ([i32p, i32, i32, ctypes.POINTER(vp)], i32),
+            "fsp_instance_create_ex": ([i32p, i32, i32, ctypes.c_uint32, ctypes.POINTER(vp)], i32),
             "fsp_instance_destroy": ([vp], None),
             "fsp_instance_query": ([vp, ctypes.POINTER(fsp_instance_info)], i32),
             "fsp_bound_pool": ([vp, vp, vp, i64, vp, vp], i32),
@@ -136,6 +139,7 @@ def load():
             "fsp_neh": ([vp, i16p, i32p], i32),
             "fsp_status_string": ([i32], ctypes.c_char_p),
             "fsp_version": ([], ctypes.c_char_p),
+            "fsp_kernel_launches": ([], i64),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -151,6 +155,11 @@ def fsp_status_string(status: int) -> str:
 
 def fsp_version() -> str:
     return load().fsp_version().decode()
+
+
+def fsp_kernel_launches() -> int:
+    """Kernels the library has enqueued in this process so far."""
+    return int(load().fsp_kernel_launches())
 
 
 def _check(status: int, where: str):
@@ -171,16 +180,17 @@ class Instance:
     """Owns one fsp_instance (the processing times and every table of the
     bound, resident on the current CUDA device)."""
 
-    def __init__(self, p):
+    def __init__(self, p, flags: int = 0):
         lib = load()
         p = np.ascontiguousarray(np.asarray(p), dtype=np.int32)
         if p.ndim != 2:
             raise ValueError("p must be a [n][m] matrix")
         self.p = p
         self.n, self.m = int(p.shape[0]), int(p.shape[1])
+        self.flags = int(flags)
         h = ctypes.c_void_p()
-        _check(lib.fsp_instance_create(p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.n, self.m,
-                                       ctypes.byref(h)), "fsp_instance_create")
+        _check(lib.fsp_instance_create_ex(p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.n, self.m,
+                                          self.flags, ctypes.byref(h)), "fsp_instance_create_ex")
         self._h = h
 
     @property

@@ -59,6 +59,7 @@ def test_instance_create_rejects_bad_arguments_before_any_cuda_call(lib):
     big = np.full((4, 3), 2 ** 28, np.int32)  # sum >= 2^30
     assert lib.fsp_instance_create(big.ctypes.data_as(P), 4, 3, ctypes.byref(h)) == fsp.FSP_EINVAL
     assert lib.fsp_instance_create(p.ctypes.data_as(P), 4, 3, None) == fsp.FSP_EINVAL
+    assert lib.fsp_instance_create_ex(p.ctypes.data_as(P), 4, 3, 0x2, ctypes.byref(h)) == fsp.FSP_EINVAL
 
 
 def test_null_handles_are_rejected(lib):
@@ -68,6 +69,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.fsp_branch_and_bound(None, 0, None, None, None) == fsp.FSP_EINVAL
     assert lib.fsp_branch_and_bound_device(None, 0, 0, 0, None, None, None) == fsp.FSP_EINVAL
     lib.fsp_instance_destroy(None)  # no-op
+    assert lib.fsp_kernel_launches() >= 0
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
