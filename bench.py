@@ -223,6 +223,49 @@ def run_batched_leg(dev, reps: int = 5):
             "work_items": q["work_items"], "bit_exact_vs_plain": bool(same), "launch": "one CUDA-graph replay"}
 
 
+def run_bnb_leg(seeds=(200, 201, 203, 202), node_limit: int = 50_000_000, expand: int = 256):
+    """Whole searches of the serving workload (n=20, m=5), NEH upper bound:
+    the host-driven DFS (branching on the host, one device pool per
+    expansion), and the device-driven search (branching and elimination on
+    the device, `expand` parents per round) in depth-first and best-first
+    order.  Node counts, wall time and optimum checks against the optima the
+    oracle stored in tests/golden."""
+    from paper_1208_3933_gb300 import fsp, workloads
+    gpath = os.path.join(ROOT, "tests", "golden", "serving_optima.json")
+    golden = json.load(open(gpath))["results"] if os.path.exists(gpath) else {}
+    probs = dict(workloads.serving_searches())
+    out = []
+    srv = fsp.Server()
+    for seed in seeds:
+        p = probs[seed]
+        rec = golden.get(str(seed)) or {}
+        with fsp.Instance(p) as inst:
+            neh_ms = fsp.fsp_neh(inst)[0]
+            row = {"seed": seed, "n": int(p.shape[0]), "m": int(p.shape[1]), "ub0_neh": int(neh_ms),
+                   "optimum_stored": rec.get("opt")}
+            runs = [("host_dfs", lambda: fsp.fsp_branch_and_bound(inst, neh_ms)),
+                    ("device_dfs", lambda: fsp.fsp_branch_and_bound_device(inst, neh_ms, expand=expand,
+                                                                           node_limit=node_limit)),
+                    ("device_best_first", lambda: fsp.fsp_branch_and_bound_device(
+                        inst, neh_ms, expand=expand, node_limit=node_limit, selection=fsp.FSP_SELECT_BEST_FIRST)),
+                    ("server_8_searchers", lambda: srv.solve(inst, neh_ms, searchers=8, expand=64,
+                                                             node_limit=node_limit)[:4])]
+            for name, fn in runs:
+                if name in ("host_dfs", "server_8_searchers") and seed == 202:
+                    continue  # 12 M nodes through host-built pools: minutes
+                t0 = time.perf_counter()
+                st, best, _, nodes = fn()
+                dt = time.perf_counter() - t0
+                # status FSP_ENOTFOUND: NEH was optimal (nothing strictly better exists)
+                found = best if st == fsp.FSP_OK else (neh_ms if st == fsp.FSP_ENOTFOUND else None)
+                row[name] = {"status": int(st), "optimum": found, "nodes": int(nodes), "seconds": dt,
+                             "nodes_per_s": nodes / dt if dt > 0 else None,
+                             "matches_stored": (found == rec.get("opt")) if rec.get("opt") is not None else None}
+        out.append(row)
+    srv.close()
+    return out
+
+
 def run_served_leg(node_limit: int = 2_000_000, expand: int = 128, seconds: float = 40.0):
     """The serving loop: 32 DFS searches (n=20, m=5 for seeds 200-215 and
     m=10 for 216-231, NEH upper bound, node limit per search) plus 16 streams
@@ -483,6 +526,7 @@ def run_gpu(args, world, rank, local):
     info = inst.info()
     batched = run_batched_leg(dev) if not (args.nodes or args.no_extra) else None
     served = run_served_leg() if not (args.nodes or args.no_extra) else None
+    bnb = run_bnb_leg() if not (args.nodes or args.no_extra) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": region_ms_max / args.steps, "higher_is_better": True,
@@ -511,6 +555,7 @@ def run_gpu(args, world, rank, local):
         "clocks": clocks,
         "batched": batched,
         "served": served,
+        "bnb_searches": bnb,
     }
     print(json.dumps(line), flush=True)
     inst.close()

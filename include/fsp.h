@@ -226,6 +226,14 @@ fsp_status fsp_branch_and_bound(const fsp_instance *inst, int32_t ub0, int16_t *
  *                  (with expand = 1 the exploration order is the same, up to
  *                  when a leaf updates UB: at generation, not when popped);
  *   expand         parents per round, 0..65536 (0 = 256);
+ *   selection      FSP_SELECT_DEPTH_FIRST: the parents are the top of the
+ *                  stack (the paper's configurations); FSP_SELECT_BEST_FIRST:
+ *                  the `expand` open nodes of smallest LB, deeper first among
+ *                  equal bounds (the paper's own GPU B&B selects best-first,
+ *                  Section IV), found by binning the key (LB, -depth) of the
+ *                  open nodes between the root's bound and UB (4096 bins; on
+ *                  a wider range nodes within a bin tie arbitrarily) and
+ *                  swapped to the top of the stack before the round;
  *   node_limit     0 = none; otherwise the search stops with FSP_ETIMEDOUT
  *                  once that many bounds were evaluated (nodes_bounded is
  *                  still written).
@@ -234,8 +242,10 @@ fsp_status fsp_branch_and_bound(const fsp_instance *inst, int32_t ub0, int16_t *
  * Errors: FSP_EINVAL, FSP_ENOMEM, FSP_ECUDA, FSP_EBADNODE, FSP_ENOTFOUND,
  * FSP_ETIMEDOUT.
  */
+#define FSP_SELECT_DEPTH_FIRST 0
+#define FSP_SELECT_BEST_FIRST 1
 fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int32_t ub0, int32_t expand,
-                                       int64_t node_limit, int16_t *best_perm,
+                                       int32_t selection, int64_t node_limit, int16_t *best_perm,
                                        int32_t *best_makespan, int64_t *nodes_bounded);
 
 /*
@@ -404,6 +414,25 @@ fsp_status fsp_neh(const fsp_instance *inst, int16_t *perm, int32_t *makespan);
 fsp_status fsp_server_search(fsp_server *srv, const fsp_instance *inst, int32_t ub0, int32_t expand,
                              int64_t node_limit, int16_t *best_perm, int32_t *best_makespan,
                              int64_t *nodes_bounded);
+
+/*
+ * fsp_server_solve -- one problem solved by `searchers` cooperating
+ * depth-first searches over the server (the multi-search extension the paper
+ * names as future work, on one GPU).  Each searcher runs fsp_server_search's
+ * step on its own stack; all share one incumbent, so a schedule found by one
+ * prunes every stack at once; a searcher whose stack is empty steals the
+ * bottom half (the shallowest nodes) of the fullest stack.  The search ends
+ * when every stack is empty and no searcher has a pool in flight.  The
+ * optimum equals fsp_branch_and_bound's; node counts vary from run to run
+ * (the interleaving of the searchers is not fixed).
+ *   searchers  1..256 host threads; expand  nodes expanded per request;
+ *   node_limit, best_perm, best_makespan, nodes_bounded  as fsp_server_search;
+ *   steals     host (or NULL): number of steals.
+ * Synchronous.  Errors as fsp_server_search.
+ */
+fsp_status fsp_server_solve(fsp_server *srv, const fsp_instance *inst, int32_t ub0, int32_t searchers,
+                            int32_t expand, int64_t node_limit, int16_t *best_perm,
+                            int32_t *best_makespan, int64_t *nodes_bounded, int64_t *steals);
 
 /* Largest number of pools fsp_bound_batch_noalloc accepts in one call. */
 #define FSP_NOALLOC_MAX_POOLS 64

@@ -193,15 +193,99 @@ __global__ void bnb_push(const int16_t *crows, const int32_t *cdep, const int32_
     slb[dst] = lb;
 }
 
+// ---- best-first selection: bring the k open nodes of smallest bound to the
+// top of the stack (positions [S - k, S)), so that the round expands them;
+// among equal bounds the deeper node first (the usual tie-break, which dives
+// to leaves instead of widening a plateau of equal bounds).  The key
+// (lb - lo) * (n + 1) + (n - d) is binned relative to the root's bound (bounds
+// never decrease along a branch): bin = min(key >> shift, nbins - 1).
+constexpr int kBestBins = 4096;
+
+struct BestState {
+    int32_t tb;        // threshold bin: every node in a lower bin is selected
+    int32_t need_tb;   // how many nodes of bin tb are selected
+    int32_t taken_tb;  // bin-tb nodes taken so far
+    int32_t n_out;     // selected nodes below the top region
+    int32_t n_in;      // unselected nodes inside the top region
+};
+
+__device__ __forceinline__ int best_bin(int32_t lb, int32_t d, int n, int32_t lo, int shift) {
+    const int64_t key = (int64_t)(lb < lo ? 0 : lb - lo) * (n + 1) + (n - d);
+    const int64_t b = key >> shift;
+    return (int)(b < kBestBins - 1 ? b : kBestBins - 1);
+}
+
+__global__ void bnb_best_hist(const int32_t *slb, const int32_t *sdep, int64_t S, int n, int32_t lo, int shift,
+                              int32_t *hist) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hist[best_bin(slb[i], sdep[i], n, lo, shift)], 1);
+}
+
+// one block: the first bin at which the cumulative count reaches k
+__global__ void __launch_bounds__(kScanThreads) bnb_best_threshold(int32_t *hist, int k, BestState *bs) {
+    block_exclusive_scan(kBestBins, [&](int i) { return hist[i]; }, hist);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBestBins; i += blockDim.x) {
+        const int before = hist[i], upto = i + 1 < kBestBins ? hist[i + 1] : hist[kBestBins];
+        if (before < k && upto >= k) {
+            bs->tb = i;
+            bs->need_tb = k - before;
+        }
+    }
+    if (threadIdx.x == 0) {
+        bs->taken_tb = 0;
+        bs->n_out = 0;
+        bs->n_in = 0;
+    }
+}
+
+__global__ void bnb_best_mark(const int32_t *slb, const int32_t *sdep, int64_t S, int n, int k, int32_t lo,
+                              int shift, BestState *bs, int64_t *out_list, int64_t *in_list) {
+    const int64_t top0 = S - k;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = best_bin(slb[i], sdep[i], n, lo, shift);
+        bool sel = b < bs->tb;
+        if (b == bs->tb) sel = atomicAdd(&bs->taken_tb, 1) < bs->need_tb;
+        if (sel && i < top0) out_list[atomicAdd(&bs->n_out, 1)] = i;
+        if (!sel && i >= top0) in_list[atomicAdd(&bs->n_in, 1)] = i;
+    }
+}
+
+// swaps the t-th selected node below the top with the t-th unselected one in
+// it (the two lists have the same length); one warp per pair
+__global__ void bnb_best_swap(int16_t *srows, int32_t *sdep, int32_t *slb, int n, const BestState *bs,
+                              const int64_t *out_list, const int64_t *in_list) {
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= bs->n_out) return;
+    const int64_t a = out_list[t], b = in_list[t];
+    for (int i = lane; i < n; i += 32) {
+        const int16_t x = srows[a * n + i];
+        srows[a * n + i] = srows[b * n + i];
+        srows[b * n + i] = x;
+    }
+    if (lane == 0) {
+        const int32_t d = sdep[a], l = slb[a];
+        sdep[a] = sdep[b];
+        slb[a] = slb[b];
+        sdep[b] = d;
+        slb[b] = l;
+    }
+}
+
 struct DevBuffers {
     int16_t *srows = nullptr, *crows = nullptr, *best_row = nullptr;
     int32_t *sdep = nullptr, *slb = nullptr, *cdep = nullptr, *clb = nullptr, *cparent = nullptr;
     int32_t *offs = nullptr, *keep = nullptr, *soffs = nullptr;
     DevState *st = nullptr;
+    int32_t *hist = nullptr;                    // best-first: bins
+    BestState *bs = nullptr;                    // best-first: threshold and list lengths
+    int64_t *out_list = nullptr, *in_list = nullptr;  // best-first: swap pairs (expand each)
     int64_t cap = 0;
     void release() {
         for (void *p : {(void *)srows, (void *)crows, (void *)best_row, (void *)sdep, (void *)slb, (void *)cdep,
-                        (void *)clb, (void *)cparent, (void *)offs, (void *)keep, (void *)soffs, (void *)st})
+                        (void *)clb, (void *)cparent, (void *)offs, (void *)keep, (void *)soffs, (void *)st,
+                        (void *)hist, (void *)bs, (void *)out_list, (void *)in_list})
             if (p) cudaFree(p);
     }
 };
@@ -244,9 +328,11 @@ fsp_status grow_stack(DevBuffers &b, int n, int64_t need, int64_t keep_nodes) {
 using namespace fspgb;
 
 extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int32_t ub0, int32_t expand,
-                                                  int64_t node_limit, int16_t *best_perm, int32_t *best_makespan,
-                                                  int64_t *nodes_bounded) {
+                                                  int32_t selection, int64_t node_limit, int16_t *best_perm,
+                                                  int32_t *best_makespan, int64_t *nodes_bounded) {
     if (!inst || expand < 0 || expand > 65536 || node_limit < 0) return FSP_EINVAL;
+    if (selection != FSP_SELECT_DEPTH_FIRST && selection != FSP_SELECT_BEST_FIRST) return FSP_EINVAL;
+    const bool best_first = selection == FSP_SELECT_BEST_FIRST;
     fsp_status st = check_device(inst);
     if (st != FSP_OK) return st;
     st = take_device_status(inst);
@@ -278,11 +364,17 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
         cudaMalloc((void **)&b.soffs, sizeof(int32_t) * (K + 1)) != cudaSuccess ||
         cudaMalloc((void **)&b.st, sizeof(DevState)) != cudaSuccess)
         return fail(FSP_ENOMEM);
+    if (best_first && (cudaMalloc((void **)&b.hist, sizeof(int32_t) * (kBestBins + 1)) != cudaSuccess ||
+                       cudaMalloc((void **)&b.bs, sizeof(BestState)) != cudaSuccess ||
+                       cudaMalloc((void **)&b.out_list, sizeof(int64_t) * K) != cudaSuccess ||
+                       cudaMalloc((void **)&b.in_list, sizeof(int64_t) * K) != cudaSuccess))
+        return fail(FSP_ENOMEM);
     st = grow_stack(b, n, std::max<int64_t>(4096, max_children), 0);
     if (st != FSP_OK) return fail(st);
 
     // the root: empty prefix, bounded like any node
     int64_t count = 0;
+    int32_t root_lb = 0;  // bounds never decrease along a branch: the floor of every bin
     {
         if (cudaMemsetAsync(b.srows, 0, sizeof(int16_t) * n, s) != cudaSuccess ||
             cudaMemsetAsync(b.sdep, 0, sizeof(int32_t), s) != cudaSuccess)
@@ -290,6 +382,8 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
         st = launch_bound(inst, b.srows, b.sdep, 1, b.slb, s, nullptr);
         if (st != FSP_OK) return fail(st);
         count = 1;
+        if (cudaMemcpyAsync(&root_lb, b.slb, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return fail(FSP_ECUDA);
         DevState init = {};
         init.best = (int32_t)std::min<int64_t>((int64_t)ub0 + 1, INT32_MAX);
         init.found = 0;
@@ -313,6 +407,20 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
         }
         const int k = (int)std::min<int64_t>(K, S);
         const int64_t top0 = S - k;
+        if (best_first && k < S) {
+            // bins of the keys from the root bound to the incumbent; coarser
+            // when the range is wide
+            int shift = 0;
+            const int64_t span = (int64_t)std::max(hst->best - root_lb, 1) * (n + 1);
+            while ((span >> shift) >= kBestBins) ++shift;
+            const int g = (int)std::min<int64_t>((S + 255) / 256, 1024);
+            note_launches(4);
+            if (cudaMemsetAsync(b.hist, 0, sizeof(int32_t) * (kBestBins + 1), s) != cudaSuccess) return fail(FSP_ECUDA);
+            bnb_best_hist<<<g, 256, 0, s>>>(b.slb, b.sdep, S, n, root_lb, shift, b.hist);
+            bnb_best_threshold<<<1, kScanThreads, 0, s>>>(b.hist, k, b.bs);
+            bnb_best_mark<<<g, 256, 0, s>>>(b.slb, b.sdep, S, n, k, root_lb, shift, b.bs, b.out_list, b.in_list);
+            bnb_best_swap<<<(k + 7) / 8, 256, 0, s>>>(b.srows, b.sdep, b.slb, n, b.bs, b.out_list, b.in_list);
+        }
         note_launches(2);
         bnb_count_children<<<1, kScanThreads, 0, s>>>(b.sdep, b.slb, top0, k, n, b.st, b.offs);
         bnb_make_children<<<(k + make_warps - 1) / make_warps, 32 * make_warps, make_smem, s>>>(

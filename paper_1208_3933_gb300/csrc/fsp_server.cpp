@@ -25,6 +25,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <iterator>
 #include <map>
 #include <mutex>
 #include <new>
@@ -651,4 +652,232 @@ extern "C" fsp_status fsp_server_search(fsp_server *srv, const fsp_instance *ins
     }
     if (cut) return FSP_ETIMEDOUT;
     return found ? FSP_OK : FSP_ENOTFOUND;
+}
+
+// ---------------------------------------------------------------------------
+// fsp_server_solve: cooperating depth-first searchers over one server.
+//
+// One problem, `searchers` host threads.  Each keeps its own stack of open
+// nodes and runs the served search's step (pop up to `expand` live nodes,
+// submit all their children as one pool, keep the children below UB) against
+// a shared incumbent, so an improvement found by one searcher prunes all of
+// them at once.  A searcher whose stack runs dry steals half of the fullest
+// stack from its bottom -- the shallowest open nodes, whose subtrees are the
+// largest.  The search ends when every stack is empty and no searcher holds
+// parents in flight.
+namespace {
+
+struct Solve {
+    const fsp_instance *inst;
+    fsp_server *srv;
+    int n, expand, searchers;
+    int64_t node_limit;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<std::vector<SNode>> stacks;
+    int busy = 0;                 // searchers holding popped parents
+    bool stop = false;            // node limit reached or an error
+    fsp_status err = FSP_OK;
+    std::atomic<int64_t> ub{0};   // prune iff LB >= ub
+    std::atomic<int64_t> count{0};
+    bool found = false, cut = false;
+    std::vector<int16_t> best;
+    int64_t steals = 0;
+};
+
+// Takes up to `expand` live nodes for searcher w (its own top, else half of
+// the fullest stack's bottom); false when the search is over.
+bool take_parents(Solve &S, int w, std::vector<SNode> &parents) {
+    std::unique_lock<std::mutex> lk(S.mu);
+    for (;;) {
+        if (S.stop) return false;
+        auto &mine = S.stacks[w];
+        if (mine.empty()) {
+            int victim = -1;
+            size_t most = 0;
+            for (int v = 0; v < S.searchers; ++v)
+                if (v != w && S.stacks[v].size() > most) {
+                    most = S.stacks[v].size();
+                    victim = v;
+                }
+            if (victim >= 0) {
+                auto &vs = S.stacks[victim];
+                const size_t take = std::max<size_t>(1, vs.size() / 2);
+                // the bottom `take` nodes, kept in stack order
+                mine.insert(mine.end(), std::make_move_iterator(vs.begin()),
+                            std::make_move_iterator(vs.begin() + (ptrdiff_t)take));
+                vs.erase(vs.begin(), vs.begin() + (ptrdiff_t)take);
+                ++S.steals;
+            }
+        }
+        const int64_t UB = S.ub.load();
+        while (!mine.empty() && (int)parents.size() < S.expand) {
+            SNode nd = std::move(mine.back());
+            mine.pop_back();
+            if (nd.lb < UB) parents.push_back(std::move(nd));
+        }
+        if (!parents.empty()) {
+            ++S.busy;
+            return true;
+        }
+        if (S.busy == 0) {  // nothing open anywhere and nothing in flight: done
+            S.stop = true;
+            S.cv.notify_all();
+            return false;
+        }
+        S.cv.wait_for(lk, std::chrono::milliseconds(50));
+    }
+}
+
+void searcher_main(Solve &S, int w) {
+    const int n = S.n;
+    const size_t cap = (size_t)S.expand * n;
+    int16_t *h_rows = nullptr;
+    int32_t *h_dep = nullptr, *h_out = nullptr;
+    auto fail = [&](fsp_status e) {
+        std::lock_guard<std::mutex> g(S.mu);
+        if (S.err == FSP_OK) S.err = e;
+        S.stop = true;
+        S.cv.notify_all();
+    };
+    if (cudaMallocHost((void **)&h_rows, sizeof(int16_t) * cap * n) != cudaSuccess ||
+        cudaMallocHost((void **)&h_dep, sizeof(int32_t) * cap) != cudaSuccess ||
+        cudaMallocHost((void **)&h_out, sizeof(int32_t) * cap) != cudaSuccess) {
+        if (h_rows) cudaFreeHost(h_rows);
+        if (h_dep) cudaFreeHost(h_dep);
+        fail(FSP_ENOMEM);
+        return;
+    }
+    std::vector<SNode> parents;
+    std::vector<int> first(S.expand + 1);
+    std::vector<char> used(n);
+    struct Kid {
+        int32_t lb, job;
+    };
+    std::vector<Kid> kids;
+    std::vector<SNode> pushed;
+    while (take_parents(S, w, parents)) {
+        // branching: all children of the popped parents form one pool
+        int64_t cnt = 0;
+        for (size_t p = 0; p < parents.size(); ++p) {
+            first[p] = (int)cnt;
+            const SNode &nd = parents[p];
+            std::fill(used.begin(), used.end(), 0);
+            for (int i = 0; i < nd.d; ++i) used[nd.row[i]] = 1;
+            for (int j = 0; j < n; ++j) {
+                if (used[j]) continue;
+                int16_t *r = h_rows + (size_t)cnt * n;
+                std::memcpy(r, nd.row.data(), sizeof(int16_t) * nd.d);
+                std::memset(r + nd.d, 0, sizeof(int16_t) * (n - nd.d));
+                r[nd.d] = (int16_t)j;
+                h_dep[cnt] = nd.d + 1;
+                ++cnt;
+            }
+        }
+        first[parents.size()] = (int)cnt;
+        fsp_request *req = nullptr;
+        fsp_status st = fsp_server_submit(S.srv, S.inst, h_rows, h_dep, cnt, h_out, &req);
+        if (st == FSP_OK) {
+            st = fsp_request_wait(req, 600000000LL);  // ten minutes: a stuck server ends the search
+            if (st == FSP_ETIMEDOUT) fsp_request_cancel(req);
+            fsp_request_release(req);
+        }
+        for (int64_t i = 0; st == FSP_OK && i < cnt; ++i)
+            if (h_out[i] == FSP_LB_INVALID) st = FSP_EBADNODE;
+        if (st != FSP_OK) {
+            fail(st);
+            std::lock_guard<std::mutex> g(S.mu);
+            --S.busy;
+            break;
+        }
+        const int64_t total = S.count.fetch_add(cnt) + cnt;
+        // leaves: the shared incumbent
+        for (int64_t i = 0; i < cnt; ++i)
+            if (h_dep[i] == n && h_out[i] < S.ub.load()) {
+                std::lock_guard<std::mutex> g(S.mu);
+                if (h_out[i] < S.ub.load()) {
+                    S.ub.store(h_out[i]);
+                    S.found = true;
+                    std::memcpy(S.best.data(), h_rows + (size_t)i * n, sizeof(int16_t) * n);
+                }
+            }
+        // elimination and depth-first order, as in the served search
+        const int64_t UB = S.ub.load();
+        pushed.clear();
+        for (int p = (int)parents.size() - 1; p >= 0; --p) {
+            const SNode &nd = parents[p];
+            if (nd.d + 1 == n) continue;
+            kids.clear();
+            for (int i = first[p]; i < first[p + 1]; ++i)
+                if (h_out[i] < UB) kids.push_back(Kid{h_out[i], h_rows[(size_t)i * n + nd.d]});
+            std::sort(kids.begin(), kids.end(),
+                      [](const Kid &x, const Kid &y) { return x.lb != y.lb ? x.lb < y.lb : x.job < y.job; });
+            for (int t = (int)kids.size() - 1; t >= 0; --t) {
+                SNode c{kids[t].lb, nd.d + 1, nd.row};
+                c.row[nd.d] = (int16_t)kids[t].job;
+                pushed.push_back(std::move(c));
+            }
+        }
+        parents.clear();
+        {
+            std::lock_guard<std::mutex> g(S.mu);
+            auto &mine = S.stacks[w];
+            mine.insert(mine.end(), std::make_move_iterator(pushed.begin()), std::make_move_iterator(pushed.end()));
+            --S.busy;
+            if (S.node_limit && total >= S.node_limit) {
+                S.cut = true;
+                S.stop = true;
+            }
+            S.cv.notify_all();
+        }
+    }
+    cudaFreeHost(h_rows);
+    cudaFreeHost(h_dep);
+    cudaFreeHost(h_out);
+}
+
+}  // namespace
+
+extern "C" fsp_status fsp_server_solve(fsp_server *srv, const fsp_instance *inst, int32_t ub0, int32_t searchers,
+                                       int32_t expand, int64_t node_limit, int16_t *best_perm,
+                                       int32_t *best_makespan, int64_t *nodes_bounded, int64_t *steals) {
+    if (!srv || !inst || searchers < 1 || searchers > 256 || expand < 1 || node_limit < 0) return FSP_EINVAL;
+    Solve S;
+    S.inst = inst;
+    S.srv = srv;
+    S.n = inst->n;
+    S.expand = expand;
+    S.searchers = searchers;
+    S.node_limit = node_limit;
+    S.stacks.resize(searchers);
+    S.best.assign(inst->n, 0);
+    S.ub.store((int64_t)ub0 + 1);
+    // the root, bounded through the server like every other pool
+    {
+        std::vector<int16_t> row(inst->n, 0);
+        int32_t dep = 0, lb = 0;
+        fsp_request *req = nullptr;
+        fsp_status st = fsp_server_submit(srv, inst, row.data(), &dep, 1, &lb, &req);
+        if (st != FSP_OK) return st;
+        st = fsp_request_wait(req, 600000000LL);
+        if (st == FSP_ETIMEDOUT) fsp_request_cancel(req);
+        fsp_request_release(req);
+        if (st != FSP_OK) return st;
+        if (lb == FSP_LB_INVALID) return FSP_EBADNODE;
+        S.count = 1;
+        if (lb < S.ub.load()) S.stacks[0].push_back(SNode{lb, 0, row});
+    }
+    std::vector<std::thread> threads;
+    threads.reserve(searchers);
+    for (int w = 0; w < searchers; ++w) threads.emplace_back(searcher_main, std::ref(S), w);
+    for (auto &t : threads) t.join();
+    if (nodes_bounded) *nodes_bounded = S.count.load();
+    if (steals) *steals = S.steals;
+    if (S.err != FSP_OK) return S.err;
+    if (S.found) {
+        if (best_makespan) *best_makespan = (int32_t)S.ub.load();
+        if (best_perm) std::memcpy(best_perm, S.best.data(), sizeof(int16_t) * inst->n);
+    }
+    if (S.cut) return FSP_ETIMEDOUT;
+    return S.found ? FSP_OK : FSP_ENOTFOUND;
 }

@@ -116,7 +116,7 @@ def load():
             "fsp_bound_pool_ex": ([vp, vp, vp, i64, vp, vp, ctypes.POINTER(fsp_launch_config)], i32),
             "fsp_bound_pool_host": ([vp, vp, vp, i64, vp, vp], i32),
             "fsp_branch_and_bound": ([vp, i32, i16p, i32p, i64p], i32),
-            "fsp_branch_and_bound_device": ([vp, i32, i32, i64, i16p, i32p, i64p], i32),
+            "fsp_branch_and_bound_device": ([vp, i32, i32, i32, i64, i16p, i32p, i64p], i32),
             "fsp_autotune": ([vp, vp, vp, i64, vp, vp, ctypes.c_char_p, ctypes.POINTER(fsp_launch_config),
                               ctypes.POINTER(ctypes.c_float)], i32),
             "fsp_tuned_config": ([vp, i64, ctypes.POINTER(fsp_launch_config)], i32),
@@ -136,6 +136,7 @@ def load():
             "fsp_server_shutdown": ([vp], i32),
             "fsp_server_destroy": ([vp], None),
             "fsp_server_search": ([vp, vp, i32, i32, i64, i16p, i32p, i64p], i32),
+            "fsp_server_solve": ([vp, vp, i32, i32, i32, i64, i16p, i32p, i64p, i64p], i32),
             "fsp_neh": ([vp, i16p, i32p], i32),
             "fsp_status_string": ([i32], ctypes.c_char_p),
             "fsp_version": ([], ctypes.c_char_p),
@@ -327,14 +328,19 @@ def fsp_branch_and_bound(inst: Instance, ub0: int):
     return st, int(best.value), perm, int(nodes.value)
 
 
-def fsp_branch_and_bound_device(inst: Instance, ub0: int, expand: int = 0, node_limit: int = 0):
+FSP_SELECT_DEPTH_FIRST = 0
+FSP_SELECT_BEST_FIRST = 1
+
+
+def fsp_branch_and_bound_device(inst: Instance, ub0: int, expand: int = 0, node_limit: int = 0,
+                                selection: int = FSP_SELECT_DEPTH_FIRST):
     """B&B with branching and elimination on the device.  Returns (status,
     best_makespan, best_perm, nodes_bounded); status is FSP_OK,
     FSP_ENOTFOUND or FSP_ETIMEDOUT (other failures raise)."""
     perm = np.zeros(inst.n, np.int16)
     best = ctypes.c_int32(0)
     nodes = ctypes.c_int64(0)
-    st = load().fsp_branch_and_bound_device(inst.handle, int(ub0), int(expand), int(node_limit),
+    st = load().fsp_branch_and_bound_device(inst.handle, int(ub0), int(expand), int(selection), int(node_limit),
                                             perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)),
                                             ctypes.byref(best), ctypes.byref(nodes))
     if st not in (FSP_OK, FSP_ENOTFOUND, FSP_ETIMEDOUT):
@@ -491,6 +497,20 @@ class Server:
         if st not in (FSP_OK, FSP_ENOTFOUND, FSP_ETIMEDOUT):
             raise FspError(st, "fsp_server_search")
         return st, int(best.value), perm, int(nodes.value)
+
+    def solve(self, inst: Instance, ub0: int, searchers: int = 8, expand: int = 64, node_limit: int = 0):
+        """fsp_server_solve: (status, best_makespan, best_perm, nodes_bounded,
+        steals) of `searchers` cooperating searches sharing one incumbent."""
+        perm = np.zeros(inst.n, np.int16)
+        best = ctypes.c_int32(0)
+        nodes = ctypes.c_int64(0)
+        steals = ctypes.c_int64(0)
+        st = load().fsp_server_solve(self._h, inst.handle, int(ub0), int(searchers), int(expand), int(node_limit),
+                                     perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), ctypes.byref(best),
+                                     ctypes.byref(nodes), ctypes.byref(steals))
+        if st not in (FSP_OK, FSP_ENOTFOUND, FSP_ETIMEDOUT):
+            raise FspError(st, "fsp_server_solve")
+        return st, int(best.value), perm, int(nodes.value), int(steals.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -67,9 +67,10 @@ def test_null_handles_are_rejected(lib):
     assert lib.fsp_bound_pool_host(None, None, None, 0, None, None) == fsp.FSP_EINVAL
     assert lib.fsp_instance_query(None, None) == fsp.FSP_EINVAL
     assert lib.fsp_branch_and_bound(None, 0, None, None, None) == fsp.FSP_EINVAL
-    assert lib.fsp_branch_and_bound_device(None, 0, 0, 0, None, None, None) == fsp.FSP_EINVAL
+    assert lib.fsp_branch_and_bound_device(None, 0, 0, 0, 0, None, None, None) == fsp.FSP_EINVAL
     lib.fsp_instance_destroy(None)  # no-op
     assert lib.fsp_kernel_launches() >= 0
+    assert lib.fsp_server_solve(None, None, 0, 1, 1, 0, None, None, None, None) == fsp.FSP_EINVAL
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

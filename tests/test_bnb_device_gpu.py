@@ -89,3 +89,39 @@ def test_serving_searches_reach_the_stored_optimum(gpu_lib, seed):
         st, best, perm, _ = fsp.fsp_branch_and_bound_device(inst, rec["neh"], expand=256)
     assert st == fsp.FSP_OK and best == rec["opt"]
     assert brute.makespan(p, perm.tolist()) == best
+
+
+@pytest.mark.parametrize("expand", [1, 5, 128])
+def test_best_first_reaches_the_optimum(gpu_lib, expand):
+    """Best-first selection (the k open nodes of smallest bound per round):
+    same optimum as brute force / the oracle, on small and 12-job instances."""
+    fsp = gpu_lib
+    p = workloads.small_bnb_instance()
+    ub0 = max(workloads.trivial_ub(p), brute.makespan(p, range(8)))
+    with fsp.Instance(p) as inst:
+        st, best, perm, _ = fsp.fsp_branch_and_bound_device(inst, ub0, expand=expand,
+                                                            selection=fsp.FSP_SELECT_BEST_FIRST)
+    assert st == fsp.FSP_OK and best == 630 and brute.makespan(p, perm.tolist()) == 630
+    p = np.random.default_rng(200).integers(1, 100, (12, 5), dtype=np.int32)
+    ub0 = brute.makespan(p, range(12))
+    _, obest, _, _ = oracle.branch_and_bound(p, ub0)
+    with fsp.Instance(p) as inst:
+        st, best, perm, _ = fsp.fsp_branch_and_bound_device(inst, ub0, expand=expand,
+                                                            selection=fsp.FSP_SELECT_BEST_FIRST)
+    assert st == fsp.FSP_OK and best == obest and brute.makespan(p, perm.tolist()) == best
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_best_first_random_instances(gpu_lib, seed):
+    fsp = gpu_lib
+    rng = np.random.default_rng(950 + seed)
+    n = int(rng.integers(1, 9))
+    m = int(rng.integers(2, 7))
+    p = rng.integers(1, 100, (n, m), dtype=np.int32)
+    with fsp.Instance(p) as inst:
+        st, best, perm, _ = fsp.fsp_branch_and_bound_device(inst, brute.makespan(p, range(n)), expand=3,
+                                                            selection=fsp.FSP_SELECT_BEST_FIRST)
+        st2, _, _, _ = fsp.fsp_branch_and_bound_device(inst, brute.optimum(p)[0] - 1, expand=3,
+                                                       selection=fsp.FSP_SELECT_BEST_FIRST)
+    assert st == fsp.FSP_OK and best == brute.optimum(p)[0]
+    assert st2 == fsp.FSP_ENOTFOUND

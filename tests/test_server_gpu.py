@@ -154,3 +154,33 @@ def test_concurrent_served_searches(gpu_lib):
         assert srv.stats()["mean_pools_per_batch"] >= 1.0
     for inst in insts.values():
         inst.close()
+
+
+@pytest.mark.parametrize("searchers", [1, 3, 8])
+def test_cooperating_searchers_reach_the_optimum(gpu_lib, searchers):
+    """fsp_server_solve: several searchers with one shared incumbent and work
+    stealing reach the optimum the oracle stored (20x5 serving searches, NEH
+    start) and brute force on the 8x5 instance; below the optimum nothing is
+    found; a node limit cuts the search."""
+    import json
+    import os
+    fsp = gpu_lib
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "serving_optima.json")))["results"]
+    probs = dict(workloads.serving_searches())
+    from oracle import brute
+    with fsp.Server() as srv:
+        for seed in (200, 201, 203):
+            rec = golden[str(seed)]
+            with fsp.Instance(probs[seed]) as inst:
+                st, best, perm, nodes, _ = srv.solve(inst, rec["neh"], searchers=searchers, expand=32)
+                assert st == fsp.FSP_OK and best == rec["opt"], (seed, best, rec["opt"])
+                assert brute.makespan(probs[seed], perm.tolist()) == best
+                assert nodes >= 1
+        p = workloads.small_bnb_instance()
+        with fsp.Instance(p) as inst:
+            st, best, perm, _, _ = srv.solve(inst, 10 ** 6, searchers=searchers, expand=4)
+            assert st == fsp.FSP_OK and best == 630 == brute.makespan(p, perm.tolist())
+            st, _, _, _, _ = srv.solve(inst, 629, searchers=searchers, expand=4)
+            assert st == fsp.FSP_ENOTFOUND
+            st, _, _, nodes, _ = srv.solve(inst, 10 ** 6, searchers=searchers, expand=1, node_limit=20)
+            assert st in (fsp.FSP_ETIMEDOUT, fsp.FSP_OK) and nodes >= 1
