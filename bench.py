@@ -388,6 +388,8 @@ def host_cpu_model() -> str:
                 name = line.split(":", 1)[1].strip()
     except OSError:
         pass
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+    name = arm_parts.get(name.lower(), name)
     return f"{name or 'unknown'} x {os.cpu_count()}"
 
 
