@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(512, 1)
             float u[32];
 #pragma unroll
             for (int b = 0; b < 32; ++b) u[b] = 0.f;
-            const uint32_t *R = reinterpret_cast<const uint32_t *>(a.grec) + (size_t)g * npad * 32 + lane;
+            const uint2 *R = reinterpret_cast<const uint2 *>(a.grec) + (size_t)g * npad * 32 + lane;
 #pragma unroll 4
             for (int i = 0; i < npad; ++i) {
                 lanes_step(__ldg(R + i * 32), F, u);
@@ -151,7 +151,7 @@ fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_p
         a.G = inst->G;
         a.npad = inst->npad;
         a.mpad = inst->mpad;
-        a.rec_bytes = (uint32_t)inst->rec_bytes;
+        a.rec_bytes = (uint32_t)inst->grec_bytes;
         a.aq_stride = pp.stride;
         a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
         a.wait_limit = 4000000000LL;

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) 
                 float u[32];
 #pragma unroll
                 for (int b = 0; b < 32; ++b) u[b] = 0.f;
-                scan_compact(reinterpret_cast<const uint32_t *>(tables + g * group_bytes) + lane, a.npad, F, u);
+                scan_compact(reinterpret_cast<const uint2 *>(tables + g * group_bytes) + lane, a.npad, F, u);
                 couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, u, lb);
             } else {
                 int u[32];
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
             }
             const int npos = min(a.chunk, a.npad - ch * a.chunk);
             if (!WIDE)
-                scan_compact(reinterpret_cast<const uint32_t *>(tb) + lane, npos, F, uf);
+                scan_compact(reinterpret_cast<const uint2 *>(tb) + lane, npos, F, uf);
             else
                 scan_wide(reinterpret_cast<const int4 *>(tb) + lane, npos, F, ui);
             if (ch == a.nchunks - 1) {
@@ -231,12 +231,12 @@ LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident,
     LanesLayout L;
     L.off_cache = (uint32_t)align_up(16 + (size_t)inst->G * 64, 128);
     L.off_tables = (uint32_t)align_up(L.off_cache + (size_t)inst->m * 32 * 8 * 2, 128);
-    const size_t group_bytes = (size_t)inst->npad * 32 * inst->rec_bytes;
+    const size_t group_bytes = (size_t)inst->npad * 32 * inst->grec_bytes;
     if (resident) {
         L.tile_stride = (uint32_t)group_bytes;
         L.off_flags = (uint32_t)align_up(L.off_tables + group_bytes * inst->G, 128);
     } else {
-        L.tile_stride = (uint32_t)align_up((size_t)chunk * 32 * inst->rec_bytes, 128);
+        L.tile_stride = (uint32_t)align_up((size_t)chunk * 32 * inst->grec_bytes, 128);
         L.off_flags = L.off_tables + 2 * L.tile_stride;
     }
     L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)warps * flag_words(inst->n) * 4, 128);
@@ -301,7 +301,7 @@ fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, si
                                               (size_t)max_smem_per_sm(inst->device) / 2 - 1024);
     if (L.total > budget) return FSP_EINVAL;
     // the resident copy completes on one mbarrier: its byte count must fit the transaction counter
-    if (resident && (size_t)inst->npad * 32 * inst->rec_bytes * inst->G >= (1u << 20)) return FSP_EINVAL;
+    if (resident && (size_t)inst->npad * 32 * inst->grec_bytes * inst->G >= (1u << 20)) return FSP_EINVAL;
     *smem_bytes = L.total;
     return FSP_OK;
 }
@@ -337,7 +337,7 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     a.chunk = chunk;
     a.nchunks = (inst->npad + chunk - 1) / chunk;
     a.ntiles = inst->G * a.nchunks;
-    a.rec_bytes = (uint32_t)inst->rec_bytes;
+    a.rec_bytes = (uint32_t)inst->grec_bytes;
     a.off_cache = L.off_cache;
     a.off_tables = L.off_tables;
     a.tile_stride = L.tile_stride;

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_scan(const LanesArgs a) {
             }
             const int npos = min(a.chunk, a.npad - ch * a.chunk);
             if (!WIDE)
-                scan_compact(reinterpret_cast<const uint32_t *>(tb) + lane, npos, F, uf);
+                scan_compact(reinterpret_cast<const uint2 *>(tb) + lane, npos, F, uf);
             else
                 scan_wide(reinterpret_cast<const int4 *>(tb) + lane, npos, F, ui);
             if (ch == a.nchunks - 1) {
@@ -212,7 +212,7 @@ struct ScanLayout {
 ScanLayout scan_layout_for(const fsp_instance *inst, int warps, int chunk) {
     ScanLayout L;
     L.off_tables = (uint32_t)align_up(32 + (size_t)inst->G * 64, 128);
-    L.tile_stride = (uint32_t)align_up((size_t)chunk * 32 * inst->rec_bytes, 128);
+    L.tile_stride = (uint32_t)align_up((size_t)chunk * 32 * inst->grec_bytes, 128);
     L.off_prep = (uint32_t)align_up(L.off_tables + 2 * (size_t)L.tile_stride, 128);
     L.total = align_up(L.off_prep + (size_t)warps * sb_words_for(inst) * 4, 128);
     return L;
@@ -327,7 +327,7 @@ fsp_status launch_split(const fsp_instance *inst, const int16_t *nodes, const in
     a.chunk = chunk;
     a.nchunks = (inst->npad + chunk - 1) / chunk;
     a.ntiles = inst->G * a.nchunks;
-    a.rec_bytes = (uint32_t)inst->rec_bytes;
+    a.rec_bytes = (uint32_t)inst->grec_bytes;
     a.aq_stride = aq_stride_for(inst->m);
     a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
     a.scratch = scratch;

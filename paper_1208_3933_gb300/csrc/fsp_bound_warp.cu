@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_warp(const LanesArgs a, uint
             }
             const int npos = min(a.chunk, a.npad - ch * a.chunk);
             if (!WIDE)
-                scan_compact(reinterpret_cast<const uint32_t *>(tb) + lane, npos, F, uf);
+                scan_compact(reinterpret_cast<const uint2 *>(tb) + lane, npos, F, uf);
             else
                 scan_wide(reinterpret_cast<const int4 *>(tb) + lane, npos, F, ui);
             if (ch == a.nchunks - 1) {
@@ -161,7 +161,7 @@ WarpLayout warp_layout_for(const fsp_instance *inst, int warps, int chunk) {
     WarpLayout L;
     L.off_cache = (uint32_t)align_up(16 + (size_t)inst->G * 64, 128);
     L.off_warps = (uint32_t)align_up(L.off_cache + (size_t)inst->m * 32 * 8 * 2, 128);
-    L.tile_stride = (uint32_t)align_up((size_t)chunk * 32 * inst->rec_bytes, 128);
+    L.tile_stride = (uint32_t)align_up((size_t)chunk * 32 * inst->grec_bytes, 128);
     L.w_off_aq = (uint32_t)align_up(128 + (size_t)flag_words(inst->n) * 4, 128);
     L.w_off_tiles = (uint32_t)align_up(L.w_off_aq + (size_t)32 * aq_stride_for(inst->m) * 4, 128);
     L.warp_stride = (uint32_t)align_up(L.w_off_tiles + (size_t)kWarpBufs * L.tile_stride, 128);
@@ -247,7 +247,7 @@ fsp_status launch_warp(const fsp_instance *inst, const int16_t *nodes, const int
     a.chunk = chunk;
     a.nchunks = (inst->npad + chunk - 1) / chunk;
     a.ntiles = inst->G * a.nchunks;
-    a.rec_bytes = (uint32_t)inst->rec_bytes;
+    a.rec_bytes = (uint32_t)inst->grec_bytes;
     a.off_cache = L.off_cache;
     a.off_flags = L.off_warps;
     a.tile_stride = L.tile_stride;

@@ -99,6 +99,7 @@ extern "C" fsp_status fsp_instance_create_ex(const int32_t *p, int32_t n, int32_
     }
     inst->compact = (n <= 1024 && maxs < 8192 && maxp < 256) ? 1 : 0;
     inst->rec_bytes = inst->compact ? 4 : 16;
+    inst->grec_bytes = inst->compact ? 8 : 16;
 
     std::vector<uint32_t> rec_c;
     std::vector<int32_t> rec_w;
@@ -130,12 +131,11 @@ extern "C" fsp_status fsp_instance_create_ex(const int32_t *p, int32_t n, int32_
     // Couple-lanes layout: couple c in group c/32, lane c%32, position-major.
     inst->G = (P + 31) / 32;
     const int G = inst->G;
-    std::vector<uint32_t> grec_c;
+    std::vector<uint32_t> grec_c;  // two words per record
     std::vector<int32_t> grec_w;
     // empty couples and padding positions hold the no-op record s = 0, delta = 0
-    const uint32_t kLanesNoop = 256u << 13;
     if (inst->compact)
-        grec_c.assign((size_t)G * npad * 32, kLanesNoop);
+        grec_c.assign((size_t)G * npad * 32 * 2, 0u);
     else
         grec_w.assign((size_t)G * npad * 32 * 4, 0);
     for (int c = 0; c < P; ++c) {
@@ -143,11 +143,18 @@ extern "C" fsp_status fsp_instance_create_ex(const int32_t *p, int32_t n, int32_
         for (int i = 0; i < npad; ++i) {
             const size_t dst = ((size_t)g * npad + i) * 32 + lane;
             if (inst->compact) {
-                // couple-lanes encoding: s bits 0..12, delta+256 bits 13..21, job bits 22..31
+                // couple-lanes encoding: word 0 = the bits of float(s) with the
+                // job in its lowest 10 mantissa bits (s < 2^13 leaves the lowest
+                // 11 bits zero), word 1 = the bits of float(delta)
                 const uint32_t r = rec_c[(size_t)c * npad + i];
                 const uint32_t j = r & 1023u, sv = (r >> 10) & 8191u;
                 const int32_t dv = (int32_t)r >> 23;
-                grec_c[dst] = sv | ((uint32_t)(dv + 256) << 13) | (j << 22);
+                const float sf = (float)sv, df = (float)dv;
+                uint32_t sb, db;
+                std::memcpy(&sb, &sf, 4);
+                std::memcpy(&db, &df, 4);
+                grec_c[2 * dst] = sb | j;
+                grec_c[2 * dst + 1] = db;
             }
             else
                 for (int f = 0; f < 4; ++f) grec_w[dst * 4 + f] = rec_w[((size_t)c * npad + i) * 4 + f];
@@ -218,7 +225,7 @@ extern "C" fsp_status fsp_instance_create_ex(const int32_t *p, int32_t n, int32_
     const size_t off_head = align_up(off_p + sizeof(int32_t) * n * m, 256);
     const size_t off_tail = align_up(off_head + sizeof(int32_t) * n * m, 256);
     const size_t off_ptm = align_up(off_tail + sizeof(int32_t) * n * m, 256);
-    const size_t grec_sz = (size_t)G * npad * 32 * inst->rec_bytes;
+    const size_t grec_sz = (size_t)G * npad * 32 * inst->grec_bytes;
     const size_t off_grec = align_up(off_ptm + sizeof(int32_t) * n * m, 256);
     const size_t off_gpairs = align_up(off_grec + grec_sz, 256);
     const size_t off_hsort = align_up(off_gpairs + gpairs.size(), 256);

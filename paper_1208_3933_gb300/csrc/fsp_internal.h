@@ -31,12 +31,11 @@
 //   bits  0..9   j
 //   bits 10..22  s
 //   bits 23..31  delta (two's complement)
-// The couple-lanes copy (grec) packs the same fields so that each becomes an
-// fp32 value with one bitwise op and one add:
-//   bits  0..12  s            -> float(0x4B000000 | s) - 2^23
-//   bits 13..21  delta + 256  -> float(0x44800000 | those bits) - 1280
-//   bits 22..31  j
-// and its no-op record (padding, empty couples) is s = 0, delta = 0.
+// The couple-lanes copy (grec) stores each compact record as two words the
+// scan uses directly: word 0 = the bits of float(s) with j in its lowest 10
+// mantissa bits (s < 2^13 leaves at least 11 of them zero, so the job adds
+// less than 1/2 to s), word 1 = the bits of float(delta); the no-op record
+// (padding, empty couples) is (0, 0).
 // Wide record: int4 {j, s, delta, 0}.
 // Padding entries and empty couples are all-zero records: for any u >= 0,
 // max(u + 0, 0) = u, so they never change the result, and an empty couple
@@ -81,7 +80,8 @@ struct fsp_instance {
     int32_t mpad = 0;               // m rounded up to 8, 12, 16, 20, 24 or 32
     int32_t compact = 1;
     int32_t device = 0;
-    int32_t rec_bytes = 4;          // bytes per Johnson record
+    int32_t rec_bytes = 4;          // bytes per Johnson record (lockstep layout)
+    int32_t grec_bytes = 8;         // bytes per couple-lanes record
     uint32_t flags = 0;             // FSP_INSTANCE_* options of fsp_instance_create_ex
     std::vector<int32_t> p;         // host copy [n][m]
     std::vector<uint8_t> pairs;     // host copy [P][2]

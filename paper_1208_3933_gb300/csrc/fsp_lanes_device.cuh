@@ -248,23 +248,25 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     return valid;
 }
 
-// One slack update of the 32 nodes for a couple-lanes record r (32-bit
-// encoding of fsp_internal.h): s and delta become exact floats by OR-ing an
-// exponent into their bit fields (s < 2^13 below the 2^23 exponent, delta+256
-// < 2^9 below the 2^10 exponent), then u_b = max(u_b + delta, s) for every
-// node b whose flag bit for job r>>22 is set.
-__device__ __forceinline__ void lanes_step(uint32_t r, const uint32_t *F, float (&u)[32]) {
-    const uint32_t fw = F[r >> 22];
-    const float sf = __int_as_float((r & 0x1FFFu) | 0x4B000000u) - 8388608.0f;
-    const float df = __int_as_float((r & 0x3FE000u) | 0x44800000u) - 1280.0f;
+// One slack update of the 32 nodes for a couple-lanes record r (the
+// two-word encoding of fsp_internal.h): r.x is float(s) carrying the job in
+// its lowest 10 mantissa bits, r.y is float(delta); then u_b = max(u_b +
+// delta, s) for every node b whose flag bit for that job is set.  The job
+// bits add less than 1/2 to s, and a max never adds them up (only delta,
+// exact, is added), so every u_b is its integer value plus a fraction below
+// 1: the integer parts follow the integer recurrence exactly and the
+// epilogue truncates.
+__device__ __forceinline__ void lanes_step(uint2 r, const uint32_t *F, float (&u)[32]) {
+    const uint32_t fw = F[r.x & 1023u];
+    const float sf = __uint_as_float(r.x), df = __uint_as_float(r.y);
 #pragma unroll
     for (int b = 0; b < 32; ++b)
         if ((fw >> b) & 1u) u[b] = fmaxf(u[b] + df, sf);
 }
 
 // One couple group's scan over positions [0, npos) of a record tile (lane =
-// couple): fp32 slack for 32-bit records, int32 for 128-bit records.
-__device__ __forceinline__ void scan_compact(const uint32_t *R, int npos, const uint32_t *F, float (&u)[32]) {
+// couple): fp32 slack for two-word records, int32 for 128-bit records.
+__device__ __forceinline__ void scan_compact(const uint2 *R, int npos, const uint32_t *F, float (&u)[32]) {
 #pragma unroll 2
     for (int i = 0; i < npos; ++i) lanes_step(R[i * 32], F, u);
 }

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(512, 1)
             float u[32];
 #pragma unroll
             for (int b = 0; b < 32; ++b) u[b] = 0.f;
-            const uint32_t *R = reinterpret_cast<const uint32_t *>(a.grec) + (size_t)g * a.npad * 32 + lane;
+            const uint2 *R = reinterpret_cast<const uint2 *>(a.grec) + (size_t)g * a.npad * 32 + lane;
 #pragma unroll 4
             for (int i = 0; i < a.npad; ++i) {
                 lanes_step(__ldg(R + i * 32), F, u);
@@ -179,7 +179,7 @@ extern "C" fsp_status fsp_bound_batch_noalloc(const fsp_pool_desc *pools, int32_
         a.G = inst->G;
         a.npad = inst->npad;
         a.mpad = inst->mpad;
-        a.rec_bytes = (uint32_t)inst->rec_bytes;
+        a.rec_bytes = (uint32_t)inst->grec_bytes;
         a.aq_stride = stride;
         a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
         offs[r + 1] = offs[r] + (p.N + 31) / 32;

@@ -89,7 +89,7 @@ std::vector<fsp_launch_config> candidates(const fsp_instance *inst, int64_t N) {
         c.staging = FSP_STAGING_RESIDENT;
         add(c);
         for (int staging : {FSP_STAGING_STREAMED, FSP_STAGING_SPLIT, FSP_STAGING_WARP})
-            for (int pos : {0, 256, 128, 64}) {
+            for (int pos : {0, 256, 128, 96, 64}) {
                 c.staging = staging;
                 c.positions_per_tile = pos;
                 add(c);
