@@ -253,3 +253,41 @@ def test_split_pool_larger_than_one_chunk(gpu_lib):
     idx = np.unique(np.concatenate([np.random.default_rng(5).choice(N, 4000, replace=False),
                                     np.arange((1 << 20) - 40, (1 << 20) + 40), [0, N - 1]]))
     assert np.array_equal(split[idx], oracle_bounds(p, rows[idx], depths[idx]))
+
+
+def test_depth_ordered_pools_with_invalid_and_extreme_depths(gpu_lib):
+    """Pools at and just above the size where the library bounds them in
+    depth order (8,192 nodes, n >= 64 jobs), with invalid depths (-1, n + 1)
+    and every depth from 0 to n mixed in; every bound lands at its node."""
+    fsp = gpu_lib
+    rng = np.random.default_rng(77)
+    n, m = 64, 6
+    p = rng.integers(1, 100, (n, m), dtype=np.int32)
+    with fsp.Instance(p) as inst:
+        for N in (8191, 8192, 8193, 20000):
+            rows, depths = workloads.random_pool(rng, n, N, max_depth=n + 1)
+            depths[rng.choice(N, 50, replace=False)] = -1
+            depths[rng.choice(N, 50, replace=False)] = n + 1
+            depths[:n + 1] = np.arange(n + 1)
+            got = gpu_bounds(fsp, inst, rows, depths)
+            assert np.array_equal(got, oracle_bounds(p, rows, depths)), N
+            assert (got[(depths < 0) | (depths > n)] == fsp.FSP_LB_INVALID).all()
+
+
+def test_host_entry_point_mixed_pinned_and_pageable(gpu_lib):
+    """fsp_bound_pool_host reads page-locked buffers in place and stages the
+    rest; a mix of the two (pinned rows, pageable depths) takes the staged
+    path; both give the oracle's bounds."""
+    import torch
+    fsp = gpu_lib
+    w = workloads.named_pool("pool_200x20", N=9000)
+    want = oracle_bounds(w.p, w.rows, w.depths)
+    with fsp.Instance(w.p) as inst:
+        pr = torch.from_numpy(w.rows).pin_memory()
+        po = torch.empty(w.N, dtype=torch.int32).pin_memory()
+        fsp.fsp_bound_pool_host(inst, pr, w.depths, po)
+        assert np.array_equal(po.numpy(), want)
+        pd = torch.from_numpy(w.depths).pin_memory()
+        po.zero_()
+        fsp.fsp_bound_pool_host(inst, pr, pd, po)
+        assert np.array_equal(po.numpy(), want)

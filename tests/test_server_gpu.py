@@ -184,3 +184,25 @@ def test_cooperating_searchers_reach_the_optimum(gpu_lib, searchers):
             assert st == fsp.FSP_ENOTFOUND
             st, _, _, nodes, _ = srv.solve(inst, 10 ** 6, searchers=searchers, expand=1, node_limit=20)
             assert st in (fsp.FSP_ETIMEDOUT, fsp.FSP_OK) and nodes >= 1
+
+
+def test_server_with_per_job_release_instances(gpu_lib):
+    """Pools of instances created with per-job release times go through the
+    server's batched launches with the same bounds as alone."""
+    fsp = gpu_lib
+    rng = np.random.default_rng(31)
+    insts = []
+    for n, m, N in [(30, 10, 2000), (60, 20, 1500)]:
+        p = rng.integers(1, 100, (n, m), dtype=np.int32)
+        rows, depths = workloads.random_pool(rng, n, N, max_depth=n + 1)
+        insts.append((fsp.Instance(p, flags=fsp.FSP_INSTANCE_RELEASE_PER_JOB), p, rows, depths))
+    with fsp.Server(slots=2) as srv:
+        for inst, p, rows, depths in insts:
+            req = srv.submit(inst, rows, depths)
+            assert req.wait(60_000_000) == fsp.FSP_OK
+            want = oracle.Tables(p).lb_pool(rows, depths, threads=8, release=oracle.RELEASE_EST)
+            assert np.array_equal(req.out, want)
+            assert np.array_equal(req.out, alone(fsp, inst, rows, depths))
+            req.release()
+    for inst, _, _, _ in insts:
+        inst.close()
