@@ -175,13 +175,11 @@ fsp_status fsp_bound_pool_ex(const fsp_instance *inst, const int16_t *nodes, con
 /*
  * fsp_bound_pool_host -- the paper's accounting of one pool (Section III-A:
  * the pool is off-loaded to the device, the bounds are returned to the
- * host): moves nodes and depths from host memory, bounds them, moves the
- * bounds back, and returns when out_lb is filled.  When all three buffers
- * are page-locked (cudaHostAlloc, cudaHostRegister, a pinned torch tensor)
- * the kernels read and write them in place over the host link, so the
- * transfer overlaps the bounding with no staging copy.  Otherwise the pool
- * is copied in chunks so that copies and bounding overlap, through device
- * staging memory from the library's stream-ordered pool.
+ * host): copies nodes and depths from host memory, bounds them, copies the
+ * bounds back, and returns when out_lb is filled.  The pool is moved in
+ * chunks so that copies and bounding overlap, through device staging memory
+ * from the library's stream-ordered pool (page-locked host buffers copy
+ * fastest).
  *   nodes host int16 [N][n]; depths host int32 [N]; out_lb host int32 [N].
  *   cuda_stream orders the work (NULL = legacy default stream); the call
  *   synchronises with it before returning.

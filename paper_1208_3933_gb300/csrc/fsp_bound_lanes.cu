@@ -4,7 +4,7 @@
 // two-machine bound of Section II-C per sub-problem), mapped the other way
 // round: a warp owns 32 nodes, and its 32 lanes take 32 different machine
 // couples (k,l).  Each lane walks its couple's Johnson order (records laid
-// out [group][position][lane], so the 32 lanes read 32 consecutive words)
+// out [group][position][lane], so the 32 lanes read 32 consecutive records)
 // and updates the slack of all 32 nodes of the warp in registers,
 //     u_b <- max(u_b + delta_j, s_j)   when job j is unscheduled in node b,
 // where bit b of the warp's flag word for job j says so.  A lane's couple
@@ -13,14 +13,17 @@
 // over all couples for node b, combined with the one-machine terms
 // max_l (A_l + q_l).
 //
-// With 32-bit records every value the scan forms is an integer below 2^24
-// (slack <= 8191 + 1024 * 255), so the scan runs in fp32: the add goes to the
-// FMA pipe and only the max to the integer ALU pipe, and the result is exact.
-// 128-bit records (large processing times) use the int32 path.
+// With compact records (two fp32 words: s carrying the job in its low
+// mantissa bits, and delta) every slack is an integer below 2^24 plus a
+// fraction below 1 (fsp_lanes_device.cuh), so the scan runs in fp32: the add
+// goes to the FMA pipe and only the max to the integer ALU pipe, and the
+// truncated result is exact.  128-bit records (large processing times) use
+// the int32 path.
 //
 // Per node the shared memory holds one flag bit per job and a row with A_k
-// (int32) and q_l (int16), so a block keeps hundreds of nodes in flight.  Two
-// staging modes:
+// (int32) and q_l (int16), so a block keeps hundreds of nodes in flight.
+// Large pools are bounded in depth order (fsp_order.cu).  Two staging modes
+// here (fsp_bound_split.cu and fsp_bound_warp.cu hold two more):
 //   resident  all record groups are copied to shared memory once per block
 //             (one cp.async.bulk per group on one mbarrier); warps are then
 //             independent and claim 32-node batches from a per-block counter,
@@ -29,10 +32,12 @@
 //             (group, positions) through two buffers, the whole block moving
 //             from tile to tile together (the paper's "does not fit" case).
 //
-// Setup, one lane per node: (1) membership flags and row validation, (2) the
-// prefix recurrence C(sigma,k) (Section II-B) and the prefix's column sums
-// in registers, (3) the minima of RM and QM as the first unscheduled job of
-// each machine's head- (tail-) sorted job list, 32 list entries per step.
+// Setup, one lane per node (fsp_lanes_device.cuh): (1) one pass over the
+// prefix for the membership bitmaps, row validation, the prefix recurrence
+// C(sigma,k) (Section II-B) and the prefix's column sums, (2) the flag words
+// by bit-matrix transposes, (3) the minima of RM and QM as the first
+// unscheduled job of each machine's head- (tail-) sorted job list, 32 list
+// entries per round.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -275,9 +275,9 @@ def test_depth_ordered_pools_with_invalid_and_extreme_depths(gpu_lib):
 
 
 def test_host_entry_point_mixed_pinned_and_pageable(gpu_lib):
-    """fsp_bound_pool_host reads page-locked buffers in place and stages the
-    rest; a mix of the two (pinned rows, pageable depths) takes the staged
-    path; both give the oracle's bounds."""
+    """fsp_bound_pool_host with a mix of page-locked and pageable buffers
+    (pinned rows, pageable depths) and with all three page-locked: both give
+    the oracle's bounds."""
     import torch
     fsp = gpu_lib
     w = workloads.named_pool("pool_200x20", N=9000)
