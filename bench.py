@@ -523,12 +523,15 @@ def run_gpu(args, world, rank, local):
     sm_max = clocks["sm_max_mhz"] or 2070.0
     peak = alu_peak_ops(props.multi_processor_count, sm_max, ALU_LANES_PER_SM)
     achieved = ops / mean_kernel_s
-    cpu_rate, cpu_sample, cpu_s, cpu_threads = cpu_oracle_rate(w, seconds=2.0)
-    cpu1_rate, cpu1_sample, cpu1_s, _ = cpu_oracle_rate(w, seconds=1.0, threads=1)
+    # the CPU baseline is measured in the single-GPU run only
+    cpu_rate, cpu_sample, cpu_s, cpu_threads = cpu_oracle_rate(w, seconds=2.0) if world == 1 else (0.0, 0, 0.0, 0)
+    cpu1_rate, cpu1_sample, cpu1_s, _ = cpu_oracle_rate(w, seconds=1.0, threads=1) if world == 1 else (0.0, 0, 0.0, 0)
     info = inst.info()
-    batched = run_batched_leg(dev) if not (args.nodes or args.no_extra) else None
-    served = run_served_leg() if not (args.nodes or args.no_extra) else None
-    bnb = run_bnb_leg() if not (args.nodes or args.no_extra) else None
+    # the extra legs run once, in the single-GPU run
+    extra = not (args.nodes or args.no_extra) and world == 1
+    batched = run_batched_leg(dev) if extra else None
+    served = run_served_leg() if extra else None
+    bnb = run_bnb_leg() if extra else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": region_ms_max / args.steps, "higher_is_better": True,
@@ -545,7 +548,7 @@ def run_gpu(args, world, rank, local):
                      "timed": "CUDA events around each step's fsp_bound_pool on its stream: the bounding "
                               "kernel(s) of the launch shape plus, for pools of >= 8192 nodes and >= 64 jobs, the "
                               "three small depth-order kernels"},
-        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
+        "cpu_baseline": None if world > 1 else {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                          "sample": f"first {cpu_sample} nodes of the pool, plain C oracle on {cpu_threads} threads, "
                                    f"{cpu_s:.1f} s",
                          "single_thread": {"value": cpu1_rate, "sample": f"first {cpu1_sample} nodes, 1 thread, "
