@@ -467,6 +467,15 @@ const char *fsp_status_string(fsp_status s);
 /* Library version as "major.minor.patch" (static string). */
 const char *fsp_version(void);
 
+/* fsp_check_wait_timeout -- self-check of the device-side bounded waits (no
+ * counterpart in the paper): every wait in the bounding kernels gives up
+ * after a clock64 limit, reports FSP_ETIMEDOUT and returns instead of
+ * hanging.  This runs one such wait, limit_cycles long (1..2^32), on a
+ * barrier phase that nothing completes; it returns FSP_ETIMEDOUT when the
+ * mechanism works (the instance stays usable), FSP_EINVAL/FSP_ECUDA on a bad
+ * argument or launch. */
+fsp_status fsp_check_wait_timeout(const fsp_instance *inst, int64_t limit_cycles);
+
 /* fsp_kernel_launches -- number of CUDA kernels this library has enqueued in
  * the process so far (every entry point counts its own launches; no compute
  * of the method, the paper has no counterpart).  For launch accounting around

@@ -635,26 +635,30 @@ extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_
     cudaStream_t user = static_cast<cudaStream_t>(cuda_stream);
     const int n = inst->n;
 
-    // Staged through device memory in chunks, alternating between the
-    // caller's stream and a second one, so the copies of one chunk overlap the
-    // bounding of the other.  (Reading page-locked pools in place over the
-    // host link measured 1.55-2.2 ms per 262,144-node 200x20 pool depending
-    // on the box; four staged chunks 1.67 ms on every box.)
+    // Staged through device memory in chunks: the copies go back to back on
+    // a copy stream, each chunk's bounding waits only for its own copy, and
+    // consecutive chunks are bounded on two streams so one chunk's last wave
+    // overlaps the next chunk's first.  (Reading page-locked pools in place
+    // over the host link measured 1.55-2.2 ms per 262,144-node 200x20 pool
+    // depending on the box.)
+    constexpr int kMaxChunks = 4;
     const int64_t nchunks = N >= 131072 ? 4 : (N >= 32768 ? 2 : 1);
     const int64_t chunk = (N + nchunks - 1) / nchunks;
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_side = nullptr;
+    cudaStream_t cpy = nullptr, comp2 = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_in[kMaxChunks] = {};
     int16_t *d_nodes = nullptr;
     int32_t *d_depths = nullptr, *d_out = nullptr;
     const size_t nodes_bytes = sizeof(int16_t) * (size_t)N * n;
     cudaMemPool_t pool = nullptr;
     st = scratch_pool(inst->device, &pool);
     if (st != FSP_OK) return st;
-    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&cpy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&comp2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming) != cudaSuccess)
         st = FSP_ECUDA;
-    }
+    for (int c = 0; st == FSP_OK && c < nchunks; ++c)
+        if (cudaEventCreateWithFlags(&ev_in[c], cudaEventDisableTiming) != cudaSuccess) st = FSP_ECUDA;
     if (st == FSP_OK &&
         (cudaMallocFromPoolAsync((void **)&d_nodes, nodes_bytes, pool, user) != cudaSuccess ||
          cudaMallocFromPoolAsync((void **)&d_depths, sizeof(int32_t) * (size_t)N, pool, user) != cudaSuccess ||
@@ -663,36 +667,83 @@ extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_
         st = FSP_ENOMEM;
     }
     if (st == FSP_OK) {
-        cudaEventRecord(ev_start, user);
-        cudaStreamWaitEvent(side, ev_start, 0);
+        cudaEventRecord(ev_start, user);  // the staging memory is ready on the caller's stream
+        cudaStreamWaitEvent(cpy, ev_start, 0);
+        cudaStreamWaitEvent(comp2, ev_start, 0);
         for (int64_t c = 0; c < nchunks && st == FSP_OK; ++c) {
             const int64_t lo = c * chunk, hi = std::min(N, lo + chunk);
             if (lo >= hi) break;
-            cudaStream_t s = (c & 1) ? side : user;
             const size_t rows = (size_t)(hi - lo);
             if (cudaMemcpyAsync(d_nodes + lo * n, nodes + lo * n, sizeof(int16_t) * rows * n, cudaMemcpyHostToDevice,
-                                s) != cudaSuccess ||
-                cudaMemcpyAsync(d_depths + lo, depths + lo, sizeof(int32_t) * rows, cudaMemcpyHostToDevice, s) !=
-                    cudaSuccess) {
+                                cpy) != cudaSuccess ||
+                cudaMemcpyAsync(d_depths + lo, depths + lo, sizeof(int32_t) * rows, cudaMemcpyHostToDevice, cpy) !=
+                    cudaSuccess ||
+                cudaEventRecord(ev_in[c], cpy) != cudaSuccess) {
                 st = FSP_ECUDA;
                 break;
             }
+            cudaStream_t s = (c & 1) ? comp2 : user;
+            cudaStreamWaitEvent(s, ev_in[c], 0);
             st = launch_bound(inst, d_nodes + lo * n, d_depths + lo, hi - lo, d_out + lo, s, nullptr);
             if (st != FSP_OK) break;
             if (cudaMemcpyAsync(out_lb + lo, d_out + lo, sizeof(int32_t) * rows, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess)
                 st = FSP_ECUDA;
         }
-        cudaEventRecord(ev_side, side);
-        cudaStreamWaitEvent(user, ev_side, 0);
+        // the caller's stream waits for both other streams (copies and chunks)
+        cudaEventRecord(ev_done, comp2);
+        cudaStreamWaitEvent(user, ev_done, 0);
+        cudaEventRecord(ev_done, cpy);
+        cudaStreamWaitEvent(user, ev_done, 0);
     }
     if (d_nodes) cudaFreeAsync(d_nodes, user);
     if (d_depths) cudaFreeAsync(d_depths, user);
     if (d_out) cudaFreeAsync(d_out, user);
     if (cudaStreamSynchronize(user) != cudaSuccess && st == FSP_OK) st = FSP_ECUDA;
+    for (int c = 0; c < kMaxChunks; ++c)
+        if (ev_in[c]) cudaEventDestroy(ev_in[c]);
     if (ev_start) cudaEventDestroy(ev_start);
-    if (ev_side) cudaEventDestroy(ev_side);
-    if (side) cudaStreamDestroy(side);
+    if (ev_done) cudaEventDestroy(ev_done);
+    if (cpy) cudaStreamDestroy(cpy);
+    if (comp2) cudaStreamDestroy(comp2);
     if (st == FSP_OK) st = take_device_status(inst);
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// Self-check of the device-side bounded waits.  Every wait of the bounding
+// kernels (tile copies, prepared-state copies, the per-warp rings) gives up
+// after a clock64 limit, reports FSP_ETIMEDOUT in the instance's status word
+// and returns, so a lost completion never hangs the GPU.  This kernel runs
+// the same wait on an mbarrier phase that nothing ever completes.
+namespace fspgb {
+
+__global__ void fsp_wait_probe(int32_t *status, long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit);  // no thread ever arrives
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) report_status(status, (int32_t)FSP_ETIMEDOUT);
+}
+
+}  // namespace fspgb
+
+extern "C" fsp_status fsp_check_wait_timeout(const fsp_instance *inst, int64_t limit_cycles) {
+    if (!inst || limit_cycles < 1 || limit_cycles > (int64_t)1 << 32) return FSP_EINVAL;
+    fsp_status st = fspgb::check_device(inst);
+    if (st != FSP_OK) return st;
+    st = fspgb::take_device_status(inst);
+    if (st != FSP_OK) return st;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return FSP_ECUDA;
+    fspgb::note_launches(1);
+    fspgb::fsp_wait_probe<<<1, 64, 0, s>>>(inst->dev_status, (long long)limit_cycles);
+    const bool launched = cudaGetLastError() == cudaSuccess;
+    const bool done = cudaStreamSynchronize(s) == cudaSuccess;
+    cudaStreamDestroy(s);
+    if (!launched || !done) return FSP_ECUDA;
+    return fspgb::take_device_status(inst);
 }

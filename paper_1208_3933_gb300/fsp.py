@@ -141,6 +141,7 @@ def load():
             "fsp_status_string": ([i32], ctypes.c_char_p),
             "fsp_version": ([], ctypes.c_char_p),
             "fsp_kernel_launches": ([], i64),
+            "fsp_check_wait_timeout": ([vp, i64], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -156,6 +157,12 @@ def fsp_status_string(status: int) -> str:
 
 def fsp_version() -> str:
     return load().fsp_version().decode()
+
+
+def fsp_check_wait_timeout(inst: Instance, limit_cycles: int = 2_000_000) -> int:
+    """Runs one device-side bounded wait that nothing completes; returns the
+    status (FSP_ETIMEDOUT when the timeout path works)."""
+    return int(load().fsp_check_wait_timeout(inst.handle, int(limit_cycles)))
 
 
 def fsp_kernel_launches() -> int:

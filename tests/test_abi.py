@@ -70,6 +70,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.fsp_branch_and_bound_device(None, 0, 0, 0, 0, None, None, None) == fsp.FSP_EINVAL
     lib.fsp_instance_destroy(None)  # no-op
     assert lib.fsp_kernel_launches() >= 0
+    assert lib.fsp_check_wait_timeout(None, 1) == fsp.FSP_EINVAL
     assert lib.fsp_server_solve(None, None, 0, 1, 1, 0, None, None, None, None) == fsp.FSP_EINVAL
 
 

@@ -291,3 +291,34 @@ def test_host_entry_point_mixed_pinned_and_pageable(gpu_lib):
         po.zero_()
         fsp.fsp_bound_pool_host(inst, pr, pd, po)
         assert np.array_equal(po.numpy(), want)
+
+
+@pytest.mark.parametrize("n,m", [(1, 2), (2, 2), (3, 2), (1, 5), (2, 7), (64, 2)])
+def test_tiny_and_two_machine_instances(gpu_lib, n, m):
+    """n = 1 and 2 jobs, m = 2 machines (one couple), every depth; at m = 2
+    the root bound is Johnson's optimum (brute force over all orders)."""
+    from oracle import brute
+    fsp = gpu_lib
+    p, rows, depths = pool(400 + 10 * n + m, n, m, 600)
+    with fsp.Instance(p) as inst:
+        got = gpu_bounds(fsp, inst, rows, depths)
+        assert np.array_equal(got, oracle_bounds(p, rows, depths))
+        if m == 2 and n <= 8:
+            root = gpu_bounds(fsp, inst, np.zeros((1, n), np.int16), np.zeros(1, np.int32))
+            assert root[0] == brute.optimum(p)[0]
+
+
+def test_largest_processing_times(gpu_lib):
+    """Processing times as large as the instance limit allows (sum of all
+    p_jk just below 2^30): 128-bit records, every intermediate value near
+    the int32 range."""
+    fsp = gpu_lib
+    rng = np.random.default_rng(9)
+    n, m = 12, 6
+    p = rng.integers(1, (2 ** 30 - 1) // (n * m), (n, m), dtype=np.int32)
+    assert int(p.sum(dtype=np.int64)) < 2 ** 30
+    rows, depths = workloads.random_pool(rng, n, 3000, max_depth=n + 1)
+    with fsp.Instance(p) as inst:
+        assert inst.info().compact == 0
+        got = gpu_bounds(fsp, inst, rows, depths)
+    assert np.array_equal(got, oracle_bounds(p, rows, depths))
