@@ -638,27 +638,34 @@ extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_
     // Staged through device memory in chunks: the copies go back to back on
     // a copy stream, each chunk's bounding waits only for its own copy, and
     // consecutive chunks are bounded on two streams so one chunk's last wave
-    // overlaps the next chunk's first.  (Reading page-locked pools in place
-    // over the host link measured 1.55-2.2 ms per 262,144-node 200x20 pool
-    // depending on the box.)
+    // overlaps the next chunk's first.  Chunk ends are fractions of the pool:
+    // a small first chunk starts the bounding early, and few chunks keep each
+    // launch's last partial wave and depth order from repeating too often
+    // (at 200x20: 20/80 % 1.62 ms per pool, four equal chunks 1.67 ms, one
+    // chunk 1.89 ms; reading page-locked pools in place over the host link
+    // 1.55-2.2 ms depending on the box).
     constexpr int kMaxChunks = 4;
-    const int64_t nchunks = N >= 131072 ? 4 : (N >= 32768 ? 2 : 1);
-    const int64_t chunk = (N + nchunks - 1) / nchunks;
-    cudaStream_t cpy = nullptr, comp2 = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_in[kMaxChunks] = {};
+    static const double kChunkEnds[] = {0.2, 1.0};
+    const int64_t nchunks = N >= 32768 ? (int64_t)(sizeof(kChunkEnds) / sizeof(kChunkEnds[0])) : 1;
+    int64_t ends[kMaxChunks + 1] = {0};
+    for (int64_t c = 0; c < nchunks; ++c)
+        ends[c + 1] = c + 1 == nchunks ? N : std::max(ends[c], std::min(N, (int64_t)(kChunkEnds[c] * (double)N)));
+    std::lock_guard<std::mutex> host_lock(inst->host_mu);
+    cudaStream_t &cpy = inst->host_streams[0], &comp2 = inst->host_streams[1];
+    cudaEvent_t &ev_start = inst->host_events[0], &ev_done = inst->host_events[1];
+    cudaEvent_t *ev_in = inst->host_events + 2;
     int16_t *d_nodes = nullptr;
     int32_t *d_depths = nullptr, *d_out = nullptr;
     const size_t nodes_bytes = sizeof(int16_t) * (size_t)N * n;
     cudaMemPool_t pool = nullptr;
     st = scratch_pool(inst->device, &pool);
     if (st != FSP_OK) return st;
-    if (cudaStreamCreateWithFlags(&cpy, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&comp2, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming) != cudaSuccess)
-        st = FSP_ECUDA;
-    for (int c = 0; st == FSP_OK && c < nchunks; ++c)
-        if (cudaEventCreateWithFlags(&ev_in[c], cudaEventDisableTiming) != cudaSuccess) st = FSP_ECUDA;
+    for (int i = 0; st == FSP_OK && i < 2; ++i)
+        if (!inst->host_streams[i] && cudaStreamCreateWithFlags(&inst->host_streams[i], cudaStreamNonBlocking) != cudaSuccess)
+            st = FSP_ECUDA;
+    for (int i = 0; st == FSP_OK && i < 6; ++i)
+        if (!inst->host_events[i] && cudaEventCreateWithFlags(&inst->host_events[i], cudaEventDisableTiming) != cudaSuccess)
+            st = FSP_ECUDA;
     if (st == FSP_OK &&
         (cudaMallocFromPoolAsync((void **)&d_nodes, nodes_bytes, pool, user) != cudaSuccess ||
          cudaMallocFromPoolAsync((void **)&d_depths, sizeof(int32_t) * (size_t)N, pool, user) != cudaSuccess ||
@@ -671,7 +678,7 @@ extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_
         cudaStreamWaitEvent(cpy, ev_start, 0);
         cudaStreamWaitEvent(comp2, ev_start, 0);
         for (int64_t c = 0; c < nchunks && st == FSP_OK; ++c) {
-            const int64_t lo = c * chunk, hi = std::min(N, lo + chunk);
+            const int64_t lo = ends[c], hi = ends[c + 1];
             if (lo >= hi) break;
             const size_t rows = (size_t)(hi - lo);
             if (cudaMemcpyAsync(d_nodes + lo * n, nodes + lo * n, sizeof(int16_t) * rows * n, cudaMemcpyHostToDevice,
@@ -700,12 +707,6 @@ extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_
     if (d_depths) cudaFreeAsync(d_depths, user);
     if (d_out) cudaFreeAsync(d_out, user);
     if (cudaStreamSynchronize(user) != cudaSuccess && st == FSP_OK) st = FSP_ECUDA;
-    for (int c = 0; c < kMaxChunks; ++c)
-        if (ev_in[c]) cudaEventDestroy(ev_in[c]);
-    if (ev_start) cudaEventDestroy(ev_start);
-    if (ev_done) cudaEventDestroy(ev_done);
-    if (cpy) cudaStreamDestroy(cpy);
-    if (comp2) cudaStreamDestroy(comp2);
     if (st == FSP_OK) st = take_device_status(inst);
     return st;
 }

@@ -300,6 +300,10 @@ extern "C" fsp_status fsp_instance_create_ex(const int32_t *p, int32_t n, int32_
 
 extern "C" void fsp_instance_destroy(fsp_instance *inst) {
     if (!inst) return;
+    for (cudaStream_t s : inst->host_streams)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : inst->host_events)
+        if (e) cudaEventDestroy(e);
     if (inst->dev_block) cudaFree(inst->dev_block);
     if (inst->host_status) cudaFreeHost(inst->host_status);
     delete inst;

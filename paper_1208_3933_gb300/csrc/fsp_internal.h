@@ -91,6 +91,11 @@ struct fsp_instance {
     int32_t *dev_status = nullptr;  // the same word as the device sees it
     fspgb::DeviceTables t;
     int32_t num_sms = 0;
+    // fsp_bound_pool_host's copy and second compute stream and its events,
+    // made on first use and kept; host_mu serialises that entry point's calls
+    mutable std::mutex host_mu;
+    mutable cudaStream_t host_streams[2] = {nullptr, nullptr};
+    mutable cudaEvent_t host_events[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     mutable std::mutex mu;          // guards the tuning cache below
     mutable std::vector<std::pair<int64_t, fsp_launch_config>> tuned;  // pool-size bucket -> shape
 };

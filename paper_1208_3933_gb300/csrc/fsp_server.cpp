@@ -692,15 +692,18 @@ bool take_parents(Solve &S, int w, std::vector<SNode> &parents) {
     for (;;) {
         if (S.stop) return false;
         auto &mine = S.stacks[w];
-        if (mine.empty()) {
-            int victim = -1;
-            size_t most = 0;
-            for (int v = 0; v < S.searchers; ++v)
-                if (v != w && S.stacks[v].size() > most) {
-                    most = S.stacks[v].size();
-                    victim = v;
-                }
-            if (victim >= 0) {
+        // pop live nodes, stealing whenever the own stack runs dry, until some
+        // are found or every stack is empty (stale nodes are dropped on the way)
+        while (parents.empty()) {
+            if (mine.empty()) {
+                int victim = -1;
+                size_t most = 0;
+                for (int v = 0; v < S.searchers; ++v)
+                    if (v != w && S.stacks[v].size() > most) {
+                        most = S.stacks[v].size();
+                        victim = v;
+                    }
+                if (victim < 0) break;
                 auto &vs = S.stacks[victim];
                 const size_t take = std::max<size_t>(1, vs.size() / 2);
                 // the bottom `take` nodes, kept in stack order
@@ -709,12 +712,12 @@ bool take_parents(Solve &S, int w, std::vector<SNode> &parents) {
                 vs.erase(vs.begin(), vs.begin() + (ptrdiff_t)take);
                 ++S.steals;
             }
-        }
-        const int64_t UB = S.ub.load();
-        while (!mine.empty() && (int)parents.size() < S.expand) {
-            SNode nd = std::move(mine.back());
-            mine.pop_back();
-            if (nd.lb < UB) parents.push_back(std::move(nd));
+            const int64_t UB = S.ub.load();
+            while (!mine.empty() && (int)parents.size() < S.expand) {
+                SNode nd = std::move(mine.back());
+                mine.pop_back();
+                if (nd.lb < UB) parents.push_back(std::move(nd));
+            }
         }
         if (!parents.empty()) {
             ++S.busy;
