@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(512, 1)
             for (int i = 0; i < npad; ++i) {
                 lanes_step(__ldg(R + i * 32), F, u);
             }
-            couple_epilogue(AQ, aq_stride, m, kk, ll, u, lb);
+            couple_epilogue<false>(AQ, aq_stride, m, kk, ll, u, lb);
         }
         const int best = transpose_max(lb, lane);
         if (x < a.N) a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
@@ -154,6 +154,7 @@ fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_p
         a.rec_bytes = (uint32_t)inst->grec_bytes;
         a.aq_stride = pp.stride;
         a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
+        a.q32 = inst->compact ? 0 : 1;
         a.wait_limit = 4000000000LL;
         const int64_t nb = (p.N + 31) / 32;
         for (int64_t k = 0; k < nb; ++k) items.push_back(make_int2(i, (int)k));

@@ -403,8 +403,13 @@ fsp_status resolve_lockstep(const fsp_instance *inst, int64_t N, const DeviceLim
 
 fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits &d, fsp_launch_config &c) {
     if (c.warps_per_block < 0 || c.warps_per_block > 16 || c.positions_per_tile < 0 ||
-        (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 4 || c.blocks_per_sm < 0 || c.blocks_per_sm > 2)
+        (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 4 || c.blocks_per_sm < 0 || c.blocks_per_sm > 2 ||
+        c.pairs_per_tile < 0)
         return FSP_EINVAL;
+    const int G = inst->G;
+    // pairs per work item: only streamed staging splits a batch by couples
+    const int req_g = lanes_groups_per_item(inst, c.pairs_per_tile);
+    auto resolved_ppt = [&](int gper) { return gper >= G ? inst->P : gper * 32; };
     if (!c.blocks_per_sm) c.blocks_per_sm = 1;
     const int npad = inst->npad;
     auto fits = [&](int W, int staging, int pos) {
@@ -437,16 +442,43 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
                 break;
             }
         }
-        if (bW) {
+        if (bW && req_g == G) {
             c.warps_per_block = bW;
             c.staging = FSP_STAGING_RESIDENT;
             c.positions_per_tile = 0;
             c.blocks_per_sm = 1;
+            c.pairs_per_tile = inst->P;
             return FSP_OK;
         }
         return FSP_EINVAL;
     }
     c.staging = tiled;
+    if (tiled != FSP_STAGING_STREAMED && req_g != G) return FSP_EINVAL;
+    // Launch model for the defaults: a wave of work items (block batches of
+    // 32 W nodes, times S couple slices of gper groups each) takes about
+    // max(warps per SM, 12) x (setup + gper / G of a full scan), the setup
+    // costing about a fifth of a full scan; slicing by couples pays for its
+    // repeated setup only when the batches leave SMs idle.
+    const double slots = (double)d.num_sms * c.blocks_per_sm;
+    auto model_time = [&](int W, int gper) {
+        const double batches = std::ceil((double)std::max<int64_t>(N, 1) / (32.0 * W));
+        const double items = batches * std::ceil((double)G / gper);
+        return std::ceil(items / slots) * std::max(W * c.blocks_per_sm, 12) * (0.2 + (double)gper / G);
+    };
+    auto best_gper = [&](int W, double *t) {
+        int bg = req_g;
+        double bt = model_time(W, req_g);
+        if (!c.pairs_per_tile && tiled == FSP_STAGING_STREAMED)
+            for (int g = G - 1; g >= 1; --g) {
+                const double tg = model_time(W, g);
+                if (tg < bt * (1.0 - 1e-9)) {
+                    bt = tg;
+                    bg = g;
+                }
+            }
+        if (t) *t = bt;
+        return bg;
+    };
     if (!c.warps_per_block) {
         double best = -1.0;
         int bW = 0;
@@ -454,10 +486,10 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
             const int ch = c.positions_per_tile ? c.positions_per_tile : best_chunk(W);
             if (ch < 4 || !fits(W, tiled, ch)) continue;
             if (!c.positions_per_tile && ch < std::min(npad, 64)) continue;
-            const double batches = std::ceil((double)std::max<int64_t>(N, 1) / (32.0 * W));
-            const double score = wave_efficiency(batches, (double)d.num_sms * c.blocks_per_sm) *
-                                 std::min(1.0, W * c.blocks_per_sm / 12.0);
-            if (score > best + 1e-9) {
+            double t = 0.0;
+            best_gper(W, &t);
+            const double score = 1.0 / t;
+            if (score > best * (1.0 + 1e-9)) {
                 best = score;
                 bW = W;
             }
@@ -465,6 +497,7 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
         if (best < 0) return FSP_EINVAL;
         c.warps_per_block = bW;
     }
+    c.pairs_per_tile = resolved_ppt(best_gper(c.warps_per_block, nullptr));
     if (!c.positions_per_tile) c.positions_per_tile = best_chunk(c.warps_per_block);
     if (c.positions_per_tile < 4) return FSP_EINVAL;
     return fits(c.warps_per_block, tiled, c.positions_per_tile) ? FSP_OK : FSP_EINVAL;

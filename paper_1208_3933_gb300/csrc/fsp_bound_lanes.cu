@@ -21,7 +21,8 @@
 // the int32 path.
 //
 // Per node the shared memory holds one flag bit per job and a row with A_k
-// (int32) and q_l (int16), so a block keeps hundreds of nodes in flight.
+// (int32) and q_l (int16 with compact records, whose tails stay below 2^15;
+// int32 with 128-bit ones), so a block keeps hundreds of nodes in flight.
 // Large pools are bounded in depth order (fsp_order.cu).  Two staging modes
 // here (fsp_bound_split.cu and fsp_bound_warp.cu hold two more):
 //   resident  all record groups are copied to shared memory once per block
@@ -31,6 +32,9 @@
 //   streamed  records too large for shared memory are staged in tiles of
 //             (group, positions) through two buffers, the whole block moving
 //             from tile to tile together (the paper's "does not fit" case).
+//             A pool too small to occupy every SM splits each block batch by
+//             couple groups over several work items, whose couple maxima meet
+//             in an atomic max on the zeroed bounds.
 //
 // Setup, one lane per node (fsp_lanes_device.cuh): (1) one pass over the
 // prefix for the membership bitmaps, row validation, the prefix recurrence
@@ -109,13 +113,13 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) 
 #pragma unroll
                 for (int b = 0; b < 32; ++b) u[b] = 0.f;
                 scan_compact(reinterpret_cast<const uint2 *>(tables + g * group_bytes) + lane, a.npad, F, u);
-                couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, u, lb);
+                couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, u, lb);
             } else {
                 int u[32];
 #pragma unroll
                 for (int b = 0; b < 32; ++b) u[b] = 0;
                 scan_wide(reinterpret_cast<const int4 *>(tables + g * group_bytes) + lane, a.npad, F, u);
-                couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, u, lb);
+                couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, u, lb);
             }
         }
         const int best = transpose_max(lb, lane);
@@ -155,12 +159,26 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
         const unsigned char *src = a.grec + ((size_t)g * a.npad + (size_t)ch * a.chunk) * 32 * a.rec_bytes;
         tp.issue(fill, src, (uint32_t)pos * 32u * a.rec_bytes);
     };
-    if (threadIdx.x == 0 && (int64_t)blockIdx.x < a.num_batches) {
-        tile_issue(0, 0);
-        if (a.ntiles == 2) tile_issue(1, 1);
+    // Work items: a block batch of 32 W nodes times a slice of gper couple
+    // groups (S slices cover all groups; S = 1 unless small pools are split
+    // by couples to occupy more SMs).  Item it = batch it / S, slice it % S;
+    // the host keeps the item count below 2^31 when S > 1.
+    const uint32_t S = a.gslices > 1 ? (uint32_t)a.gslices : 1u;
+    const int gper = S > 1 ? a.gper : a.G;
+    const int64_t items = a.num_batches * S;
+    auto slice_of = [&](int64_t it) { return S > 1 ? (int)((uint32_t)it % S) : 0; };
+    if (threadIdx.x == 0 && (int64_t)blockIdx.x < items) {
+        if (tp.resident) {
+            tile_issue(0, 0);
+            if (a.ntiles == 2) tile_issue(1, 1);
+        } else {
+            tile_issue(0, slice_of(blockIdx.x) * gper * a.nchunks);
+        }
     }
 
-    for (int64_t bt = blockIdx.x; bt < a.num_batches; bt += gridDim.x) {
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int sl = slice_of(it);
+        const int64_t bt = S > 1 ? (int64_t)((uint32_t)it / S) : it;
         const int64_t x = node_at(a, bt * (int64_t)(32 * W) + warp * 32 + lane);
         int bterm = 0;
         const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
@@ -174,11 +192,14 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
             ui[b] = 0;
         }
         int kk = 0, ll = 1;
-        for (int t = 0; t < a.ntiles; ++t) {
+        const int t1 = min(a.G, (sl + 1) * gper) * a.nchunks;
+        for (int t = sl * gper * a.nchunks; t < t1; ++t) {
             const int g = t / a.nchunks, ch = t - g * a.nchunks;
             if (!tp.resident && threadIdx.x == 0) {
-                const bool has_next = (t + 1 < a.ntiles) || (bt + gridDim.x < a.num_batches);
-                if (has_next) tile_issue(tp.fill + 1, (t + 1) % a.ntiles);
+                // the next tile of this item, else the first of the block's next item
+                const int next = t + 1 < t1 ? t + 1
+                                 : (it + gridDim.x < items ? slice_of(it + gridDim.x) * gper * a.nchunks : -1);
+                if (next >= 0) tile_issue(tp.fill + 1, next);
             }
             if (!tp.wait(t, a.wait_limit)) {
                 if (threadIdx.x == 0) {
@@ -204,9 +225,9 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
                 scan_wide(reinterpret_cast<const int4 *>(tb) + lane, npos, F, ui);
             if (ch == a.nchunks - 1) {
                 if (!WIDE)
-                    couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, uf, lb);
+                    couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, uf, lb);
                 else
-                    couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, ui, lb);
+                    couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, ui, lb);
             }
             if (!tp.resident) {
                 __syncthreads();
@@ -214,7 +235,14 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
             }
         }
         const int best = transpose_max(lb, lane);
-        if (x < a.N) a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
+        if (x < a.N) {
+            if (S == 1)
+                a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
+            else if (!valid)
+                a.out[x] = FSP_LB_INVALID;  // every slice finds the row invalid
+            else
+                atomicMax(a.out + x, max(best, bterm));  // out was zeroed; bounds are >= 0
+        }
         __syncwarp();  // the flag and row arrays are rewritten by the next batch
     }
 }
@@ -230,7 +258,8 @@ struct LanesLayout {
     size_t total;
 };
 
-int aq_stride_for(int m) { return (m + (m + 1) / 2) | 1; }
+// ints per node row: A_k as int32, then q_l as int16 (compact records) or int32
+int aq_stride_for(int m, bool q32) { return (m + (q32 ? m : (m + 1) / 2)) | 1; }
 
 LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident, int chunk) {
     LanesLayout L;
@@ -245,7 +274,7 @@ LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident,
         L.off_flags = L.off_tables + 2 * L.tile_stride;
     }
     L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)warps * flag_words(inst->n) * 4, 128);
-    L.aq_stride = aq_stride_for(inst->m);
+    L.aq_stride = aq_stride_for(inst->m, !inst->compact);
     L.total = align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
     return L;
 }
@@ -290,6 +319,11 @@ cudaError_t launch_lanes_mp(const LanesArgs &a, int mp, bool resident, int grid,
 }
 
 }  // namespace
+
+int lanes_groups_per_item(const fsp_instance *inst, int pairs_per_tile) {
+    if (pairs_per_tile <= 0 || pairs_per_tile >= inst->P) return inst->G;
+    return std::min(inst->G, (pairs_per_tile + 31) / 32);
+}
 
 fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, size_t *smem_bytes) {
     if (c.staging == FSP_STAGING_SPLIT) return split_layout(inst, c, smem_bytes);
@@ -350,6 +384,7 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     a.off_aq = L.off_aq;
     a.aq_stride = L.aq_stride;
     a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
+    a.q32 = inst->compact ? 0 : 1;
     a.wait_limit = 4000000000LL;
     int grid;
     if (resident) {
@@ -359,11 +394,17 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
         grid = (int)std::min<int64_t>((a.num_batches + per_block - 1) / per_block, (int64_t)num_sms(inst->device));
     } else {
         a.num_batches = (N + 32 * W - 1) / (32 * W);
+        a.gper = lanes_groups_per_item(inst, cfg.pairs_per_tile);
+        a.gslices = (inst->G + a.gper - 1) / a.gper;
+        if (a.gslices > 1 && a.num_batches * a.gslices >= ((int64_t)1 << 31)) return FSP_EINVAL;
         const int bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 1;
-        grid = (int)std::min<int64_t>(a.num_batches, (int64_t)num_sms(inst->device) * bps);
+        grid = (int)std::min<int64_t>(a.num_batches * a.gslices, (int64_t)num_sms(inst->device) * bps);
     }
     grid = std::max(grid, 1);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // couple slices combine by atomic max into zeroed bounds
+    if (a.gslices > 1 && cudaMemsetAsync(out_lb, 0, sizeof(int32_t) * (size_t)N, s) != cudaSuccess)
+        return FSP_ECUDA;
     int32_t *order = nullptr;
     st = depth_order(inst, depths, N, s, &order);
     if (st != FSP_OK) return st;

@@ -11,7 +11,7 @@
 //                    (latency hidden by occupancy).  Per 32-node batch it
 //                    builds the same state the fused kernel keeps in shared
 //                    memory -- the job flag words F[j], the node rows
-//                    (A_k int32, q_l int16), the one-machine term and the node
+//                    (A_k int32, q_l int16 or int32), the one-machine term and the node
 //                    index -- and writes it as one contiguous block of scratch
 //                    (large pools are taken in depth order, fsp_order.cu).
 //   fsp_lanes_scan   the block-synchronous tile scan of the fused kernel, with
@@ -166,9 +166,9 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_scan(const LanesArgs a) {
                 scan_wide(reinterpret_cast<const int4 *>(tb) + lane, npos, F, ui);
             if (ch == a.nchunks - 1) {
                 if (!WIDE)
-                    couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, uf, lb);
+                    couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, uf, lb);
                 else
-                    couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, ui, lb);
+                    couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, ui, lb);
             }
             if (!tp.resident) {
                 __syncthreads();
@@ -183,11 +183,12 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_scan(const LanesArgs a) {
 // ------------------------------------------------------------------ host
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-int aq_stride_for(int m) { return (m + (m + 1) / 2) | 1; }
+// ints per node row: A_k as int32, then q_l as int16 (compact records) or int32
+int aq_stride_for(int m, bool q32) { return (m + (q32 ? m : (m + 1) / 2)) | 1; }
 
 // Words of one 32-node batch block of scratch (a multiple of 4: 16 bytes).
 int sb_words_for(const fsp_instance *inst) {
-    return (int)align_up((size_t)inst->n + 32 * (size_t)aq_stride_for(inst->m) + 64, 4);
+    return (int)align_up((size_t)inst->n + 32 * (size_t)aq_stride_for(inst->m, !inst->compact) + 64, 4);
 }
 
 struct PrepLayout {
@@ -200,7 +201,7 @@ PrepLayout prep_layout_for(const fsp_instance *inst) {
     L.off_cache = 0;
     L.off_flags = (uint32_t)align_up((size_t)inst->m * 32 * 8 * 2, 128);
     L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)kPrepWarps * flag_words(inst->n) * 4, 128);
-    L.total = align_up(L.off_aq + (size_t)kPrepWarps * 32 * aq_stride_for(inst->m) * 4, 128);
+    L.total = align_up(L.off_aq + (size_t)kPrepWarps * 32 * aq_stride_for(inst->m, !inst->compact) * 4, 128);
     return L;
 }
 
@@ -328,8 +329,9 @@ fsp_status launch_split(const fsp_instance *inst, const int16_t *nodes, const in
     a.nchunks = (inst->npad + chunk - 1) / chunk;
     a.ntiles = inst->G * a.nchunks;
     a.rec_bytes = (uint32_t)inst->grec_bytes;
-    a.aq_stride = aq_stride_for(inst->m);
+    a.aq_stride = aq_stride_for(inst->m, !inst->compact);
     a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
+    a.q32 = inst->compact ? 0 : 1;
     a.scratch = scratch;
     a.sb_words = sb;
     a.wait_limit = 4000000000LL;

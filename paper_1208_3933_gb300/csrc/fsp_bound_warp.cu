@@ -125,9 +125,9 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_warp(const LanesArgs a, uint
                 scan_wide(reinterpret_cast<const int4 *>(tb) + lane, npos, F, ui);
             if (ch == a.nchunks - 1) {
                 if (!WIDE)
-                    couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, uf, lb);
+                    couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, uf, lb);
                 else
-                    couple_epilogue(AQ, a.aq_stride, a.m, kk, ll, ui, lb);
+                    couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, ui, lb);
             }
             ++consumed;
             __syncwarp();  // every lane is done with buffer bi
@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_warp(const LanesArgs a, uint
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-int aq_stride_for(int m) { return (m + (m + 1) / 2) | 1; }
+// ints per node row: A_k as int32, then q_l as int16 (compact records) or int32
+int aq_stride_for(int m, bool q32) { return (m + (q32 ? m : (m + 1) / 2)) | 1; }
 
 struct WarpLayout {
     uint32_t off_cache, off_warps, warp_stride, w_off_aq, w_off_tiles, tile_stride;
@@ -163,7 +164,7 @@ WarpLayout warp_layout_for(const fsp_instance *inst, int warps, int chunk) {
     L.off_warps = (uint32_t)align_up(L.off_cache + (size_t)inst->m * 32 * 8 * 2, 128);
     L.tile_stride = (uint32_t)align_up((size_t)chunk * 32 * inst->grec_bytes, 128);
     L.w_off_aq = (uint32_t)align_up(128 + (size_t)flag_words(inst->n) * 4, 128);
-    L.w_off_tiles = (uint32_t)align_up(L.w_off_aq + (size_t)32 * aq_stride_for(inst->m) * 4, 128);
+    L.w_off_tiles = (uint32_t)align_up(L.w_off_aq + (size_t)32 * aq_stride_for(inst->m, !inst->compact) * 4, 128);
     L.warp_stride = (uint32_t)align_up(L.w_off_tiles + (size_t)kWarpBufs * L.tile_stride, 128);
     L.total = (size_t)L.off_warps + (size_t)warps * L.warp_stride;
     return L;
@@ -251,8 +252,9 @@ fsp_status launch_warp(const fsp_instance *inst, const int16_t *nodes, const int
     a.off_cache = L.off_cache;
     a.off_flags = L.off_warps;
     a.tile_stride = L.tile_stride;
-    a.aq_stride = aq_stride_for(inst->m);
+    a.aq_stride = aq_stride_for(inst->m, !inst->compact);
     a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
+    a.q32 = inst->compact ? 0 : 1;
     a.wait_limit = 4000000000LL;
     // whole blocks' worth of warps per SM; at least one batch per warp of the grid
     const int64_t per_block = W;

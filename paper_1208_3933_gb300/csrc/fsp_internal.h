@@ -109,6 +109,9 @@ fsp_status launch_bound(const fsp_instance *inst, const int16_t *nodes, const in
                         int64_t N, int32_t *out_lb, void *stream, const fsp_launch_config *cfg);
 // Couple-lanes kernel (fsp_bound_lanes.cu).
 fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &cfg, size_t *smem_bytes);
+// Couple groups of 32 per streamed work item for a requested pairs_per_tile
+// (0 or >= P: all G groups; else rounded up to whole groups).
+int lanes_groups_per_item(const fsp_instance *inst, int pairs_per_tile);
 fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
                         int32_t *out_lb, void *stream, const fsp_launch_config &cfg);
 // The same bound as a prep kernel and a scan kernel (fsp_bound_split.cu).

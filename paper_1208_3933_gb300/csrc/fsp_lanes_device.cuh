@@ -37,6 +37,20 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
     return x;
 }
 
+// The latency q_l of a node row (after the m values A_k): int16 for
+// instances with compact records (every tail is below 2^15 there), int32
+// otherwise.
+__device__ __forceinline__ void store_q(int32_t *row, int m, int l, int v, bool q32) {
+    if (q32)
+        row[m + l] = v;
+    else
+        reinterpret_cast<int16_t *>(row + m)[l] = (int16_t)v;
+}
+
+__device__ __forceinline__ int load_q(const int32_t *row, int m, int l, bool q32) {
+    return q32 ? row[m + l] : (int)reinterpret_cast<const int16_t *>(row + m)[l];
+}
+
 // Copies the first 32 entries of every machine's head- and tail-sorted job
 // lists into shared memory ([m][32] each; entries past n read (0,0)).
 __device__ __forceinline__ void load_sorted_heads(const LanesArgs &a, int2 *hcache, int2 *tcache) {
@@ -50,7 +64,7 @@ __device__ __forceinline__ void load_sorted_heads(const LanesArgs &a, int2 *hcac
 // Setup of node x (lane = node) for the warp's 32 nodes: the flag words F[j]
 // (bit b: job j unscheduled in the warp's node b; F holds 32 * ceil(n / 32)
 // words, which first hold the lanes' membership bitmaps), the lane's row
-// (A_k = r_k + S_k as int32, q_l as int16) and the one-machine term
+// (A_k = r_k + S_k as int32, then q_l, see store_q) and the one-machine term
 // max_{l>=1} (A_l + q_l).  Returns whether the row is valid.
 template <int MP>
 __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int lane, uint32_t *F, int32_t *myrow,
@@ -184,7 +198,7 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     // entries (from the shared-memory copy when given); nodes whose entries
     // were all scheduled go on round by round.
     const bool settled = !valid || d == n;  // nothing to search for
-    int16_t *qrow = reinterpret_cast<int16_t *>(myrow + m);
+    const bool q32 = a.q32 != 0;
     uint32_t open_h = 0, open_t = 0;  // machines still searching (bit k)
     const bool in = lane < n;
 #pragma unroll
@@ -208,7 +222,7 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
             else
                 myrow[k] = (per_job ? R[k] : max(C[k], mh)) + myrow[k];
             if (want_t && !settled && ft < 0) open_t |= 1u << k;
-            qrow[k] = (int16_t)ql;
+            store_q(myrow, m, k, ql, q32);
         }
     }
     // later rounds: list entries [base, base + 32) of every machine some node
@@ -236,14 +250,14 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
                     open_h &= ~(1u << k);
                 }
                 if (((open_t >> k) & 1u) && ft >= 0) {
-                    qrow[k] = (int16_t)vt;
+                    store_q(myrow, m, k, vt, q32);
                     open_t &= ~(1u << k);
                 }
             }
         }
     }
     bterm = 0;
-    for (int l = 1; l < m; ++l) bterm = max(bterm, myrow[l] + qrow[l]);
+    for (int l = 1; l < m; ++l) bterm = max(bterm, myrow[l] + load_q(myrow, m, l, q32));
     __syncwarp();
     return valid;
 }
@@ -282,13 +296,15 @@ __device__ __forceinline__ void scan_wide(const int4 *R, int npos, const uint32_
     }
 }
 
-template <typename U>
+// A lane's couple values A_k + q_l + u_b folded into lb; Q32 says how the
+// rows hold q (store_q): int32 with 128-bit records, int16 with compact ones.
+template <bool Q32, typename U>
 __device__ __forceinline__ void couple_epilogue(const int32_t *AQ, int stride, int m, int kk, int ll, const U (&u)[32],
                                                 int (&lb)[32]) {
 #pragma unroll
     for (int b = 0; b < 32; ++b) {
         const int32_t *rb = AQ + b * stride;
-        const int base = rb[kk] + reinterpret_cast<const int16_t *>(rb + m)[ll];
+        const int base = rb[kk] + load_q(rb, m, ll, Q32);
         lb[b] = max(lb[b], base + (int)u[b]);
     }
 }

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(512, 1)
             for (int i = 0; i < a.npad; ++i) {
                 lanes_step(__ldg(R + i * 32), F, u);
             }
-            couple_epilogue(AQ, aq_stride, a.m, kk, ll, u, lb);
+            couple_epilogue<false>(AQ, aq_stride, a.m, kk, ll, u, lb);
         }
         const int best = transpose_max(lb, lane);
         if (x < a.N) a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
@@ -182,6 +182,7 @@ extern "C" fsp_status fsp_bound_batch_noalloc(const fsp_pool_desc *pools, int32_
         a.rec_bytes = (uint32_t)inst->grec_bytes;
         a.aq_stride = stride;
         a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
+        a.q32 = inst->compact ? 0 : 1;
         offs[r + 1] = offs[r] + (p.N + 31) / 32;
     }
     const int64_t nitems = offs[count];

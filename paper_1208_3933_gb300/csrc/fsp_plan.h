@@ -42,8 +42,11 @@ struct LanesArgs {
     const int32_t *order; // slot -> node (depth order), or null: slot i bounds node i
     uint32_t *scratch;    // split kernels: prepared state, [32-node batch][sb_words]
     int32_t sb_words;
-    int32_t aq_stride;    // ints per node row (odd): A as int32 [m], then q as int16 [m]
+    int32_t aq_stride;    // ints per node row (odd): A as int32 [m], then q as int16 [m] (int32 if q32)
+    int32_t q32;          // q stored as int32: instances with 128-bit records, whose tails may pass 2^15
     int32_t release;      // 0: release times from the head minima; 1: per-job earliest starts
+    int32_t gper;         // streamed: couple groups per work item (slices of a block batch)
+    int32_t gslices;      // streamed: work items per block batch, ceil(G / gper); 0 or 1 = no split
     long long wait_limit;
 };
 

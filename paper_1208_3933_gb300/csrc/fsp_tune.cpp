@@ -74,6 +74,7 @@ void remember(const fsp_instance *inst, int64_t N, const fsp_launch_config &c) {
 
 std::vector<fsp_launch_config> candidates(const fsp_instance *inst, int64_t N) {
     std::vector<fsp_launch_config> out;
+    const int sms = fspgb::num_sms(inst->device);
     auto add = [&](fsp_launch_config c) {
         fsp_launch_config r;
         size_t smem = 0;
@@ -92,12 +93,26 @@ std::vector<fsp_launch_config> candidates(const fsp_instance *inst, int64_t N) {
             for (int pos : {0, 256, 128, 96, 64}) {
                 c.staging = staging;
                 c.positions_per_tile = pos;
+                c.pairs_per_tile = 0;
                 add(c);
                 if (W <= 8) {
                     fsp_launch_config c2 = c;
                     c2.blocks_per_sm = 2;
                     add(c2);
                 }
+                // pools of under two waves of block batches: work items of
+                // fewer couples (streamed staging) as well
+                if (staging == FSP_STAGING_STREAMED && pos == 0 && N < 2 * 32 * W * (int64_t)sms)
+                    for (int ppt : {32, 64, 96}) {
+                        if (ppt >= inst->P) break;
+                        c.pairs_per_tile = ppt;
+                        add(c);
+                        if (W <= 8) {
+                            fsp_launch_config c2 = c;
+                            c2.blocks_per_sm = 2;
+                            add(c2);
+                        }
+                    }
             }
     }
     for (int K : {8, 4, 2, 1})

@@ -85,6 +85,76 @@ def test_every_lanes_shape_matches_oracle(gpu_lib, W, staging, positions, nm):
     assert np.array_equal(got, oracle_bounds(p, rows, depths))
 
 
+@pytest.mark.parametrize("ppt", [32, 64, 96, 160])
+@pytest.mark.parametrize("W,positions", [(1, 12), (4, 12), (3, 0)])
+@pytest.mark.parametrize("nm", [(40, 20), (70, 12), (33, 27), (23, 9)])
+def test_couple_sliced_work_items_match_oracle(gpu_lib, ppt, W, positions, nm):
+    """Streamed staging with every block batch split by couples over several
+    work items (pairs_per_tile 32 to 160: one to five groups of 32 couples per
+    item, the last slice ragged or a single group), the slices combined by
+    atomic max into zeroed bounds; positions staged 12 at a time (tiles
+    re-staged within and across items) or in whole groups.  Invalid rows in
+    the pool: every slice must agree on them."""
+    fsp = gpu_lib
+    n, m = nm
+    p, rows, depths = pool(500 + n + m, n, m, 3 * 32 * W * 4 + 21)
+    depths[[3, 50]] = [-1, n + 1]
+    rows[7, :2] = [5, 5]
+    depths[7] = max(int(depths[7]), 2)
+    cfg = dict(kernel=2, warps_per_block=W, positions_per_tile=positions, staging=2, pairs_per_tile=ppt)
+    with fsp.Instance(p) as inst:
+        got = gpu_bounds(fsp, inst, rows, depths, config=cfg)
+    want = oracle_bounds(p, rows, depths)
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+    assert got[3] == got[50] == got[7] == fsp.FSP_LB_INVALID
+
+
+def test_couple_slices_with_depth_order_release_and_wide_records(gpu_lib):
+    """Couple slices on a depth-ordered pool (n >= 64, N >= 8,192), with
+    per-job release times, and with 128-bit records; the default shape of a
+    small pool splits batches by couples and matches the unsplit shape."""
+    import torch
+    fsp = gpu_lib
+    w = workloads.named_pool("pool_200x20", N=9000)
+    sliced = dict(kernel=2, warps_per_block=8, positions_per_tile=96, staging=2, pairs_per_tile=64)
+    whole = dict(sliced, pairs_per_tile=190, blocks_per_sm=2)
+    idx = np.random.default_rng(4).choice(w.N, 300, replace=False)
+    with fsp.Instance(w.p) as inst:
+        a = gpu_bounds(fsp, inst, w.rows, w.depths, config=sliced)
+        b = gpu_bounds(fsp, inst, w.rows, w.depths, config=whole)
+        assert np.array_equal(a, b)
+        assert np.array_equal(a[idx], oracle_bounds(w.p, w.rows[idx], w.depths[idx]))
+        small = w.rows[:2000], w.depths[:2000]
+        auto = fsp.fsp_tuned_config(inst, 2000)
+        assert auto["kernel"] == fsp.FSP_KERNEL_LANES and auto["pairs_per_tile"] < 190
+        assert np.array_equal(gpu_bounds(fsp, inst, *small), b[:2000])
+    with fsp.Instance(w.p, flags=fsp.FSP_INSTANCE_RELEASE_PER_JOB) as inst:
+        got = gpu_bounds(fsp, inst, w.rows[:3000], w.depths[:3000], config=sliced)
+    want = oracle.Tables(w.p).lb_pool(w.rows[:3000], w.depths[:3000], threads=THREADS, release=oracle.RELEASE_EST)
+    assert np.array_equal(got, want)
+    p, rows, depths = pool(9, 45, 11, 1700, hi=20000)
+    with fsp.Instance(p) as inst:
+        assert inst.info().compact == 0
+        got = gpu_bounds(fsp, inst, rows, depths, config=dict(kernel=2, warps_per_block=2, positions_per_tile=8,
+                                                              staging=2, pairs_per_tile=32))
+    assert np.array_equal(got, oracle_bounds(p, rows, depths))
+
+
+def test_couple_slices_refused_outside_streamed_staging(gpu_lib):
+    import torch
+    fsp = gpu_lib
+    p, rows, depths = pool(2, 30, 12, 100)
+    r, d = to_dev(rows, depths)
+    with fsp.Instance(p) as inst:
+        for staging in (1, 3, 4):
+            with pytest.raises(fsp.FspError):
+                fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=staging, pairs_per_tile=32))
+            # all couples in one work item is every staging's own shape
+            out = fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=staging, pairs_per_tile=66))
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy(), oracle_bounds(p, rows, depths))
+
+
 def test_wide_records_match_oracle(gpu_lib):
     """Processing times above 255 select the 128-bit Johnson records."""
     fsp = gpu_lib
@@ -108,6 +178,31 @@ def test_wide_records_match_oracle(gpu_lib):
     assert np.array_equal(got_res, want)
     assert np.array_equal(got_split, want)
     assert np.array_equal(got_warp, want)
+
+
+def test_latencies_above_int16(gpu_lib):
+    """Processing times up to 210,000 (128-bit records): minimum tails q_l
+    far above 2^15, which the couple-lanes rows must hold in full.  On these
+    pools about one node in twelve has a bound that a 16-bit q would change
+    (checked on the CPU when the pools were chosen); every staging mode and
+    the node-lockstep kernel must match the oracle."""
+    fsp = gpu_lib
+    rng = np.random.default_rng(41)
+    for trial in range(8):
+        n = int(rng.integers(3, 8))
+        m = int(rng.integers(3, 10))
+        p = rng.integers(1, 70000, (n, m)).astype(np.int32)
+        p[:, 1] *= 3
+        rows, depths = workloads.random_pool(rng, n, 300, max_depth=n)
+        want = oracle_bounds(p, rows, depths)
+        with fsp.Instance(p) as inst:
+            assert inst.info().compact == 0
+            cfgs = [None, dict(kernel=1, nodes_per_thread=2)]
+            cfgs += [dict(kernel=2, warps_per_block=2, staging=st, positions_per_tile=0 if st == 1 else 4)
+                     for st in (1, 2, 3, 4)]
+            for cfg in cfgs:
+                got = gpu_bounds(fsp, inst, rows, depths, config=cfg)
+                assert np.array_equal(got, want), (trial, cfg, np.nonzero(got != want)[0][:5])
 
 
 def test_pair_tiled_500x20_matches_oracle(gpu_lib):
