@@ -223,6 +223,43 @@ def run_batched_leg(dev, reps: int = 5):
             "work_items": q["work_items"], "bit_exact_vs_plain": bool(same), "launch": "one CUDA-graph replay"}
 
 
+def run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, P: int, reps: int = 10):
+    """Nodes/s against pool size on the same 200x20 instance (the paper varies
+    the pool from 4,096 to 262,144 nodes): each size is a slice of the
+    device-resident pool copies, a new slice every launch, timed with CUDA
+    events; the default launch shape (batches split by couples while the pool
+    leaves SMs idle) beside the same shape with every couple in one work item.
+    Both shapes must give identical bounds."""
+    import torch
+    total = rows_d[0].shape[0]
+    out = []
+    for N in (4096, 8192, 16384, 32768, 65536, 131072):
+        shape = fsp.fsp_tuned_config(inst, N)
+        whole = dict(shape, pairs_per_tile=P)
+        row = {"nodes": N, "launch": shape}
+        for key, cfg in (("default", None), ("one_work_item_per_batch", whole)):
+            for i in range(3):
+                fsp.fsp_bound_pool(inst, rows_d[i % 3][:N], dep_d[i % 3][:N], outs[i % 3][:N], stream=stream,
+                                   config=cfg)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for i in range(reps):
+                lo = (i * N) % (total - N + 1)
+                c = i % 3
+                fsp.fsp_bound_pool(inst, rows_d[c][lo:lo + N], dep_d[c][lo:lo + N], outs[c][lo:lo + N],
+                                   stream=stream, config=cfg)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[key + "_nodes_per_s"] = N * reps / (e0.elapsed_time(e1) * 1e-3)
+        a = fsp.fsp_bound_pool(inst, rows_d[0][:N], dep_d[0][:N], stream=stream)
+        b = fsp.fsp_bound_pool(inst, rows_d[0][:N], dep_d[0][:N], stream=stream, config=whole)
+        torch.cuda.synchronize()
+        row["same_bounds"] = bool(torch.equal(a, b))
+        out.append(row)
+    return out
+
+
 def run_bnb_leg(seeds=(200, 201, 203, 202), node_limit: int = 50_000_000, expand: int = 256):
     """Whole searches of the serving workload (n=20, m=5), NEH upper bound:
     the host-driven DFS (branching on the host, one device pool per
@@ -532,6 +569,7 @@ def run_gpu(args, world, rank, local):
     batched = run_batched_leg(dev) if extra else None
     served = run_served_leg() if extra else None
     bnb = run_bnb_leg() if extra else None
+    sizes = run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, info.pairs) if extra else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": region_ms_max / args.steps, "higher_is_better": True,
@@ -561,6 +599,7 @@ def run_gpu(args, world, rank, local):
         "batched": batched,
         "served": served,
         "bnb_searches": bnb,
+        "pool_sizes": sizes,
     }
     print(json.dumps(line), flush=True)
     inst.close()

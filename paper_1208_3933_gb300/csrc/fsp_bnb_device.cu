@@ -196,18 +196,47 @@ __global__ void bnb_push(const int16_t *crows, const int32_t *cdep, const int32_
 // ---- best-first selection: bring the k open nodes of smallest bound to the
 // top of the stack (positions [S - k, S)), so that the round expands them;
 // among equal bounds the deeper node first (the usual tie-break, which dives
-// to leaves instead of widening a plateau of equal bounds).  The key
-// (lb - lo) * (n + 1) + (n - d) is binned relative to the root's bound (bounds
-// never decrease along a branch): bin = min(key >> shift, nbins - 1).
+// to leaves instead of widening a plateau of equal bounds), and among equal
+// keys the node higher on the stack (the most recently pushed, as depth-first
+// order would take it).  The key (lb - lo) * (n + 1) + (n - d) is binned
+// relative to the root's bound (bounds never decrease along a branch):
+// bin = min(key >> shift, nbins - 1).  Every step is deterministic: the
+// threshold bin's share is taken by stack position through per-tile counts
+// and scans, and the swap lists are built in stack order, so a search
+// expands the same nodes on every run.
 constexpr int kBestBins = 4096;
+constexpr int kTile = 256;  // stack entries per block step of the selection passes
 
 struct BestState {
     int32_t tb;        // threshold bin: every node in a lower bin is selected
-    int32_t need_tb;   // how many nodes of bin tb are selected
-    int32_t taken_tb;  // bin-tb nodes taken so far
+    int32_t need_tb;   // how many nodes of bin tb are selected (the highest on the stack)
     int32_t n_out;     // selected nodes below the top region
     int32_t n_in;      // unselected nodes inside the top region
 };
+
+// Block of kTile threads: how many threads of higher (after) or lower
+// (before) index in the block have f set.
+__device__ __forceinline__ int block_count_after(bool f, int32_t *wsum) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    int c = lane == 31 ? 0 : __popc(bal >> (lane + 1));
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    for (int v = w + 1; v < kTile / 32; ++v) c += wsum[v];
+    __syncthreads();
+    return c;
+}
+
+__device__ __forceinline__ int block_count_before(bool f, int32_t *wsum) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    int c = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    for (int v = 0; v < w; ++v) c += wsum[v];
+    __syncthreads();
+    return c;
+}
 
 __device__ __forceinline__ int best_bin(int32_t lb, int32_t d, int n, int32_t lo, int shift) {
     const int64_t key = (int64_t)(lb < lo ? 0 : lb - lo) * (n + 1) + (n - d);
@@ -232,22 +261,78 @@ __global__ void __launch_bounds__(kScanThreads) bnb_best_threshold(int32_t *hist
             bs->need_tb = k - before;
         }
     }
-    if (threadIdx.x == 0) {
-        bs->taken_tb = 0;
-        bs->n_out = 0;
-        bs->n_in = 0;
+}
+
+// bin-tb nodes per tile of kTile stack entries
+__global__ void __launch_bounds__(kTile) bnb_best_tile_count(const int32_t *slb, const int32_t *sdep, int64_t S,
+                                                            int n, int32_t lo, int shift, const BestState *bs,
+                                                            int32_t *tcount) {
+    const int tb = bs->tb;
+    for (int64_t t = blockIdx.x; t * kTile < S; t += gridDim.x) {
+        const int64_t i = t * kTile + threadIdx.x;
+        const int c = __syncthreads_count(i < S && best_bin(slb[i], sdep[i], n, lo, shift) == tb);
+        if (threadIdx.x == 0) tcount[t] = c;
     }
 }
 
-__global__ void bnb_best_mark(const int32_t *slb, const int32_t *sdep, int64_t S, int n, int k, int32_t lo,
-                              int shift, BestState *bs, int64_t *out_list, int64_t *in_list) {
+// one block: tabove[T - 1 - t] = bin-tb nodes in the tiles above tile t
+__global__ void __launch_bounds__(kScanThreads) bnb_best_tile_above(const int32_t *tcount, int T, int32_t *tabove) {
+    block_exclusive_scan(T, [&](int r) { return tcount[T - 1 - r]; }, tabove);
+}
+
+// Selection of every node: bins below tb, and the need_tb nodes of bin tb
+// highest on the stack; per tile, the selected nodes below the top region
+// and the unselected ones inside it.
+__global__ void __launch_bounds__(kTile) bnb_best_mark(const int32_t *slb, const int32_t *sdep, int64_t S, int n,
+                                                      int k, int32_t lo, int shift, const BestState *bs,
+                                                      const int32_t *tabove, int T, uint8_t *sel_flag,
+                                                      int32_t *out_cnt, int32_t *in_cnt) {
+    __shared__ int32_t wsum[kTile / 32];
+    const int tb = bs->tb, need = bs->need_tb;
     const int64_t top0 = S - k;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
-        const int b = best_bin(slb[i], sdep[i], n, lo, shift);
-        bool sel = b < bs->tb;
-        if (b == bs->tb) sel = atomicAdd(&bs->taken_tb, 1) < bs->need_tb;
-        if (sel && i < top0) out_list[atomicAdd(&bs->n_out, 1)] = i;
-        if (!sel && i >= top0) in_list[atomicAdd(&bs->n_in, 1)] = i;
+    for (int64_t t = blockIdx.x; t * kTile < S; t += gridDim.x) {
+        const int64_t i = t * kTile + threadIdx.x;
+        const int b = i < S ? best_bin(slb[i], sdep[i], n, lo, shift) : kBestBins;
+        const int rank = tabove[T - 1 - t] + block_count_after(b == tb, wsum);
+        const bool sel = b < tb || (b == tb && rank < need);
+        if (i < S) sel_flag[i] = sel ? 1 : 0;
+        const int no = __syncthreads_count(sel && i < top0);
+        const int ni = __syncthreads_count(i < S && !sel && i >= top0);
+        if (threadIdx.x == 0) {
+            out_cnt[t] = no;
+            in_cnt[t] = ni;
+        }
+    }
+}
+
+// one block: list offsets per tile (exclusive scans) and the list lengths
+__global__ void __launch_bounds__(kScanThreads) bnb_best_list_offsets(const int32_t *out_cnt, const int32_t *in_cnt,
+                                                                      int T, int32_t *out_off, int32_t *in_off,
+                                                                      BestState *bs) {
+    block_exclusive_scan(T, [&](int t) { return out_cnt[t]; }, out_off);
+    __syncthreads();
+    block_exclusive_scan(T, [&](int t) { return in_cnt[t]; }, in_off);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bs->n_out = out_off[T];
+        bs->n_in = in_off[T];
+    }
+}
+
+// both swap lists in stack order
+__global__ void __launch_bounds__(kTile) bnb_best_lists(int64_t S, int k, const uint8_t *sel_flag,
+                                                       const int32_t *out_off, const int32_t *in_off,
+                                                       int64_t *out_list, int64_t *in_list) {
+    __shared__ int32_t wsum[kTile / 32];
+    const int64_t top0 = S - k;
+    for (int64_t t = blockIdx.x; t * kTile < S; t += gridDim.x) {
+        const int64_t i = t * kTile + threadIdx.x;
+        const bool sel = i < S && sel_flag[i];
+        const bool o = sel && i < top0, q = i < S && !sel && i >= top0;
+        const int ro = block_count_before(o, wsum);
+        const int rq = block_count_before(q, wsum);
+        if (o) out_list[out_off[t] + ro] = i;
+        if (q) in_list[in_off[t] + rq] = i;
     }
 }
 
@@ -281,14 +366,33 @@ struct DevBuffers {
     int32_t *hist = nullptr;                    // best-first: bins
     BestState *bs = nullptr;                    // best-first: threshold and list lengths
     int64_t *out_list = nullptr, *in_list = nullptr;  // best-first: swap pairs (expand each)
-    int64_t cap = 0;
+    int32_t *tiles = nullptr;                   // best-first: six per-tile arrays of tiles_cap + 1
+    uint8_t *sel_flag = nullptr;                // best-first: selection of every stack entry
+    int64_t cap = 0, tiles_cap = 0;
     void release() {
         for (void *p : {(void *)srows, (void *)crows, (void *)best_row, (void *)sdep, (void *)slb, (void *)cdep,
                         (void *)clb, (void *)cparent, (void *)offs, (void *)keep, (void *)soffs, (void *)st,
-                        (void *)hist, (void *)bs, (void *)out_list, (void *)in_list})
+                        (void *)hist, (void *)bs, (void *)out_list, (void *)in_list, (void *)tiles,
+                        (void *)sel_flag})
             if (p) cudaFree(p);
     }
 };
+
+// Best-first scratch for a stack of b.cap entries (contents not kept).
+fsp_status grow_best(DevBuffers &b) {
+    const int64_t T = (b.cap + kTile - 1) / kTile;
+    if (T <= b.tiles_cap) return FSP_OK;
+    if (b.tiles) cudaFree(b.tiles);
+    if (b.sel_flag) cudaFree(b.sel_flag);
+    b.tiles = nullptr;
+    b.sel_flag = nullptr;
+    b.tiles_cap = 0;
+    if (cudaMalloc((void **)&b.tiles, sizeof(int32_t) * 6 * (size_t)(T + 1)) != cudaSuccess ||
+        cudaMalloc((void **)&b.sel_flag, (size_t)b.cap) != cudaSuccess)
+        return FSP_ENOMEM;
+    b.tiles_cap = T;
+    return FSP_OK;
+}
 
 // Grows the stack to hold `need` nodes, keeping its first `keep_nodes`.
 fsp_status grow_stack(DevBuffers &b, int n, int64_t need, int64_t keep_nodes) {
@@ -414,11 +518,24 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
             const int64_t span = (int64_t)std::max(hst->best - root_lb, 1) * (n + 1);
             while ((span >> shift) >= kBestBins) ++shift;
             const int g = (int)std::min<int64_t>((S + 255) / 256, 1024);
-            note_launches(4);
+            const int64_t T64 = (S + kTile - 1) / kTile;
+            if (T64 > INT32_MAX - 1) return fail(FSP_ENOMEM);
+            const int T = (int)T64, gt = (int)std::min<int64_t>(T64, 4096);
+            st = grow_best(b);
+            if (st != FSP_OK) return fail(st);
+            const size_t ts = (size_t)b.tiles_cap + 1;
+            int32_t *tcount = b.tiles, *tabove = b.tiles + ts, *out_cnt = b.tiles + 2 * ts,
+                    *in_cnt = b.tiles + 3 * ts, *out_off = b.tiles + 4 * ts, *in_off = b.tiles + 5 * ts;
+            note_launches(8);
             if (cudaMemsetAsync(b.hist, 0, sizeof(int32_t) * (kBestBins + 1), s) != cudaSuccess) return fail(FSP_ECUDA);
             bnb_best_hist<<<g, 256, 0, s>>>(b.slb, b.sdep, S, n, root_lb, shift, b.hist);
             bnb_best_threshold<<<1, kScanThreads, 0, s>>>(b.hist, k, b.bs);
-            bnb_best_mark<<<g, 256, 0, s>>>(b.slb, b.sdep, S, n, k, root_lb, shift, b.bs, b.out_list, b.in_list);
+            bnb_best_tile_count<<<gt, kTile, 0, s>>>(b.slb, b.sdep, S, n, root_lb, shift, b.bs, tcount);
+            bnb_best_tile_above<<<1, kScanThreads, 0, s>>>(tcount, T, tabove);
+            bnb_best_mark<<<gt, kTile, 0, s>>>(b.slb, b.sdep, S, n, k, root_lb, shift, b.bs, tabove, T, b.sel_flag,
+                                               out_cnt, in_cnt);
+            bnb_best_list_offsets<<<1, kScanThreads, 0, s>>>(out_cnt, in_cnt, T, out_off, in_off, b.bs);
+            bnb_best_lists<<<gt, kTile, 0, s>>>(S, k, b.sel_flag, out_off, in_off, b.out_list, b.in_list);
             bnb_best_swap<<<(k + 7) / 8, 256, 0, s>>>(b.srows, b.sdep, b.slb, n, b.bs, b.out_list, b.in_list);
         }
         note_launches(2);

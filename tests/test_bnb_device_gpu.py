@@ -125,3 +125,23 @@ def test_best_first_random_instances(gpu_lib, seed):
                                                        selection=fsp.FSP_SELECT_BEST_FIRST)
     assert st == fsp.FSP_OK and best == brute.optimum(p)[0]
     assert st2 == fsp.FSP_ENOTFOUND
+
+
+@pytest.mark.parametrize("seed", [200, 202])
+def test_best_first_is_deterministic(gpu_lib, seed):
+    """The best-first selection takes ties by stack position (no atomic
+    order decides), so a search expands the same nodes on every run: same
+    node count and the same optimal permutation, twice, at the optimum the
+    oracle stored."""
+    fsp = gpu_lib
+    rec = json.load(open(GOLDEN))["results"][str(seed)]
+    p = dict(workloads.serving_searches([seed]))[seed]
+    runs = []
+    with fsp.Instance(p) as inst:
+        for _ in range(2):
+            st, best, perm, nodes = fsp.fsp_branch_and_bound_device(inst, rec["neh"], expand=256,
+                                                                    selection=fsp.FSP_SELECT_BEST_FIRST)
+            assert st == fsp.FSP_OK and best == rec["opt"]
+            assert brute.makespan(p, perm.tolist()) == best
+            runs.append((nodes, perm.tolist()))
+    assert runs[0] == runs[1]
