@@ -410,6 +410,8 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     // pairs per work item: only streamed staging splits a batch by couples
     const int req_g = lanes_groups_per_item(inst, c.pairs_per_tile);
     auto resolved_ppt = [&](int gper) { return gper >= G ? inst->P : gper * 32; };
+    // blocks per SM: chosen with the warps when neither is given, else 1
+    const bool bps_free = !c.blocks_per_sm && !c.warps_per_block;
     if (!c.blocks_per_sm) c.blocks_per_sm = 1;
     const int npad = inst->npad;
     auto fits = [&](int W, int staging, int pos) {
@@ -424,9 +426,14 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     // kernels) or warp (a tile pipeline per warp)
     const int tiled = (c.staging == FSP_STAGING_SPLIT || c.staging == FSP_STAGING_WARP) ? c.staging
                                                                                         : FSP_STAGING_STREAMED;
-    // largest record tile (multiple of 4, at most npad) for W warps; 0 if none
+    // record tile for W warps: the largest multiple of 4 up to min(npad, 96)
+    // that fits (larger tiles leave less L1 to the setup's tables: at 200x20,
+    // 8 warps x 2 blocks, 96 positions 0.99 ms, 128 positions 1.05 ms for
+    // 209,716 nodes), else the largest that fits at all; 0 if none
     auto best_chunk = [&](int W) {
-        for (int ch = npad; ch >= 4; ch -= 4)
+        for (int ch = std::min(npad, 96) & ~3; ch >= 4; ch -= 4)
+            if (fits(W, tiled, ch)) return ch;
+        for (int ch = npad; ch > 96; ch -= 4)
             if (fits(W, tiled, ch)) return ch;
         return 0;
     };
@@ -456,14 +463,18 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     if (tiled != FSP_STAGING_STREAMED && req_g != G) return FSP_EINVAL;
     // Launch model for the defaults: a wave of work items (block batches of
     // 32 W nodes, times S couple slices of gper groups each) takes about
-    // max(warps per SM, 12) x (setup + gper / G of a full scan), the setup
+    // max(warps per SM, 16) x (setup + gper / G of a full scan), the setup
     // costing about a fifth of a full scan; slicing by couples pays for its
-    // repeated setup only when the batches leave SMs idle.
-    const double slots = (double)d.num_sms * c.blocks_per_sm;
+    // repeated setup only when the batches leave SMs idle.  One block per SM
+    // runs about 1.2x slower per warp than two (at 200x20: 14 warps x 1 block
+    // 1.30 ms, 8 warps x 2 blocks 1.08 ms), whose barriers and setups fall
+    // out of phase.
     auto model_time = [&](int W, int gper) {
+        const double slots = (double)d.num_sms * c.blocks_per_sm;
         const double batches = std::ceil((double)std::max<int64_t>(N, 1) / (32.0 * W));
         const double items = batches * std::ceil((double)G / gper);
-        return std::ceil(items / slots) * std::max(W * c.blocks_per_sm, 12) * (0.2 + (double)gper / G);
+        return std::ceil(items / slots) * std::max(W * c.blocks_per_sm, 16) * (0.2 + (double)gper / G) *
+               (c.blocks_per_sm == 1 ? 1.2 : 1.0);
     };
     auto best_gper = [&](int W, double *t) {
         int bg = req_g;
@@ -481,21 +492,30 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     };
     if (!c.warps_per_block) {
         double best = -1.0;
-        int bW = 0;
-        for (int W = 16 / c.blocks_per_sm; W >= 1; --W) {
-            const int ch = c.positions_per_tile ? c.positions_per_tile : best_chunk(W);
-            if (ch < 4 || !fits(W, tiled, ch)) continue;
-            if (!c.positions_per_tile && ch < std::min(npad, 64)) continue;
-            double t = 0.0;
-            best_gper(W, &t);
-            const double score = 1.0 / t;
-            if (score > best * (1.0 + 1e-9)) {
-                best = score;
-                bW = W;
+        int bW = 0, bB = c.blocks_per_sm;
+        const int bps_lo = c.blocks_per_sm, bps_hi = bps_free ? 2 : c.blocks_per_sm;
+        for (int bps = bps_hi; bps >= bps_lo; --bps) {
+            c.blocks_per_sm = bps;
+            for (int W = 16 / bps; W >= 1; --W) {
+                // even warp counts above 2 (odd ones measured slower: 7 x 2
+                // blocks 1.29 ms, 8 x 2 1.08 ms at 200x20)
+                if (W > 2 && (W & 1)) continue;
+                const int ch = c.positions_per_tile ? c.positions_per_tile : best_chunk(W);
+                if (ch < 4 || !fits(W, tiled, ch)) continue;
+                if (!c.positions_per_tile && ch < std::min(npad, 64)) continue;
+                double t = 0.0;
+                best_gper(W, &t);
+                const double score = 1.0 / t;
+                if (score > best * (1.0 + 1e-9)) {
+                    best = score;
+                    bW = W;
+                    bB = bps;
+                }
             }
         }
         if (best < 0) return FSP_EINVAL;
         c.warps_per_block = bW;
+        c.blocks_per_sm = bB;
     }
     c.pairs_per_tile = resolved_ppt(best_gper(c.warps_per_block, nullptr));
     if (!c.positions_per_tile) c.positions_per_tile = best_chunk(c.warps_per_block);
@@ -683,6 +703,18 @@ extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_
     int64_t ends[kMaxChunks + 1] = {0};
     for (int64_t c = 0; c < nchunks; ++c)
         ends[c + 1] = c + 1 == nchunks ? N : std::max(ends[c], std::min(N, (int64_t)(kChunkEnds[c] * (double)N)));
+    // every chunk is bounded with the launch shape tuned for the whole pool,
+    // when the caller tuned one (the chunks' own sizes have none)
+    fsp_launch_config tuned = {};
+    bool have_tuned = false;
+    {
+        std::lock_guard<std::mutex> g(inst->mu);
+        for (auto &e : inst->tuned)
+            if (e.first == N) {
+                tuned = e.second;
+                have_tuned = true;
+            }
+    }
     std::lock_guard<std::mutex> host_lock(inst->host_mu);
     cudaStream_t &cpy = inst->host_streams[0], &comp2 = inst->host_streams[1];
     cudaEvent_t &ev_start = inst->host_events[0], &ev_done = inst->host_events[1];
@@ -724,7 +756,8 @@ extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_
             }
             cudaStream_t s = (c & 1) ? comp2 : user;
             cudaStreamWaitEvent(s, ev_in[c], 0);
-            st = launch_bound(inst, d_nodes + lo * n, d_depths + lo, hi - lo, d_out + lo, s, nullptr);
+            st = launch_bound(inst, d_nodes + lo * n, d_depths + lo, hi - lo, d_out + lo, s,
+                              have_tuned ? &tuned : nullptr);
             if (st != FSP_OK) break;
             if (cudaMemcpyAsync(out_lb + lo, d_out + lo, sizeof(int32_t) * rows, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess)
