@@ -110,7 +110,11 @@ typedef struct fsp_launch_config {
     int32_t warps_per_block;     /* lanes: 1..16 warps of 32 nodes */
     int32_t positions_per_tile;  /* lanes, streamed/split/warp: Johnson positions per tile (multiple of 4) */
     int32_t staging;             /* lanes: FSP_STAGING_* */
-    int32_t reserved;
+    int32_t tail_slices;         /* lanes, streamed, every couple per work item: the block
+                                    batches of the last partial wave are split into this many
+                                    couple slices (at most G), so that they occupy more of the
+                                    grid; 0 or 1 = none (the default; the autotuner also tries
+                                    2 and 3); other stagings: 1 */
 } fsp_launch_config;
 
 /*

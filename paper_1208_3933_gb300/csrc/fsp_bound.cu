@@ -404,7 +404,7 @@ fsp_status resolve_lockstep(const fsp_instance *inst, int64_t N, const DeviceLim
 fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits &d, fsp_launch_config &c) {
     if (c.warps_per_block < 0 || c.warps_per_block > 16 || c.positions_per_tile < 0 ||
         (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 4 || c.blocks_per_sm < 0 || c.blocks_per_sm > 2 ||
-        c.pairs_per_tile < 0)
+        c.pairs_per_tile < 0 || c.tail_slices < 0)
         return FSP_EINVAL;
     const int G = inst->G;
     // pairs per work item: only streamed staging splits a batch by couples
@@ -449,18 +449,19 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
                 break;
             }
         }
-        if (bW && req_g == G) {
+        if (bW && req_g == G && c.tail_slices <= 1) {
             c.warps_per_block = bW;
             c.staging = FSP_STAGING_RESIDENT;
             c.positions_per_tile = 0;
             c.blocks_per_sm = 1;
             c.pairs_per_tile = inst->P;
+            c.tail_slices = 1;
             return FSP_OK;
         }
         return FSP_EINVAL;
     }
     c.staging = tiled;
-    if (tiled != FSP_STAGING_STREAMED && req_g != G) return FSP_EINVAL;
+    if (tiled != FSP_STAGING_STREAMED && (req_g != G || c.tail_slices > 1)) return FSP_EINVAL;
     // Launch model for the defaults: a wave of work items (block batches of
     // 32 W nodes, times S couple slices of gper groups each) takes about
     // max(warps per SM, 16) x (setup + gper / G of a full scan), the setup
@@ -469,17 +470,32 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     // runs about 1.2x slower per warp than two (at 200x20: 14 warps x 1 block
     // 1.30 ms, 8 warps x 2 blocks 1.08 ms), whose barriers and setups fall
     // out of phase.
+    // Streamed staging with whole batches may slice the last partial wave's
+    // batches (tail_slices, on request or from the tuner; the model below
+    // takes it into account when requested).
+    const bool tail_ok = tiled == FSP_STAGING_STREAMED && c.tail_slices > 1;
+    auto tail_for = [&](int64_t batches, int64_t slots) -> int {
+        const int64_t r = batches % slots;
+        if (batches <= slots || r == 0) return 1;
+        return std::min(G, c.tail_slices);
+    };
     auto model_time = [&](int W, int gper) {
-        const double slots = (double)d.num_sms * c.blocks_per_sm;
-        const double batches = std::ceil((double)std::max<int64_t>(N, 1) / (32.0 * W));
-        const double items = batches * std::ceil((double)G / gper);
-        return std::ceil(items / slots) * std::max(W * c.blocks_per_sm, 16) * (0.2 + (double)gper / G) *
-               (c.blocks_per_sm == 1 ? 1.2 : 1.0);
+        const int64_t slots = (int64_t)d.num_sms * c.blocks_per_sm;
+        const int64_t batches = (std::max<int64_t>(N, 1) + 32 * W - 1) / (32 * W);
+        const double occ = std::max(W * c.blocks_per_sm, 16) * (c.blocks_per_sm == 1 ? 1.2 : 1.0);
+        if (gper < G) {
+            const double items = (double)batches * std::ceil((double)G / gper);
+            return std::ceil(items / (double)slots) * occ * (0.2 + (double)gper / G);
+        }
+        const int st = tail_ok ? tail_for(batches, slots) : 1;
+        const int64_t full_waves = st > 1 ? batches / slots : (batches + slots - 1) / slots;
+        const double tail = st > 1 ? 0.2 + std::ceil((double)G / st) / G : 0.0;
+        return ((double)full_waves * 1.2 + tail) * occ;
     };
     auto best_gper = [&](int W, double *t) {
         int bg = req_g;
         double bt = model_time(W, req_g);
-        if (!c.pairs_per_tile && tiled == FSP_STAGING_STREAMED)
+        if (!c.pairs_per_tile && tiled == FSP_STAGING_STREAMED && c.tail_slices <= 1)
             for (int g = G - 1; g >= 1; --g) {
                 const double tg = model_time(W, g);
                 if (tg < bt * (1.0 - 1e-9)) {
@@ -517,7 +533,21 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
         c.warps_per_block = bW;
         c.blocks_per_sm = bB;
     }
-    c.pairs_per_tile = resolved_ppt(best_gper(c.warps_per_block, nullptr));
+    const int gper = best_gper(c.warps_per_block, nullptr);
+    c.pairs_per_tile = resolved_ppt(gper);
+    if (gper < G) {
+        if (c.tail_slices > 1) return FSP_EINVAL;  // already split throughout
+        c.tail_slices = 1;
+    } else if (tiled != FSP_STAGING_STREAMED) {
+        c.tail_slices = 1;
+    } else if (c.tail_slices == 0) {
+        // none by default: slicing the last wave measured 5-15% faster for
+        // some pool sizes and up to 10% slower for others (at 200x20, 262,144
+        // nodes: 1.08 ms whole, 1.20 ms in two slices -- the last wave holds
+        // the deepest nodes, whose setups the slices repeat), so the tuner
+        // decides
+        c.tail_slices = 1;
+    }
     if (!c.positions_per_tile) c.positions_per_tile = best_chunk(c.warps_per_block);
     if (c.positions_per_tile < 4) return FSP_EINVAL;
     return fits(c.warps_per_block, tiled, c.positions_per_tile) ? FSP_OK : FSP_EINVAL;
@@ -554,7 +584,7 @@ fsp_status resolve_config(const fsp_instance *inst, int64_t N, const fsp_launch_
     if (req) c = *req;
     if (c.kernel < 0 || c.kernel > 2) return FSP_EINVAL;
     const bool unset = c.kernel == 0 && !c.nodes_per_thread && !c.blocks_per_sm && !c.pairs_per_tile &&
-                       !c.warps_per_block && !c.positions_per_tile && !c.staging;
+                       !c.warps_per_block && !c.positions_per_tile && !c.staging && !c.tail_slices;
     if (unset) {
         std::lock_guard<std::mutex> g(inst->mu);
         for (auto &e : inst->tuned)

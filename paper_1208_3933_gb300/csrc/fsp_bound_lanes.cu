@@ -159,26 +159,31 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
         const unsigned char *src = a.grec + ((size_t)g * a.npad + (size_t)ch * a.chunk) * 32 * a.rec_bytes;
         tp.issue(fill, src, (uint32_t)pos * 32u * a.rec_bytes);
     };
-    // Work items: a block batch of 32 W nodes times a slice of gper couple
-    // groups (S slices cover all groups; S = 1 unless small pools are split
-    // by couples to occupy more SMs).  Item it = batch it / S, slice it % S;
-    // the host keeps the item count below 2^31 when S > 1.
+    // Work items: block batches of 32 W nodes, the first `full` of them whole
+    // (all couple groups), each later one split into S slices of gper couple
+    // groups.  S = 1 unless a small pool is split by couples throughout
+    // (full = 0) to occupy more SMs, or the batches of the last partial wave
+    // are (full = the batches before it).  Sliced item it = batch full +
+    // (it - full) / S, slice (it - full) % S; the host keeps the sliced item
+    // count below 2^31.
     const uint32_t S = a.gslices > 1 ? (uint32_t)a.gslices : 1u;
+    const int64_t full = S > 1 ? a.full_batches : a.num_batches;
     const int gper = S > 1 ? a.gper : a.G;
-    const int64_t items = a.num_batches * S;
-    auto slice_of = [&](int64_t it) { return S > 1 ? (int)((uint32_t)it % S) : 0; };
+    const int64_t items = full + (a.num_batches - full) * S;
+    auto slice_of = [&](int64_t it) { return it < full ? -1 : (int)((uint32_t)(it - full) % S); };
+    auto first_tile = [&](int sl) { return sl < 0 ? 0 : sl * gper * a.nchunks; };
     if (threadIdx.x == 0 && (int64_t)blockIdx.x < items) {
         if (tp.resident) {
             tile_issue(0, 0);
             if (a.ntiles == 2) tile_issue(1, 1);
         } else {
-            tile_issue(0, slice_of(blockIdx.x) * gper * a.nchunks);
+            tile_issue(0, first_tile(slice_of(blockIdx.x)));
         }
     }
 
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int sl = slice_of(it);
-        const int64_t bt = S > 1 ? (int64_t)((uint32_t)it / S) : it;
+        const int64_t bt = sl < 0 ? it : full + (int64_t)((uint32_t)(it - full) / S);
         const int64_t x = node_at(a, bt * (int64_t)(32 * W) + warp * 32 + lane);
         int bterm = 0;
         const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
@@ -192,13 +197,13 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
             ui[b] = 0;
         }
         int kk = 0, ll = 1;
-        const int t1 = min(a.G, (sl + 1) * gper) * a.nchunks;
-        for (int t = sl * gper * a.nchunks; t < t1; ++t) {
+        const int t1 = sl < 0 ? a.ntiles : min(a.G, (sl + 1) * gper) * a.nchunks;
+        for (int t = first_tile(sl); t < t1; ++t) {
             const int g = t / a.nchunks, ch = t - g * a.nchunks;
             if (!tp.resident && threadIdx.x == 0) {
                 // the next tile of this item, else the first of the block's next item
                 const int next = t + 1 < t1 ? t + 1
-                                 : (it + gridDim.x < items ? slice_of(it + gridDim.x) * gper * a.nchunks : -1);
+                                 : (it + gridDim.x < items ? first_tile(slice_of(it + gridDim.x)) : -1);
                 if (next >= 0) tile_issue(tp.fill + 1, next);
             }
             if (!tp.wait(t, a.wait_limit)) {
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
         }
         const int best = transpose_max(lb, lane);
         if (x < a.N) {
-            if (S == 1)
+            if (sl < 0)
                 a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
             else if (!valid)
                 a.out[x] = FSP_LB_INVALID;  // every slice finds the row invalid
@@ -394,11 +399,21 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
         grid = (int)std::min<int64_t>((a.num_batches + per_block - 1) / per_block, (int64_t)num_sms(inst->device));
     } else {
         a.num_batches = (N + 32 * W - 1) / (32 * W);
+        const int bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 1;
+        const int64_t slots = (int64_t)num_sms(inst->device) * bps;
         a.gper = lanes_groups_per_item(inst, cfg.pairs_per_tile);
         a.gslices = (inst->G + a.gper - 1) / a.gper;
-        if (a.gslices > 1 && a.num_batches * a.gslices >= ((int64_t)1 << 31)) return FSP_EINVAL;
-        const int bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 1;
-        grid = (int)std::min<int64_t>(a.num_batches * a.gslices, (int64_t)num_sms(inst->device) * bps);
+        a.full_batches = 0;
+        if (a.gslices == 1 && cfg.tail_slices > 1 && a.num_batches > slots) {
+            // whole batches in full waves, the last partial wave's batches sliced
+            const int st = std::min(cfg.tail_slices, inst->G);
+            a.gper = (inst->G + st - 1) / st;
+            a.gslices = (inst->G + a.gper - 1) / a.gper;
+            a.full_batches = a.num_batches - a.num_batches % slots;
+            if (a.full_batches == a.num_batches) a.gslices = 1;
+        }
+        if (a.gslices > 1 && (a.num_batches - a.full_batches) * a.gslices >= ((int64_t)1 << 31)) return FSP_EINVAL;
+        grid = (int)std::min<int64_t>(a.full_batches + (a.num_batches - a.full_batches) * a.gslices, slots);
     }
     grid = std::max(grid, 1);
     cudaStream_t s = static_cast<cudaStream_t>(stream);

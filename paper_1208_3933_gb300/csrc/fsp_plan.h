@@ -46,7 +46,8 @@ struct LanesArgs {
     int32_t q32;          // q stored as int32: instances with 128-bit records, whose tails may pass 2^15
     int32_t release;      // 0: release times from the head minima; 1: per-job earliest starts
     int32_t gper;         // streamed: couple groups per work item (slices of a block batch)
-    int32_t gslices;      // streamed: work items per block batch, ceil(G / gper); 0 or 1 = no split
+    int32_t gslices;      // streamed: work items per sliced block batch, ceil(G / gper); 0 or 1 = no split
+    int64_t full_batches; // streamed, gslices > 1: block batches [0, full_batches) are whole work items
     long long wait_limit;
 };
 

@@ -43,8 +43,9 @@ bool cache_lookup(const char *path, const std::string &key, fsp_launch_config *c
         const size_t kl = key.size();
         if (std::strncmp(line, key.c_str(), kl) != 0 || line[kl] != ' ') continue;
         fsp_launch_config c = {};
-        if (std::sscanf(line + kl, " => %d %d %d %d %d %d %d", &c.kernel, &c.nodes_per_thread, &c.blocks_per_sm,
-                        &c.pairs_per_tile, &c.warps_per_block, &c.positions_per_tile, &c.staging) == 7) {
+        if (std::sscanf(line + kl, " => %d %d %d %d %d %d %d %d", &c.kernel, &c.nodes_per_thread, &c.blocks_per_sm,
+                        &c.pairs_per_tile, &c.warps_per_block, &c.positions_per_tile, &c.staging,
+                        &c.tail_slices) >= 7) {
             *cfg = c;  // the last entry for a key wins
             found = true;
         }
@@ -57,8 +58,9 @@ void cache_store(const char *path, const std::string &key, const fsp_launch_conf
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s => %d %d %d %d %d %d %d  # %.4f ms\n", key.c_str(), c.kernel, c.nodes_per_thread,
-                 c.blocks_per_sm, c.pairs_per_tile, c.warps_per_block, c.positions_per_tile, c.staging, ms);
+    std::fprintf(f, "%s => %d %d %d %d %d %d %d %d  # %.4f ms\n", key.c_str(), c.kernel, c.nodes_per_thread,
+                 c.blocks_per_sm, c.pairs_per_tile, c.warps_per_block, c.positions_per_tile, c.staging,
+                 c.tail_slices, ms);
     std::fclose(f);
 }
 
@@ -94,18 +96,32 @@ std::vector<fsp_launch_config> candidates(const fsp_instance *inst, int64_t N) {
                 c.staging = staging;
                 c.positions_per_tile = pos;
                 c.pairs_per_tile = 0;
+                c.tail_slices = 0;
                 add(c);
                 if (W <= 8) {
                     fsp_launch_config c2 = c;
                     c2.blocks_per_sm = 2;
                     add(c2);
                 }
+                // pools of more than one wave: the last partial wave's batches
+                // split by couples as well
+                if (staging == FSP_STAGING_STREAMED && pos == 0 && N > 32 * W * (int64_t)sms)
+                    for (int ts : {2, 3}) {
+                        fsp_launch_config c3 = c;
+                        c3.tail_slices = ts;
+                        add(c3);
+                        if (W <= 8) {
+                            c3.blocks_per_sm = 2;
+                            add(c3);
+                        }
+                    }
                 // pools of under two waves of block batches: work items of
                 // fewer couples (streamed staging) as well
                 if (staging == FSP_STAGING_STREAMED && pos == 0 && N < 2 * 32 * W * (int64_t)sms)
                     for (int ppt : {32, 64, 96}) {
                         if (ppt >= inst->P) break;
                         c.pairs_per_tile = ppt;
+                        c.tail_slices = 0;
                         add(c);
                         if (W <= 8) {
                             fsp_launch_config c2 = c;

@@ -60,10 +60,10 @@ class fsp_launch_config(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("pairs_per_tile", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("positions_per_tile", ctypes.c_int32),
-                ("staging", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("staging", ctypes.c_int32), ("tail_slices", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 class fsp_pool_desc(ctypes.Structure):

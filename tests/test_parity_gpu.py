@@ -140,15 +140,45 @@ def test_couple_slices_with_depth_order_release_and_wide_records(gpu_lib):
     assert np.array_equal(got, oracle_bounds(p, rows, depths))
 
 
+@pytest.mark.parametrize("ts", [2, 3, 6])
+@pytest.mark.parametrize("W,bps", [(1, 1), (2, 2)])
+def test_tail_sliced_batches_match_oracle(gpu_lib, ts, W, bps):
+    """Pools of more than one wave of block batches whose last partial wave
+    is split by couples (tail_slices 2, 3 and 6 of the 6 groups at m = 20):
+    the whole batches store their bounds, the tail's slices meet in the
+    atomic max; the last batch is ragged and the pool holds invalid rows."""
+    import torch
+    fsp = gpu_lib
+    slots = torch.cuda.get_device_properties(0).multi_processor_count * bps
+    N = (slots + 37) * 32 * W + 19
+    p, rows, depths = pool(640 + ts, 40, 20, N)
+    depths[[5, N - 3]] = [-1, 41]
+    rows[N - 1, :2] = [7, 7]
+    depths[N - 1] = max(int(depths[N - 1]), 2)
+    cfg = dict(kernel=2, staging=2, warps_per_block=W, blocks_per_sm=bps, positions_per_tile=12, tail_slices=ts)
+    with fsp.Instance(p) as inst:
+        got = gpu_bounds(fsp, inst, rows, depths, config=cfg)
+        whole = gpu_bounds(fsp, inst, rows, depths, config=dict(cfg, tail_slices=1))
+    assert np.array_equal(got, whole)
+    assert got[5] == got[N - 3] == got[N - 1] == fsp.FSP_LB_INVALID
+    idx = np.concatenate([np.arange(0, N, 97), np.arange(N - 40 * 32 * W, N)])
+    assert np.array_equal(got[idx], oracle_bounds(p, rows[idx], depths[idx]))
+
+
 def test_couple_slices_refused_outside_streamed_staging(gpu_lib):
     import torch
     fsp = gpu_lib
     p, rows, depths = pool(2, 30, 12, 100)
     r, d = to_dev(rows, depths)
     with fsp.Instance(p) as inst:
+        # slices throughout and slices of the last wave exclude each other
+        with pytest.raises(fsp.FspError):
+            fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=2, pairs_per_tile=32, tail_slices=2))
         for staging in (1, 3, 4):
             with pytest.raises(fsp.FspError):
                 fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=staging, pairs_per_tile=32))
+            with pytest.raises(fsp.FspError):
+                fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=staging, tail_slices=2))
             # all couples in one work item is every staging's own shape
             out = fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=staging, pairs_per_tile=66))
             torch.cuda.synchronize()
