@@ -720,30 +720,54 @@ extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_
 
     // Staged through device memory in chunks: the copies go back to back on
     // a copy stream, each chunk's bounding waits only for its own copy, and
-    // consecutive chunks are bounded on two streams so one chunk's last wave
-    // overlaps the next chunk's first.  Chunk ends are fractions of the pool:
-    // a small first chunk starts the bounding early, and few chunks keep each
-    // launch's last partial wave and depth order from repeating too often
-    // (at 200x20: 20/80 % 1.62 ms per pool, four equal chunks 1.67 ms, one
-    // chunk 1.89 ms; reading page-locked pools in place over the host link
-    // 1.55-2.2 ms depending on the box).
-    constexpr int kMaxChunks = 4;
-    static const double kChunkEnds[] = {0.2, 1.0};
-    const int64_t nchunks = N >= 32768 ? (int64_t)(sizeof(kChunkEnds) / sizeof(kChunkEnds[0])) : 1;
-    int64_t ends[kMaxChunks + 1] = {0};
-    for (int64_t c = 0; c < nchunks; ++c)
-        ends[c + 1] = c + 1 == nchunks ? N : std::max(ends[c], std::min(N, (int64_t)(kChunkEnds[c] * (double)N)));
-    // every chunk is bounded with the launch shape tuned for the whole pool,
-    // when the caller tuned one (the chunks' own sizes have none)
-    fsp_launch_config tuned = {};
+    // consecutive chunks are bounded on two streams, so one chunk's last wave
+    // overlaps the next chunk's first.  Every chunk is bounded with the launch
+    // shape tuned for the whole pool when the caller tuned one (the chunks'
+    // own sizes have none), else with the default shape of the pool.
+    fsp_launch_config shape = {};
     bool have_tuned = false;
     {
         std::lock_guard<std::mutex> g(inst->mu);
         for (auto &e : inst->tuned)
             if (e.first == N) {
-                tuned = e.second;
+                shape = e.second;
                 have_tuned = true;
             }
+    }
+    if (!have_tuned) {
+        size_t smem = 0;
+        st = resolve_config(inst, N, nullptr, &shape, &smem);
+        if (st != FSP_OK) return st;
+    }
+    // Chunk ends.  With the couple-lanes streamed shape, a first chunk of two
+    // thirds of a wave of block batches (bounding starts after a short copy),
+    // then whole waves, so that every launch but the last fills the grid; the
+    // copies (about 2 ns per 200-job node at 207 GB/s here, against about
+    // 4 ns of bounding) stay ahead.  At 200x20: 1.32 ms per 262,144-node
+    // pool, against 1.56 ms for a 20/80 split and 1.64 ms for one chunk.
+    // Pools under two waves, or other shapes: 20/80 from 32,768 nodes.
+    constexpr int kMaxChunks = 8;
+    int64_t ends[kMaxChunks + 1] = {0};
+    int nchunks = 1;
+    ends[1] = N;
+    const int64_t wave = (shape.kernel == FSP_KERNEL_LANES && shape.staging == FSP_STAGING_STREAMED)
+                             ? (int64_t)num_sms(inst->device) * std::max(1, shape.blocks_per_sm) * 32 *
+                                   shape.warps_per_block
+                             : 0;
+    if (wave > 0 && N >= 2 * wave) {
+        const int64_t first = wave * 2 / 3;
+        // whole waves per chunk, enough of them to stay within kMaxChunks
+        const int64_t rest_waves = (N - first + wave - 1) / wave;
+        const int64_t step = (rest_waves + kMaxChunks - 2) / (kMaxChunks - 1) * wave;
+        ends[1] = first;
+        while (ends[nchunks] < N) {
+            ends[nchunks + 1] = std::min(N, ends[nchunks] + step);
+            ++nchunks;
+        }
+    } else if (N >= 32768) {
+        nchunks = 2;
+        ends[1] = N / 5;
+        ends[2] = N;
     }
     std::lock_guard<std::mutex> host_lock(inst->host_mu);
     cudaStream_t &cpy = inst->host_streams[0], &comp2 = inst->host_streams[1];
@@ -758,7 +782,7 @@ extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_
     for (int i = 0; st == FSP_OK && i < 2; ++i)
         if (!inst->host_streams[i] && cudaStreamCreateWithFlags(&inst->host_streams[i], cudaStreamNonBlocking) != cudaSuccess)
             st = FSP_ECUDA;
-    for (int i = 0; st == FSP_OK && i < 6; ++i)
+    for (int i = 0; st == FSP_OK && i < 2 + kMaxChunks; ++i)
         if (!inst->host_events[i] && cudaEventCreateWithFlags(&inst->host_events[i], cudaEventDisableTiming) != cudaSuccess)
             st = FSP_ECUDA;
     if (st == FSP_OK &&
@@ -786,8 +810,7 @@ extern "C" fsp_status fsp_bound_pool_host(const fsp_instance *inst, const int16_
             }
             cudaStream_t s = (c & 1) ? comp2 : user;
             cudaStreamWaitEvent(s, ev_in[c], 0);
-            st = launch_bound(inst, d_nodes + lo * n, d_depths + lo, hi - lo, d_out + lo, s,
-                              have_tuned ? &tuned : nullptr);
+            st = launch_bound(inst, d_nodes + lo * n, d_depths + lo, hi - lo, d_out + lo, s, &shape);
             if (st != FSP_OK) break;
             if (cudaMemcpyAsync(out_lb + lo, d_out + lo, sizeof(int32_t) * rows, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess)

@@ -95,7 +95,7 @@ struct fsp_instance {
     // made on first use and kept; host_mu serialises that entry point's calls
     mutable std::mutex host_mu;
     mutable cudaStream_t host_streams[2] = {nullptr, nullptr};
-    mutable cudaEvent_t host_events[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    mutable cudaEvent_t host_events[10] = {};  // start, done, one per chunk (at most 8)
     mutable std::mutex mu;          // guards the tuning cache below
     mutable std::vector<std::pair<int64_t, fsp_launch_config>> tuned;  // pool-size bucket -> shape
 };

@@ -316,6 +316,29 @@ def test_host_buffer_entry_point(gpu_lib):
         assert np.array_equal(po.numpy(), want)
 
 
+def test_host_entry_point_wave_chunks(gpu_lib):
+    """Pools of two to nine waves of block batches: the host path stages
+    them as a first chunk of two thirds of a wave and then whole waves (at
+    most eight chunks, so the largest pool takes two waves per chunk); its
+    bounds equal the device path's on every node and the oracle's on a
+    sample, with and without a tuned shape."""
+    import torch
+    fsp = gpu_lib
+    for N in (160001, 700001):
+        w = workloads.named_pool("pool_20x20", N=N)
+        r, d = to_dev(w.rows, w.depths)
+        with fsp.Instance(w.p) as inst:
+            dev = fsp.fsp_bound_pool(inst, r, d)
+            torch.cuda.synchronize()
+            dev = dev.cpu().numpy()
+            assert np.array_equal(fsp.fsp_bound_pool_host(inst, w.rows, w.depths), dev)
+            if N == 160001:
+                fsp.fsp_autotune(inst, r, d)
+                assert np.array_equal(fsp.fsp_bound_pool_host(inst, w.rows, w.depths), dev)
+        idx = np.random.default_rng(N).choice(N, 3000, replace=False)
+        assert np.array_equal(dev[idx], oracle_bounds(w.p, w.rows[idx], w.depths[idx]))
+
+
 def test_side_stream_and_repeat_calls(gpu_lib):
     import torch
     fsp = gpu_lib
