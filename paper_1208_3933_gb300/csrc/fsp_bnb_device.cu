@@ -15,8 +15,12 @@
 //      incumbent, and pushes the survivors back where the parents were, the
 //      children of the topmost parent on top and, within a parent, in
 //      decreasing (bound, job) order so that the smallest is popped first.
-// The host reads two counters per round (children generated, new stack size)
-// to size the next launches.
+// The round's sizes (stack size, parents popped, children generated) live in
+// device state that the round kernels read, so a depth-first search enqueues
+// rounds back to back and the host reads the state once per group of rounds
+// (stack growth, node limit, termination) -- no host round trip per pool.
+// Best-first selection and searches whose children would need a large
+// bounding launch read the state once per round instead.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +42,11 @@ struct DevState {
     int32_t total;         // children generated this round
     int32_t survivors;     // children pushed this round
     unsigned long long round_key;  // (makespan << 32) | child of this round's best leaf
+    long long S;           // open nodes on the stack
+    long long top0;        // first parent popped this round (S - k)
+    long long count;       // nodes bounded so far
+    int32_t k;             // parents popped this round
+    int32_t pad;
 };
 
 // Block-wide exclusive scan of `count(i)` over i in [0, k): out[i] and the
@@ -69,13 +78,18 @@ __device__ void block_exclusive_scan(int k, CountF count, int32_t *out) {
 
 // (1)+(2a) children per popped parent: n - d for a parent still below the
 // incumbent, else 0; offsets of each parent's children.
-__global__ void __launch_bounds__(kScanThreads) bnb_count_children(const int32_t *sdep, const int32_t *slb,
-                                                                     int64_t top0, int k, int n, DevState *st,
-                                                                     int32_t *offs) {
+// The round pops k = min(K, S) parents from the top of the stack.
+__global__ void __launch_bounds__(kScanThreads) bnb_count_children(const int32_t *sdep, const int32_t *slb, int K,
+                                                                     int n, DevState *st, int32_t *offs) {
     const int32_t best = st->best;
+    const int64_t S = st->S;
+    const int k = (int)(S < K ? S : K);
+    const int64_t top0 = S - k;
     block_exclusive_scan(
         k, [&](int i) { return slb[top0 + i] < best ? n - sdep[top0 + i] : 0; }, offs);
     if (threadIdx.x == 0) {
+        st->k = k;
+        st->top0 = top0;
         st->total = offs[k];
         st->round_key = ~0ull;
     }
@@ -83,11 +97,12 @@ __global__ void __launch_bounds__(kScanThreads) bnb_count_children(const int32_t
 
 // (2b) one warp per parent writes its children: the parent's prefix plus one
 // unscheduled job, in job order.
-__global__ void bnb_make_children(const int16_t *srows, const int32_t *sdep, int64_t top0, int k, int n,
+__global__ void bnb_make_children(const int16_t *srows, const int32_t *sdep, int n, const DevState *st,
                                   const int32_t *offs, int16_t *crows, int32_t *cdep, int32_t *cparent) {
     const int lane = threadIdx.x & 31;
     const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (p >= k) return;
+    if (p >= st->k) return;
+    const int64_t top0 = st->top0;
     const int c0 = offs[p], cnt = offs[p + 1] - c0;
     if (cnt == 0) return;
     const int d = sdep[top0 + p];
@@ -125,10 +140,9 @@ __global__ void bnb_make_children(const int16_t *srows, const int32_t *sdep, int
 
 // (4a) leaves update the round's best; other children survive while their
 // bound is below the incumbent.
-__global__ void bnb_filter(const int32_t *clb, const int32_t *cdep, int total, int n, DevState *st,
-                           int32_t *keep) {
+__global__ void bnb_filter(const int32_t *clb, const int32_t *cdep, int n, DevState *st, int32_t *keep) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= total) return;
+    if (c >= st->total) return;
     const int32_t best = st->best, lb = clb[c];
     int kv = 0;
     if (lb >= 0 && lb < best) {
@@ -155,9 +169,11 @@ __global__ void bnb_incumbent(const int16_t *crows, int n, DevState *st, int16_t
     }
 }
 
-// (4c) survivors per parent and their offsets in the stack.
-__global__ void __launch_bounds__(kScanThreads) bnb_count_survivors(const int32_t *offs, const int32_t *keep, int k,
+// (4c) survivors per parent and their offsets in the stack; the new stack
+// size (the survivors replace the popped parents) and the node count.
+__global__ void __launch_bounds__(kScanThreads) bnb_count_survivors(const int32_t *offs, const int32_t *keep,
                                                                       DevState *st, int32_t *soffs) {
+    const int k = st->k;
     block_exclusive_scan(
         k,
         [&](int p) {
@@ -166,16 +182,21 @@ __global__ void __launch_bounds__(kScanThreads) bnb_count_survivors(const int32_
             return s;
         },
         soffs);
-    if (threadIdx.x == 0) st->survivors = soffs[k];
+    if (threadIdx.x == 0) {
+        st->survivors = soffs[k];
+        st->S = st->top0 + soffs[k];
+        st->count += st->total;
+    }
 }
 
 // (4d) push: survivor c of parent p goes to top0 + soffs[p] + (number of
 // surviving siblings with a larger (bound, job)).
 __global__ void bnb_push(const int16_t *crows, const int32_t *cdep, const int32_t *clb, const int32_t *cparent,
-                         const int32_t *offs, const int32_t *keep, const int32_t *soffs, int total, int n, int64_t top0,
+                         const int32_t *offs, const int32_t *keep, const int32_t *soffs, int n, const DevState *st,
                          int16_t *srows, int32_t *sdep, int32_t *slb) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= total || !keep[c]) return;
+    if (c >= st->total || !keep[c]) return;
+    const int64_t top0 = st->top0;
     const int p = cparent[c];
     const int32_t lb = clb[c];
     const int d = cdep[c];
@@ -492,12 +513,23 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
         init.best = (int32_t)std::min<int64_t>((int64_t)ub0 + 1, INT32_MAX);
         init.found = 0;
         init.round_key = ~0ull;
+        init.S = 1;
+        init.count = 1;
         *hst = init;
         if (cudaMemcpyAsync(b.st, hst, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return fail(FSP_ECUDA);
     }
-    int64_t S = 1;  // stack size
+    // A depth-first search whose rounds bound at most kAsyncMaxChildren
+    // children enqueues kRoundsPerSync rounds at a time, each bounding every
+    // child slot (slots past the round's children hold stale rows, bounded
+    // and ignored); otherwise the host reads the round's child count and
+    // bounds exactly those.
+    constexpr int64_t kAsyncMaxChildren = 16384;
+    constexpr int kRoundsPerSync = 16;
+    const bool async_rounds = !best_first && max_children <= kAsyncMaxChildren;
+    if (cudaMemsetAsync(b.cdep, 0xff, sizeof(int32_t) * max_children, s) != cudaSuccess) return fail(FSP_ECUDA);
+    int64_t S = 1;  // the root is open (and counted as bounded)
     const int make_warps = 8;
     const size_t make_smem = (size_t)make_warps * ((n + 31) / 32) * 4;
     while (S > 0) {
@@ -509,68 +541,76 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
             cudaStreamDestroy(s);
             return FSP_ETIMEDOUT;
         }
-        const int k = (int)std::min<int64_t>(K, S);
-        const int64_t top0 = S - k;
-        if (best_first && k < S) {
-            // bins of the keys from the root bound to the incumbent; coarser
-            // when the range is wide
-            int shift = 0;
-            const int64_t span = (int64_t)std::max(hst->best - root_lb, 1) * (n + 1);
-            while ((span >> shift) >= kBestBins) ++shift;
-            const int g = (int)std::min<int64_t>((S + 255) / 256, 1024);
-            const int64_t T64 = (S + kTile - 1) / kTile;
-            if (T64 > INT32_MAX - 1) return fail(FSP_ENOMEM);
-            const int T = (int)T64, gt = (int)std::min<int64_t>(T64, 4096);
-            st = grow_best(b);
-            if (st != FSP_OK) return fail(st);
-            const size_t ts = (size_t)b.tiles_cap + 1;
-            int32_t *tcount = b.tiles, *tabove = b.tiles + ts, *out_cnt = b.tiles + 2 * ts,
-                    *in_cnt = b.tiles + 3 * ts, *out_off = b.tiles + 4 * ts, *in_off = b.tiles + 5 * ts;
-            note_launches(8);
-            if (cudaMemsetAsync(b.hist, 0, sizeof(int32_t) * (kBestBins + 1), s) != cudaSuccess) return fail(FSP_ECUDA);
-            bnb_best_hist<<<g, 256, 0, s>>>(b.slb, b.sdep, S, n, root_lb, shift, b.hist);
-            bnb_best_threshold<<<1, kScanThreads, 0, s>>>(b.hist, k, b.bs);
-            bnb_best_tile_count<<<gt, kTile, 0, s>>>(b.slb, b.sdep, S, n, root_lb, shift, b.bs, tcount);
-            bnb_best_tile_above<<<1, kScanThreads, 0, s>>>(tcount, T, tabove);
-            bnb_best_mark<<<gt, kTile, 0, s>>>(b.slb, b.sdep, S, n, k, root_lb, shift, b.bs, tabove, T, b.sel_flag,
-                                               out_cnt, in_cnt);
-            bnb_best_list_offsets<<<1, kScanThreads, 0, s>>>(out_cnt, in_cnt, T, out_off, in_off, b.bs);
-            bnb_best_lists<<<gt, kTile, 0, s>>>(S, k, b.sel_flag, out_off, in_off, b.out_list, b.in_list);
-            bnb_best_swap<<<(k + 7) / 8, 256, 0, s>>>(b.srows, b.sdep, b.slb, n, b.bs, b.out_list, b.in_list);
-        }
-        note_launches(2);
-        bnb_count_children<<<1, kScanThreads, 0, s>>>(b.sdep, b.slb, top0, k, n, b.st, b.offs);
-        bnb_make_children<<<(k + make_warps - 1) / make_warps, 32 * make_warps, make_smem, s>>>(
-            b.srows, b.sdep, top0, k, n, b.offs, b.crows, b.cdep, b.cparent);
-        if (cudaGetLastError() != cudaSuccess ||
-            cudaMemcpyAsync(hst, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return fail(FSP_ECUDA);
-        const int total = hst->total;
-        if (total == 0) {
-            S = top0;
-            continue;
-        }
-        st = launch_bound(inst, b.crows, b.cdep, total, b.clb, s, nullptr);
+        // A round pops at most K nodes, so a stack of S nodes cannot empty
+        // within S / K rounds: the group never runs past the search's end.
+        const int group = async_rounds ? (int)std::max<int64_t>(1, std::min<int64_t>(kRoundsPerSync, S / K)) : 1;
+        // room for every child of this group's rounds
+        st = grow_stack(b, n, S + (int64_t)group * max_children, S);
         if (st != FSP_OK) return fail(st);
-        count += total;
-        // every child could survive: the stack must hold top0 + total nodes
-        st = grow_stack(b, n, top0 + total, top0);
-        if (st != FSP_OK) return fail(st);
-        const int tb = 256, gb = (total + tb - 1) / tb;
-        note_launches(4);
-        bnb_filter<<<gb, tb, 0, s>>>(b.clb, b.cdep, total, n, b.st, b.keep);
-        bnb_incumbent<<<1, 128, 0, s>>>(b.crows, n, b.st, b.best_row);
-        bnb_count_survivors<<<1, kScanThreads, 0, s>>>(b.offs, b.keep, k, b.st, b.soffs);
-        bnb_push<<<gb, tb, 0, s>>>(b.crows, b.cdep, b.clb, b.cparent, b.offs, b.keep, b.soffs, total, n, top0,
-                                   b.srows, b.sdep, b.slb);
-        if (cudaGetLastError() != cudaSuccess ||
-            cudaMemcpyAsync(hst, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        for (int r = 0; r < group; ++r) {
+            const int k = (int)std::min<int64_t>(K, S);  // best-first: group == 1, S is current
+            if (best_first && k < S) {
+                // bins of the keys from the root bound to the incumbent; coarser
+                // when the range is wide
+                int shift = 0;
+                const int64_t span = (int64_t)std::max(hst->best - root_lb, 1) * (n + 1);
+                while ((span >> shift) >= kBestBins) ++shift;
+                const int g = (int)std::min<int64_t>((S + 255) / 256, 1024);
+                const int64_t T64 = (S + kTile - 1) / kTile;
+                if (T64 > INT32_MAX - 1) return fail(FSP_ENOMEM);
+                const int T = (int)T64, gt = (int)std::min<int64_t>(T64, 4096);
+                st = grow_best(b);
+                if (st != FSP_OK) return fail(st);
+                const size_t ts = (size_t)b.tiles_cap + 1;
+                int32_t *tcount = b.tiles, *tabove = b.tiles + ts, *out_cnt = b.tiles + 2 * ts,
+                        *in_cnt = b.tiles + 3 * ts, *out_off = b.tiles + 4 * ts, *in_off = b.tiles + 5 * ts;
+                note_launches(8);
+                if (cudaMemsetAsync(b.hist, 0, sizeof(int32_t) * (kBestBins + 1), s) != cudaSuccess)
+                    return fail(FSP_ECUDA);
+                bnb_best_hist<<<g, 256, 0, s>>>(b.slb, b.sdep, S, n, root_lb, shift, b.hist);
+                bnb_best_threshold<<<1, kScanThreads, 0, s>>>(b.hist, k, b.bs);
+                bnb_best_tile_count<<<gt, kTile, 0, s>>>(b.slb, b.sdep, S, n, root_lb, shift, b.bs, tcount);
+                bnb_best_tile_above<<<1, kScanThreads, 0, s>>>(tcount, T, tabove);
+                bnb_best_mark<<<gt, kTile, 0, s>>>(b.slb, b.sdep, S, n, k, root_lb, shift, b.bs, tabove, T,
+                                                   b.sel_flag, out_cnt, in_cnt);
+                bnb_best_list_offsets<<<1, kScanThreads, 0, s>>>(out_cnt, in_cnt, T, out_off, in_off, b.bs);
+                bnb_best_lists<<<gt, kTile, 0, s>>>(S, k, b.sel_flag, out_off, in_off, b.out_list, b.in_list);
+                bnb_best_swap<<<(k + 7) / 8, 256, 0, s>>>(b.srows, b.sdep, b.slb, n, b.bs, b.out_list, b.in_list);
+            }
+            note_launches(2);
+            bnb_count_children<<<1, kScanThreads, 0, s>>>(b.sdep, b.slb, K, n, b.st, b.offs);
+            bnb_make_children<<<(K + make_warps - 1) / make_warps, 32 * make_warps, make_smem, s>>>(
+                b.srows, b.sdep, n, b.st, b.offs, b.crows, b.cdep, b.cparent);
+            if (cudaGetLastError() != cudaSuccess) return fail(FSP_ECUDA);
+            // child slots to bound: every slot of the group's rounds (a
+            // one-round group pops exactly k parents), or the counted children
+            int64_t nb = group == 1 ? (int64_t)k * n : max_children;
+            if (!async_rounds) {
+                if (cudaMemcpyAsync(hst, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess)
+                    return fail(FSP_ECUDA);
+                nb = hst->total;
+            }
+            if (nb > 0) {
+                st = launch_bound(inst, b.crows, b.cdep, nb, b.clb, s, nullptr);
+                if (st != FSP_OK) return fail(st);
+            }
+            const int tb = 256, gb = (int)((std::max<int64_t>(nb, 1) + tb - 1) / tb);
+            note_launches(4);
+            bnb_filter<<<gb, tb, 0, s>>>(b.clb, b.cdep, n, b.st, b.keep);
+            bnb_incumbent<<<1, 128, 0, s>>>(b.crows, n, b.st, b.best_row);
+            bnb_count_survivors<<<1, kScanThreads, 0, s>>>(b.offs, b.keep, b.st, b.soffs);
+            bnb_push<<<gb, tb, 0, s>>>(b.crows, b.cdep, b.clb, b.cparent, b.offs, b.keep, b.soffs, n, b.st, b.srows,
+                                       b.sdep, b.slb);
+            if (cudaGetLastError() != cudaSuccess) return fail(FSP_ECUDA);
+        }
+        if (cudaMemcpyAsync(hst, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return fail(FSP_ECUDA);
         st = take_device_status(inst);
         if (st != FSP_OK) return fail(st);
-        S = top0 + hst->survivors;
+        S = hst->S;
+        count = hst->count;
     }
     const bool found = hst->found != 0;
     const int32_t best = hst->best;
