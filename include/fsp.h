@@ -231,7 +231,11 @@ fsp_status fsp_branch_and_bound(const fsp_instance *inst, int32_t ub0, int16_t *
  * children with LB >= UB and pushes the rest where the parents were -- the
  * children of the topmost parent on top, each parent's children in
  * decreasing (LB, job) order so the smallest is popped first.  Node rows
- * never leave the device; the host reads a few counters per round.
+ * never leave the device, and the round's sizes live in device state: a
+ * depth-first search with at most 16,384 child slots per round (expand * n)
+ * enqueues up to 16 rounds at a time and the host reads the state once per
+ * such group (node limit, stack growth, end); other searches read it once
+ * per round.
  *   ub0, best_perm, best_makespan, nodes_bounded  as fsp_branch_and_bound
  *                  (with expand = 1 the exploration order is the same, up to
  *                  when a leaf updates UB: at generation, not when popped);
@@ -241,12 +245,14 @@ fsp_status fsp_branch_and_bound(const fsp_instance *inst, int32_t ub0, int16_t *
  *                  the `expand` open nodes of smallest LB, deeper first among
  *                  equal bounds (the paper's own GPU B&B selects best-first,
  *                  Section IV), found by binning the key (LB, -depth) of the
- *                  open nodes between the root's bound and UB (4096 bins; on
- *                  a wider range nodes within a bin tie arbitrarily) and
- *                  swapped to the top of the stack before the round;
+ *                  open nodes between the root's bound and UB (4096 bins;
+ *                  on a wider range a bin holds several keys) and swapped to
+ *                  the top of the stack before the round; nodes of one bin
+ *                  are taken by stack position, the most recently pushed
+ *                  first, so the search is deterministic;
  *   node_limit     0 = none; otherwise the search stops with FSP_ETIMEDOUT
- *                  once that many bounds were evaluated (nodes_bounded is
- *                  still written).
+ *                  once that many bounds were evaluated, checked between
+ *                  groups of rounds (nodes_bounded is still written).
  * Synchronous; uses its own CUDA stream; device memory grows with the stack
  * (at least expand * n children of n int16 jobs, plus the stack).
  * Errors: FSP_EINVAL, FSP_ENOMEM, FSP_ECUDA, FSP_EBADNODE, FSP_ENOTFOUND,
