@@ -233,9 +233,9 @@ fsp_status fsp_branch_and_bound(const fsp_instance *inst, int32_t ub0, int16_t *
  * decreasing (LB, job) order so the smallest is popped first.  Node rows
  * never leave the device, and the round's sizes live in device state: a
  * depth-first search with at most 16,384 child slots per round (expand * n)
- * enqueues up to 16 rounds at a time and the host reads the state once per
- * such group (node limit, stack growth, end); other searches read it once
- * per round.
+ * enqueues up to 16 rounds at a time (replays of one captured round) and
+ * the host reads the state once per such group (node limit, stack growth,
+ * end); other searches read it once per round.
  *   ub0, best_perm, best_makespan, nodes_bounded  as fsp_branch_and_bound
  *                  (with expand = 1 the exploration order is the same, up to
  *                  when a leaf updates UB: at generation, not when popped);

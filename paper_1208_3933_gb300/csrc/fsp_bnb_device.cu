@@ -390,7 +390,12 @@ struct DevBuffers {
     int32_t *tiles = nullptr;                   // best-first: six per-tile arrays of tiles_cap + 1
     uint8_t *sel_flag = nullptr;                // best-first: selection of every stack entry
     int64_t cap = 0, tiles_cap = 0;
+    cudaGraphExec_t round_exec = nullptr;       // one depth-first round, captured
+    const int16_t *round_rows = nullptr;        // the stack the captured round writes
+    int round_kernels = 0;                      // kernels in the captured round
     void release() {
+        if (round_exec) cudaGraphExecDestroy(round_exec);
+        round_exec = nullptr;
         for (void *p : {(void *)srows, (void *)crows, (void *)best_row, (void *)sdep, (void *)slb, (void *)cdep,
                         (void *)clb, (void *)cparent, (void *)offs, (void *)keep, (void *)soffs, (void *)st,
                         (void *)hist, (void *)bs, (void *)out_list, (void *)in_list, (void *)tiles,
@@ -547,8 +552,76 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
         // room for every child of this group's rounds
         st = grow_stack(b, n, S + (int64_t)group * max_children, S);
         if (st != FSP_OK) return fail(st);
-        for (int r = 0; r < group; ++r) {
-            const int k = (int)std::min<int64_t>(K, S);  // best-first: group == 1, S is current
+        // the kernels of one round over nb child slots; with nb < 0 the
+        // children are counted first, and a round without children ends
+        // there (*ended: the stack lost its k popped parents)
+        bool ended = false;
+        auto enqueue_round = [&](int64_t nb) -> fsp_status {
+            note_launches(2);
+            bnb_count_children<<<1, kScanThreads, 0, s>>>(b.sdep, b.slb, K, n, b.st, b.offs);
+            bnb_make_children<<<(K + make_warps - 1) / make_warps, 32 * make_warps, make_smem, s>>>(
+                b.srows, b.sdep, n, b.st, b.offs, b.crows, b.cdep, b.cparent);
+            if (cudaGetLastError() != cudaSuccess) return FSP_ECUDA;
+            if (nb < 0) {  // the counted children (read back now)
+                if (cudaMemcpyAsync(hst, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess)
+                    return FSP_ECUDA;
+                nb = hst->total;
+                if (nb == 0) {
+                    // nothing to bound or push: the new stack size is top0
+                    hst->S = hst->top0;
+                    ended = true;
+                    return cudaMemcpyAsync(&b.st->S, &hst->S, sizeof(hst->S), cudaMemcpyHostToDevice, s) ==
+                                   cudaSuccess
+                               ? FSP_OK
+                               : FSP_ECUDA;
+                }
+            }
+            if (nb > 0) {
+                const fsp_status bs = launch_bound(inst, b.crows, b.cdep, nb, b.clb, s, nullptr);
+                if (bs != FSP_OK) return bs;
+            }
+            const int tb = 256, gb = (int)((std::max<int64_t>(nb, 1) + tb - 1) / tb);
+            note_launches(4);
+            bnb_filter<<<gb, tb, 0, s>>>(b.clb, b.cdep, n, b.st, b.keep);
+            bnb_incumbent<<<1, 128, 0, s>>>(b.crows, n, b.st, b.best_row);
+            bnb_count_survivors<<<1, kScanThreads, 0, s>>>(b.offs, b.keep, b.st, b.soffs);
+            bnb_push<<<gb, tb, 0, s>>>(b.crows, b.cdep, b.clb, b.cparent, b.offs, b.keep, b.soffs, n, b.st,
+                                       b.srows, b.sdep, b.slb);
+            return cudaGetLastError() == cudaSuccess ? FSP_OK : FSP_ECUDA;
+        };
+        if (async_rounds && group > 1) {
+            // Groups of depth-first rounds replay one captured round, each
+            // bounding every child slot; it is captured again when the stack
+            // has moved (the first round of a search runs uncaptured, so the
+            // kernels' one-time attributes are set outside any capture).
+            if (!b.round_exec || b.round_rows != b.srows) {
+                cudaMemPool_t pool = nullptr;  // created outside the capture, if the bound needs scratch
+                st = scratch_pool(inst->device, &pool);
+                if (st != FSP_OK) return fail(st);
+                if (b.round_exec) cudaGraphExecDestroy(b.round_exec);
+                b.round_exec = nullptr;
+                cudaGraph_t g = nullptr;
+                const int64_t before = fsp_kernel_launches();
+                if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                    return fail(FSP_ECUDA);
+                const fsp_status rs = enqueue_round(max_children);
+                const cudaError_t ec = cudaStreamEndCapture(s, &g);
+                b.round_kernels = (int)(fsp_kernel_launches() - before);
+                note_launches(-b.round_kernels);  // counted when replayed
+                if (rs != FSP_OK || ec != cudaSuccess || cudaGraphInstantiate(&b.round_exec, g, 0) != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return fail(rs != FSP_OK ? rs : FSP_ECUDA);
+                }
+                cudaGraphDestroy(g);
+                b.round_rows = b.srows;
+            }
+            for (int r = 0; r < group; ++r) {
+                note_launches(b.round_kernels);
+                if (cudaGraphLaunch(b.round_exec, s) != cudaSuccess) return fail(FSP_ECUDA);
+            }
+        } else {
+            const int k = (int)std::min<int64_t>(K, S);  // one round: S is current
             if (best_first && k < S) {
                 // bins of the keys from the root bound to the incumbent; coarser
                 // when the range is wide
@@ -577,32 +650,14 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
                 bnb_best_lists<<<gt, kTile, 0, s>>>(S, k, b.sel_flag, out_off, in_off, b.out_list, b.in_list);
                 bnb_best_swap<<<(k + 7) / 8, 256, 0, s>>>(b.srows, b.sdep, b.slb, n, b.bs, b.out_list, b.in_list);
             }
-            note_launches(2);
-            bnb_count_children<<<1, kScanThreads, 0, s>>>(b.sdep, b.slb, K, n, b.st, b.offs);
-            bnb_make_children<<<(K + make_warps - 1) / make_warps, 32 * make_warps, make_smem, s>>>(
-                b.srows, b.sdep, n, b.st, b.offs, b.crows, b.cdep, b.cparent);
-            if (cudaGetLastError() != cudaSuccess) return fail(FSP_ECUDA);
-            // child slots to bound: every slot of the group's rounds (a
-            // one-round group pops exactly k parents), or the counted children
-            int64_t nb = group == 1 ? (int64_t)k * n : max_children;
-            if (!async_rounds) {
-                if (cudaMemcpyAsync(hst, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                    cudaStreamSynchronize(s) != cudaSuccess)
-                    return fail(FSP_ECUDA);
-                nb = hst->total;
+            // child slots to bound: the popped parents' (a depth-first round
+            // pops exactly k), or the counted children
+            st = enqueue_round(async_rounds ? (int64_t)k * n : -1);
+            if (st != FSP_OK) return fail(st);
+            if (ended) {  // the state on the host is current
+                S = hst->S;
+                continue;
             }
-            if (nb > 0) {
-                st = launch_bound(inst, b.crows, b.cdep, nb, b.clb, s, nullptr);
-                if (st != FSP_OK) return fail(st);
-            }
-            const int tb = 256, gb = (int)((std::max<int64_t>(nb, 1) + tb - 1) / tb);
-            note_launches(4);
-            bnb_filter<<<gb, tb, 0, s>>>(b.clb, b.cdep, n, b.st, b.keep);
-            bnb_incumbent<<<1, 128, 0, s>>>(b.crows, n, b.st, b.best_row);
-            bnb_count_survivors<<<1, kScanThreads, 0, s>>>(b.offs, b.keep, b.st, b.soffs);
-            bnb_push<<<gb, tb, 0, s>>>(b.crows, b.cdep, b.clb, b.cparent, b.offs, b.keep, b.soffs, n, b.st, b.srows,
-                                       b.sdep, b.slb);
-            if (cudaGetLastError() != cudaSuccess) return fail(FSP_ECUDA);
         }
         if (cudaMemcpyAsync(hst, b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
