@@ -51,6 +51,27 @@ __device__ __forceinline__ int load_q(const int32_t *row, int m, int l, bool q32
     return q32 ? row[m + l] : (int)reinterpret_cast<const int16_t *>(row + m)[l];
 }
 
+// NV bit-matrix transposes at once (as warp_transpose32, one matrix per
+// value): the five shuffle stages are interleaved across the values, so a
+// stage's NV shuffles are in flight together instead of one chain at a time.
+template <int NV>
+__device__ __forceinline__ void warp_transpose32_n(uint32_t (&x)[NV], int lane) {
+    uint32_t mask = 0x0000ffffu;
+#pragma unroll
+    for (int j = 16; j >= 1; j >>= 1) {
+        uint32_t y[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) y[v] = __shfl_xor_sync(kFull, x[v], j);
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            x[v] = (lane & j) ? ((x[v] & ~mask) | ((y[v] >> j) & mask)) : ((x[v] & mask) | ((y[v] & mask) << j));
+        mask ^= mask << (j >> 1);
+    }
+}
+
+// Machines of the minima search handled together (MP is a multiple of 4).
+constexpr int kMinimaChunk = 4;
+
 // Copies the first 32 entries of every machine's head- and tail-sorted job
 // lists into shared memory ([m][32] each; entries past n read (0,0)).
 __device__ __forceinline__ void load_sorted_heads(const LanesArgs &a, int2 *hcache, int2 *tcache) {
@@ -201,57 +222,88 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     const bool q32 = a.q32 != 0;
     uint32_t open_h = 0, open_t = 0;  // machines still searching (bit k)
     const bool in = lane < n;
+    constexpr int CH = kMinimaChunk;
+    // Machines are taken kMinimaChunk at a time: their list entries and flag
+    // words are loaded together and their transposes interleaved.
 #pragma unroll
-    for (int k = 0; k < MP; ++k) {
-        if (k < m) {
-            // heads are 0 on machine 0 and not needed with per-job release
-            // times; tails are 0 on machine m-1
-            const bool want_h = k > 0 && !per_job, want_t = k < m - 1;
-            int2 eh = make_int2(0, 0), et = make_int2(0, 0);
-            if (in && want_h) eh = hcache ? hcache[k * 32 + lane] : __ldg(a.hsort + (size_t)k * n + lane);
-            if (in && want_t) et = tcache ? tcache[k * 32 + lane] : __ldg(a.tsort + (size_t)k * n + lane);
-            const uint32_t wh = (in && want_h) ? F[eh.x] : 0u, wt = (in && want_t) ? F[et.x] : 0u;
-            const uint32_t hh = warp_transpose32(wh, lane), ht = warp_transpose32(wt, lane);
-            const int fh = __ffs(hh) - 1, ft = __ffs(ht) - 1;
-            const int vh = __shfl_sync(kFull, eh.y, fh < 0 ? 0 : fh);
-            const int vt = __shfl_sync(kFull, et.y, ft < 0 ? 0 : ft);
-            const int mh = (!settled && fh >= 0) ? vh : 0;
-            const int ql = (!settled && ft >= 0) ? vt : 0;
-            if (want_h && !settled && fh < 0)
-                open_h |= 1u << k;  // A_k once a later round finds the minimum
-            else
-                myrow[k] = (per_job ? R[k] : max(C[k], mh)) + myrow[k];
-            if (want_t && !settled && ft < 0) open_t |= 1u << k;
-            store_q(myrow, m, k, ql, q32);
+    for (int k0 = 0; k0 < MP; k0 += CH) {
+        if (k0 < m) {
+            int2 eh[CH], et[CH];
+            uint32_t w[2 * CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int k = k0 + c;
+                // heads are 0 on machine 0 and not needed with per-job release
+                // times; tails are 0 on machine m-1
+                const bool want_h = in && k < m && k > 0 && !per_job, want_t = in && k < m - 1;
+                eh[c] = make_int2(0, 0);
+                et[c] = make_int2(0, 0);
+                if (want_h) eh[c] = hcache ? hcache[k * 32 + lane] : __ldg(a.hsort + (size_t)k * n + lane);
+                if (want_t) et[c] = tcache ? tcache[k * 32 + lane] : __ldg(a.tsort + (size_t)k * n + lane);
+                w[2 * c] = want_h ? F[eh[c].x] : 0u;
+                w[2 * c + 1] = want_t ? F[et[c].x] : 0u;
+            }
+            warp_transpose32_n<2 * CH>(w, lane);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int k = k0 + c;
+                const bool want_h = k < m && k > 0 && !per_job, want_t = k < m - 1;
+                const int fh = __ffs(w[2 * c]) - 1, ft = __ffs(w[2 * c + 1]) - 1;
+                const int vh = __shfl_sync(kFull, eh[c].y, fh < 0 ? 0 : fh);
+                const int vt = __shfl_sync(kFull, et[c].y, ft < 0 ? 0 : ft);
+                if (k < m) {
+                    const int mh = (!settled && fh >= 0) ? vh : 0;
+                    const int ql = (!settled && ft >= 0) ? vt : 0;
+                    if (want_h && !settled && fh < 0)
+                        open_h |= 1u << k;  // A_k once a later round finds the minimum
+                    else
+                        myrow[k] = (per_job ? R[k] : max(C[k], mh)) + myrow[k];
+                    if (want_t && !settled && ft < 0) open_t |= 1u << k;
+                    store_q(myrow, m, k, ql, q32);
+                }
+            }
         }
     }
     // later rounds: list entries [base, base + 32) of every machine some node
-    // still searches, all machines at once so their loads and transposes
-    // overlap
+    // still searches, the machines taken as in round 0
     for (int base = 32; base < n; base += 32) {
         const uint32_t any_h = __reduce_or_sync(kFull, open_h), any_t = __reduce_or_sync(kFull, open_t);
         if ((any_h | any_t) == 0u) break;
         const int pos = base + lane;
         const bool inr = pos < n;
 #pragma unroll
-        for (int k = 0; k < MP; ++k) {
-            if (k < m) {
-                const bool lh = inr && ((any_h >> k) & 1u), lt = inr && ((any_t >> k) & 1u);
-                int2 eh = make_int2(0, 0), et = make_int2(0, 0);
-                if (lh) eh = __ldg(a.hsort + (size_t)k * n + pos);
-                if (lt) et = __ldg(a.tsort + (size_t)k * n + pos);
-                const uint32_t wh = lh ? F[eh.x] : 0u, wt = lt ? F[et.x] : 0u;
-                const uint32_t hh = warp_transpose32(wh, lane), ht = warp_transpose32(wt, lane);
-                const int fh = __ffs(hh) - 1, ft = __ffs(ht) - 1;
-                const int vh = __shfl_sync(kFull, eh.y, fh < 0 ? 0 : fh);
-                const int vt = __shfl_sync(kFull, et.y, ft < 0 ? 0 : ft);
-                if (((open_h >> k) & 1u) && fh >= 0) {
-                    myrow[k] = max(C[k], vh) + myrow[k];
-                    open_h &= ~(1u << k);
+        for (int k0 = 0; k0 < MP; k0 += CH) {
+            if (k0 < m && (((any_h | any_t) >> k0) & ((1u << CH) - 1u))) {
+                int2 eh[CH], et[CH];
+                uint32_t w[2 * CH];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const int k = k0 + c;
+                    const bool lh = inr && k < m && ((any_h >> k) & 1u), lt = inr && k < m && ((any_t >> k) & 1u);
+                    eh[c] = make_int2(0, 0);
+                    et[c] = make_int2(0, 0);
+                    if (lh) eh[c] = __ldg(a.hsort + (size_t)k * n + pos);
+                    if (lt) et[c] = __ldg(a.tsort + (size_t)k * n + pos);
+                    w[2 * c] = lh ? F[eh[c].x] : 0u;
+                    w[2 * c + 1] = lt ? F[et[c].x] : 0u;
                 }
-                if (((open_t >> k) & 1u) && ft >= 0) {
-                    store_q(myrow, m, k, vt, q32);
-                    open_t &= ~(1u << k);
+                warp_transpose32_n<2 * CH>(w, lane);
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const int k = k0 + c;
+                    const int fh = __ffs(w[2 * c]) - 1, ft = __ffs(w[2 * c + 1]) - 1;
+                    const int vh = __shfl_sync(kFull, eh[c].y, fh < 0 ? 0 : fh);
+                    const int vt = __shfl_sync(kFull, et[c].y, ft < 0 ? 0 : ft);
+                    if (k < m) {
+                        if (((open_h >> k) & 1u) && fh >= 0) {
+                            myrow[k] = max(C[k], vh) + myrow[k];
+                            open_h &= ~(1u << k);
+                        }
+                        if (((open_t >> k) & 1u) && ft >= 0) {
+                            store_q(myrow, m, k, vt, q32);
+                            open_t &= ~(1u << k);
+                        }
+                    }
                 }
             }
         }
