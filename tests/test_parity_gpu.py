@@ -339,6 +339,17 @@ def test_host_entry_point_wave_chunks(gpu_lib):
         assert np.array_equal(dev[idx], oracle_bounds(w.p, w.rows[idx], w.depths[idx]))
 
 
+@pytest.mark.parametrize("n,m,N", [(20, 20, 1), (20, 20, 500), (30, 5, 40000), (64, 6, 9000)])
+def test_host_entry_point_small_and_lockstep_pools(gpu_lib, n, m, N):
+    """fsp_bound_pool_host on one-chunk pools, on a node-lockstep instance
+    (m = 5: 10 couples, split 20/80) and on a depth-ordered one-chunk pool."""
+    fsp = gpu_lib
+    p, rows, depths = pool(7 * n + m, n, m, N)
+    with fsp.Instance(p) as inst:
+        got = fsp.fsp_bound_pool_host(inst, rows, depths)
+    assert np.array_equal(got, oracle_bounds(p, rows, depths))
+
+
 def test_side_stream_and_repeat_calls(gpu_lib):
     import torch
     fsp = gpu_lib
