@@ -618,11 +618,22 @@ def main():
                     help="bound only the first NODES nodes of the pool (small profiling cases)")
     ap.add_argument("--alu-peak", action="store_true", help="run the integer-pipe throughput probe and exit")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served legs")
+    ap.add_argument("--leg", default="", choices=["", "batched", "served", "searches"],
+                    help="run one extra leg alone (single GPU) and print its JSON line (profiling)")
     ap.add_argument("--config", default="",
                     help="force a launch shape, e.g. kernel=2,warps_per_block=14 (profiling); default: autotuned")
     args = ap.parse_args()
     if args.alu_peak:
         run_alu_peak()
+        return
+    if args.leg:
+        import torch
+        from paper_1208_3933_gb300 import build
+        build.build()
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        leg = {"batched": lambda: run_batched_leg(dev), "served": run_served_leg, "searches": run_bnb_leg}[args.leg]()
+        print(json.dumps({"leg": args.leg, "result": leg}), flush=True)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "fsp_internal.h"
+#include "fsp_batch_scan.cuh"
 #include "fsp_lanes_device.cuh"
 #include "fsp_ptx.cuh"
 
@@ -51,10 +52,7 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
             for (int b = 0; b < 32; ++b) u[b] = 0.f;
             const uint2 *R = reinterpret_cast<const uint2 *>(a.grec) + (size_t)g * npad * 32 + lane;
-#pragma unroll 4
-            for (int i = 0; i < npad; ++i) {
-                lanes_step(__ldg(R + i * 32), F, u);
-            }
+            scan_compact_global(R, npad, F, u);
             couple_epilogue<false>(AQ, aq_stride, m, kk, ll, u, lb);
         }
         const int best = transpose_max(lb, lane);

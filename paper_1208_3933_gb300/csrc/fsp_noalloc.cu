@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include "fsp_internal.h"
+#include "fsp_batch_scan.cuh"
 #include "fsp_lanes_device.cuh"
 
 namespace fspgb {
@@ -81,10 +82,7 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
             for (int b = 0; b < 32; ++b) u[b] = 0.f;
             const uint2 *R = reinterpret_cast<const uint2 *>(a.grec) + (size_t)g * a.npad * 32 + lane;
-#pragma unroll 4
-            for (int i = 0; i < a.npad; ++i) {
-                lanes_step(__ldg(R + i * 32), F, u);
-            }
+            scan_compact_global(R, a.npad, F, u);
             couple_epilogue<false>(AQ, aq_stride, a.m, kk, ll, u, lb);
         }
         const int best = transpose_max(lb, lane);
