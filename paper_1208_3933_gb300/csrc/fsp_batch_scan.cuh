@@ -11,7 +11,7 @@ namespace fspgb {
 // of the next kScanAhead positions are loaded while the current ones are
 // applied, so each load's latency (longer than a shared-memory read's) is
 // covered by the updates before it is needed.
-constexpr int kScanAhead = 8;
+constexpr int kScanAhead = 4;
 __device__ __forceinline__ void scan_compact_global(const uint2 *R, int npos, const uint32_t *F, float (&u)[32]) {
     uint2 buf[kScanAhead];
 #pragma unroll
