@@ -211,7 +211,9 @@ def run_batched_leg(dev, reps: int = 5):
             fsp.fsp_bound_pool(inst, r, d, o)
 
     plain_ms = timed(per_pool)
-    with fsp.Batch([(i, r, d, o) for i, (r, d), o in zip(insts, bufs, outs_b)]) as b:
+    batch_pools = [(i, r, d, o) for i, (r, d), o in zip(insts, bufs, outs_b)]
+    tuned_w, _ = fsp.fsp_batch_autotune(batch_pools)
+    with fsp.Batch(batch_pools, warps_per_block=tuned_w) as b:
         batch_ms = timed(b.launch_graph)
         q = b.query()
     same = all(torch.equal(a, c) for a, c in zip(outs, outs_b))
@@ -220,7 +222,8 @@ def run_batched_leg(dev, reps: int = 5):
     return {"workload": "64 instances, seeds 100-163", "pools": len(ws), "nodes": total,
             "batched_nodes_per_s": total / (batch_ms * 1e-3), "plain_nodes_per_s": total / (plain_ms * 1e-3),
             "batched_ms": batch_ms, "plain_ms": plain_ms, "speedup": plain_ms / batch_ms,
-            "work_items": q["work_items"], "bit_exact_vs_plain": bool(same), "launch": "one CUDA-graph replay"}
+            "work_items": q["work_items"], "warps_per_block": q["warps_per_block"],
+            "bit_exact_vs_plain": bool(same), "launch": "one CUDA-graph replay, warps per block autotuned"}
 
 
 def run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, P: int, reps: int = 10):

@@ -337,6 +337,20 @@ fsp_status fsp_batch_query(const fsp_batch *batch, int64_t *work_items, int64_t 
 /* Frees the plan; none of its launches may be in flight.  NULL is a no-op. */
 void fsp_batch_destroy(fsp_batch *batch);
 
+/*
+ * fsp_batch_autotune -- picks the node tile of a batch plan (warps, hence
+ * 32-node work items in flight, per block) by timing plans of the same pools
+ * with 16, 12, 8, 6, 4 and 2 warps per block on the stream (one warm-up and
+ * three timed launches each; shapes that do not fit are skipped).  The pools'
+ * out_lb buffers are written (every shape writes the same bounds).
+ *   pools, count   as fsp_batch_create (count >= 1);
+ *   best_warps     receives the fastest warps_per_block, for fsp_batch_create;
+ *   best_ms        (or NULL) receives its time per launch.
+ * Synchronous.  Errors: FSP_EINVAL, FSP_ENOMEM, FSP_ECUDA.
+ */
+fsp_status fsp_batch_autotune(const fsp_pool_desc *pools, int32_t count, void *cuda_stream,
+                              int32_t *best_warps, float *best_ms);
+
 /* ---------------------------------------------------------------------
  * Bounding server: continuous batching of many clients' pools.
  * --------------------------------------------------------------------- */

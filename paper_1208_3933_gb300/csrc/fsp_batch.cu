@@ -310,3 +310,53 @@ extern "C" void fsp_batch_destroy(fsp_batch *b) {
     if (b->dev_block) cudaFree(b->dev_block);
     delete b;
 }
+
+// Times plans of the same pools with 16, 12, 8, 6, 4 and 2 warps per block
+// (each on the stream: one warm-up launch, then three timed ones) and
+// reports the fastest.  Every candidate writes the same bounds.
+extern "C" fsp_status fsp_batch_autotune(const fsp_pool_desc *pools, int32_t count, void *cuda_stream,
+                                         int32_t *best_warps, float *best_ms) {
+    if (!pools || count < 1 || !best_warps) return FSP_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return FSP_ECUDA;
+    }
+    fsp_status st = FSP_OK;
+    float best = 1e30f;
+    int bw = 0;
+    for (int W : {16, 12, 8, 6, 4, 2}) {
+        fsp_batch *b = nullptr;
+        const fsp_status cs = fsp_batch_create(pools, count, W, &b);
+        if (cs == FSP_EINVAL) continue;  // the shape does not fit this batch
+        if (cs != FSP_OK) {
+            st = cs;
+            break;
+        }
+        constexpr int kReps = 3;
+        float ms = 0.f;
+        st = fsp_batch_launch(b, s);
+        if (st == FSP_OK && cudaEventRecord(e0, s) != cudaSuccess) st = FSP_ECUDA;
+        for (int r = 0; r < kReps && st == FSP_OK; ++r) st = fsp_batch_launch(b, s);
+        if (st == FSP_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = FSP_ECUDA;
+        cudaStreamSynchronize(s);
+        fsp_batch_destroy(b);
+        if (st != FSP_OK) break;
+        ms /= kReps;
+        if (ms < best) {
+            best = ms;
+            bw = W;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != FSP_OK) return st;
+    if (!bw) return FSP_EINVAL;
+    *best_warps = bw;
+    if (best_ms) *best_ms = best;
+    return FSP_OK;
+}
+

@@ -125,6 +125,8 @@ def load():
             "fsp_batch_launch_graph": ([vp, vp], i32),
             "fsp_batch_query": ([vp, i64p, i64p, i32p, i32p], i32),
             "fsp_batch_destroy": ([vp], None),
+            "fsp_batch_autotune": ([ctypes.POINTER(fsp_pool_desc), i32, vp, i32p, ctypes.POINTER(ctypes.c_float)],
+                                   i32),
             "fsp_bound_batch_noalloc": ([ctypes.POINTER(fsp_pool_desc), i32, vp], i32),
             "fsp_server_create": ([ctypes.POINTER(fsp_server_config), ctypes.POINTER(vp)], i32),
             "fsp_server_submit": ([vp, vp, vp, vp, i64, vp, ctypes.POINTER(vp)], i32),
@@ -403,6 +405,20 @@ class Batch:
 
 def fsp_batch_create(pools, warps_per_block: int = 0) -> Batch:
     return Batch(pools, warps_per_block)
+
+
+def fsp_batch_autotune(pools, stream=None):
+    """Fastest warps_per_block for a batch of (instance, nodes, depths, out)
+    pools (torch CUDA tensors); returns (warps_per_block, ms per launch)."""
+    lib = load()
+    descs = (fsp_pool_desc * max(1, len(pools)))()
+    for i, (inst, nodes, depths, out) in enumerate(pools):
+        N = _check_pool(inst, nodes, depths, out)
+        descs[i] = fsp_pool_desc(inst.handle.value, nodes.data_ptr(), depths.data_ptr(), out.data_ptr(), N)
+    w, ms = ctypes.c_int32(), ctypes.c_float()
+    _check(lib.fsp_batch_autotune(descs, len(pools), _stream_handle(stream), ctypes.byref(w), ctypes.byref(ms)),
+           "fsp_batch_autotune")
+    return int(w.value), float(ms.value)
 
 
 FSP_NOALLOC_MAX_POOLS = 64

@@ -117,3 +117,30 @@ def test_full_batched_workload_sampled(gpu_lib):
         assert np.array_equal(got[idx], oracle.Tables(w.p).lb_pool(w.rows[idx], w.depths[idx], threads=16)), w.name
     for inst in insts:
         inst.close()
+
+
+def test_batch_autotune_and_every_node_tile_agree(gpu_lib):
+    """fsp_batch_autotune picks one of the timed node tiles; plans with 16, 8
+    and 2 warps per block and the tuned one write the same bounds, equal to
+    the oracle's."""
+    import torch
+    fsp = gpu_lib
+    ws = small_batch(range(120, 128), 900)
+    insts = [fsp.Instance(w.p) for w in ws]
+    bufs = [(dev(w.rows), dev(w.depths)) for w in ws]
+    outs = [torch.empty(w.N, dtype=torch.int32, device="cuda") for w in ws]
+    pools = [(inst, r, d, o) for inst, (r, d), o in zip(insts, bufs, outs)]
+    best_w, ms = fsp.fsp_batch_autotune(pools)
+    assert best_w in (16, 12, 8, 6, 4, 2) and ms > 0
+    wants = [oracle.Tables(w.p).lb_pool(w.rows, w.depths, threads=16) for w in ws]
+    for W in (16, 8, 2, best_w):
+        for o in outs:
+            o.fill_(-7)
+        with fsp.Batch(pools, warps_per_block=W) as b:
+            assert b.query()["warps_per_block"] == W
+            b.launch_graph()
+            torch.cuda.synchronize()
+        for o, want in zip(outs, wants):
+            assert np.array_equal(o.cpu().numpy(), want), W
+    for inst in insts:
+        inst.close()
