@@ -140,10 +140,9 @@ __global__ void bnb_make_children(const int16_t *srows, const int32_t *sdep, int
 
 // (4a) leaves update the round's best; other children survive while their
 // bound is below the incumbent.
-__global__ void bnb_filter(const int32_t *clb, const int32_t *cdep, int n, DevState *st, int32_t *keep) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= st->total) return;
-    const int32_t best = st->best, lb = clb[c];
+__device__ __forceinline__ void filter_child(int c, const int32_t *clb, const int32_t *cdep, int n, int32_t best,
+                                             DevState *st, int32_t *keep) {
+    const int32_t lb = clb[c];
     int kv = 0;
     if (lb >= 0 && lb < best) {
         if (cdep[c] == n)
@@ -152,6 +151,12 @@ __global__ void bnb_filter(const int32_t *clb, const int32_t *cdep, int n, DevSt
             kv = 1;
     }
     keep[c] = kv;
+}
+
+__global__ void bnb_filter(const int32_t *clb, const int32_t *cdep, int n, DevState *st, int32_t *keep) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st->total) return;
+    filter_child(c, clb, cdep, n, st->best, st, keep);
 }
 
 // (4b) the incumbent from this round's best leaf.
@@ -191,12 +196,10 @@ __global__ void __launch_bounds__(kScanThreads) bnb_count_survivors(const int32_
 
 // (4d) push: survivor c of parent p goes to top0 + soffs[p] + (number of
 // surviving siblings with a larger (bound, job)).
-__global__ void bnb_push(const int16_t *crows, const int32_t *cdep, const int32_t *clb, const int32_t *cparent,
-                         const int32_t *offs, const int32_t *keep, const int32_t *soffs, int n, const DevState *st,
-                         int16_t *srows, int32_t *sdep, int32_t *slb) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= st->total || !keep[c]) return;
-    const int64_t top0 = st->top0;
+__device__ __forceinline__ void push_child(int c, const int16_t *crows, const int32_t *cdep, const int32_t *clb,
+                                           const int32_t *cparent, const int32_t *offs, const int32_t *keep,
+                                           const int32_t *soffs, int n, int64_t top0, int16_t *srows,
+                                           int32_t *sdep, int32_t *slb) {
     const int p = cparent[c];
     const int32_t lb = clb[c];
     const int d = cdep[c];
@@ -212,6 +215,63 @@ __global__ void bnb_push(const int16_t *crows, const int32_t *cdep, const int32_
     for (int i = 0; i < n; ++i) srows[dst * n + i] = crows[(int64_t)c * n + i];
     sdep[dst] = d;
     slb[dst] = lb;
+}
+
+__global__ void bnb_push(const int16_t *crows, const int32_t *cdep, const int32_t *clb, const int32_t *cparent,
+                         const int32_t *offs, const int32_t *keep, const int32_t *soffs, int n, const DevState *st,
+                         int16_t *srows, int32_t *sdep, int32_t *slb) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st->total || !keep[c]) return;
+    push_child(c, crows, cdep, clb, cparent, offs, keep, soffs, n, st->top0, srows, sdep, slb);
+}
+
+// (4a)-(4d) in one block, for rounds of at most a few thousand children:
+// the same filter, incumbent, survivor count and push as the four kernels
+// above, separated by block barriers instead of launches.
+__global__ void __launch_bounds__(kScanThreads) bnb_round_tail(const int16_t *crows, const int32_t *cdep,
+                                                                 const int32_t *clb, const int32_t *cparent,
+                                                                 const int32_t *offs, int n, DevState *st,
+                                                                 int32_t *keep, int32_t *soffs, int16_t *best_row,
+                                                                 int16_t *srows, int32_t *sdep, int32_t *slb) {
+    __shared__ int s_leaf;
+    __shared__ int32_t s_ms;
+    const int total = st->total, k = st->k;
+    const int64_t top0 = st->top0;
+    const int32_t best = st->best;
+    for (int c = threadIdx.x; c < total; c += blockDim.x) filter_child(c, clb, cdep, n, best, st, keep);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long key = st->round_key;
+        s_leaf = -1;
+        if (key != ~0ull && (int32_t)(key >> 32) < best) {
+            s_leaf = (int)(key & 0xffffffffu);
+            s_ms = (int32_t)(key >> 32);
+        }
+    }
+    __syncthreads();
+    if (s_leaf >= 0) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) best_row[i] = crows[(int64_t)s_leaf * n + i];
+        if (threadIdx.x == 0) {
+            st->best = s_ms;
+            st->found = 1;
+        }
+    }
+    block_exclusive_scan(
+        k,
+        [&](int p) {
+            int v = 0;
+            for (int c = offs[p]; c < offs[p + 1]; ++c) v += keep[c];
+            return v;
+        },
+        soffs);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->survivors = soffs[k];
+        st->S = top0 + soffs[k];
+        st->count += total;
+    }
+    for (int c = threadIdx.x; c < total; c += blockDim.x)
+        if (keep[c]) push_child(c, crows, cdep, clb, cparent, offs, keep, soffs, n, top0, srows, sdep, slb);
 }
 
 // ---- best-first selection: bring the k open nodes of smallest bound to the
@@ -580,6 +640,12 @@ extern "C" fsp_status fsp_branch_and_bound_device(const fsp_instance *inst, int3
             if (nb > 0) {
                 const fsp_status bs = launch_bound(inst, b.crows, b.cdep, nb, b.clb, s, nullptr);
                 if (bs != FSP_OK) return bs;
+            }
+            if (async_rounds) {  // at most kAsyncMaxChildren children: one block
+                note_launches(1);
+                bnb_round_tail<<<1, kScanThreads, 0, s>>>(b.crows, b.cdep, b.clb, b.cparent, b.offs, n, b.st,
+                                                          b.keep, b.soffs, b.best_row, b.srows, b.sdep, b.slb);
+                return cudaGetLastError() == cudaSuccess ? FSP_OK : FSP_ECUDA;
             }
             const int tb = 256, gb = (int)((std::max<int64_t>(nb, 1) + tb - 1) / tb);
             note_launches(4);
