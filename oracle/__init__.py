@@ -71,6 +71,9 @@ def _load():
             lib.fo_lb_pool_ex.restype = ctypes.c_int64
             lib.fo_bnb.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int32, i16p, i32p, i64p]
             lib.fo_bnb.restype = ctypes.c_int
+            lib.fo_bnb_ex.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int32, ctypes.c_int, i16p,
+                                      ctypes.c_int32, i16p, i32p, i64p]
+            lib.fo_bnb_ex.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -154,17 +157,23 @@ class Tables:
         return out
 
 
-def branch_and_bound(p: np.ndarray, ub0: int):
-    """Depth-first B&B of fsp_oracle.c.  Returns (status, best_makespan,
-    best_perm, nodes_bounded); status is FO_OK or FO_ENOTFOUND."""
+def branch_and_bound(p: np.ndarray, ub0: int, release: int = RELEASE_HEADS, prefix=()):
+    """Depth-first B&B of fsp_oracle.c, every node bounded with the given
+    reading of RM, over the subtree of ``prefix`` (the whole tree when it is
+    empty).  Returns (status, best_makespan, best_perm, nodes_bounded);
+    status is FO_OK or FO_ENOTFOUND."""
     lib = _load()
     p = np.ascontiguousarray(p, dtype=np.int32)
     n, m = p.shape
     perm = np.zeros(n, np.int16)
+    root = np.zeros(max(1, len(prefix)), np.int16)
+    root[:len(prefix)] = np.asarray(prefix, dtype=np.int16)
     best = ctypes.c_int32(0)
     nodes = ctypes.c_int64(0)
-    rc = lib.fo_bnb(n, m, _ptr(p, ctypes.c_int32), int(ub0), _ptr(perm, ctypes.c_int16),
-                    ctypes.byref(best), ctypes.byref(nodes))
+    rc = lib.fo_bnb_ex(n, m, _ptr(p, ctypes.c_int32), int(ub0), int(release), _ptr(root, ctypes.c_int16),
+                       len(prefix), _ptr(perm, ctypes.c_int16), ctypes.byref(best), ctypes.byref(nodes))
+    if rc == FO_EBADNODE:
+        raise ValueError(f"invalid prefix {list(prefix)}")
     if rc not in (FO_OK, FO_ENOTFOUND):
         raise RuntimeError(f"fo_bnb failed: {rc}")
     return rc, int(best.value), perm, int(nodes.value)

@@ -248,7 +248,14 @@ int64_t fo_lb_pool(int n, int m, const int32_t *p, const int32_t *mm, const int3
  *     (LB, job) ascending and pushed so that the smallest is popped first;
  *     children with LB >= UB are dropped at once.
  * *nodes counts LB evaluations (root included).  Returns FO_ENOTFOUND when no
- * schedule has makespan <= ub0.
+ * schedule has makespan <= ub0.  `release` picks the reading of RM used by
+ * every bound (FO_RELEASE_HEADS or FO_RELEASE_EST, see fo_lb_ex): both give
+ * valid bounds, so both searches reach the same optimum; the per-job reading
+ * is at least as tight and prunes at least as early.
+ * fo_bnb_ex searches only the subtree of the node whose prefix is
+ * root[0..root_d) (every schedule that starts with it); root_d = 0 is the
+ * whole tree.  The subtrees of all prefixes of one length cover every
+ * schedule, so the smallest of their optima is the optimum.
  */
 typedef struct {
     int32_t lb;
@@ -268,9 +275,11 @@ static int fo_ccmp(const void *a, const void *b) {
     return 0;
 }
 
-int fo_bnb(int n, int m, const int32_t *p, int32_t ub0, int16_t *best_perm,
-           int32_t *best_makespan, int64_t *nodes) {
+int fo_bnb_ex(int n, int m, const int32_t *p, int32_t ub0, int release, const int16_t *root,
+              int32_t root_d, int16_t *best_perm, int32_t *best_makespan, int64_t *nodes) {
     if (n < 1 || m < 2 || !p) return FO_EINVAL;
+    if (release != FO_RELEASE_HEADS && release != FO_RELEASE_EST) return FO_EINVAL;
+    if (root_d < 0 || root_d > n || (root_d > 0 && !root)) return FO_EINVAL;
     int P = fo_num_pairs(m);
     int32_t *mm = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)P);
     int32_t *lag = (int32_t *)malloc(sizeof(int32_t) * (size_t)P * n);
@@ -293,10 +302,14 @@ int fo_bnb(int n, int m, const int32_t *p, int32_t ub0, int16_t *best_perm,
     int64_t count = 0;
     size_t top = 0;
     int32_t lb = 0;
-    fo_lb(n, m, p, mm, lag, jm, tmp, 0, NULL, &lb);
+    /* the search starts at the node of the given prefix (the whole tree for
+       root_d = 0); a bad prefix is refused */
+    for (int i = 0; i < root_d; ++i) tmp[i] = root[i];
+    if (fo_lb_ex(n, m, p, mm, lag, jm, tmp, root_d, release, NULL, &lb) != FO_OK) { rc = FO_EBADNODE; goto done; }
     ++count;
+    memcpy(stack[0].row, tmp, sizeof(int16_t) * (size_t)root_d);
     stack[0].lb = lb;
-    stack[0].d = 0;
+    stack[0].d = root_d;
     top = 1;
     while (top > 0) {
         fo_node *nd = &stack[--top];
@@ -316,7 +329,7 @@ int fo_bnb(int n, int m, const int32_t *p, int32_t ub0, int16_t *best_perm,
             if (used[j]) continue;
             tmp[d] = (int16_t)j;
             int32_t v = 0;
-            fo_lb(n, m, p, mm, lag, jm, tmp, d + 1, NULL, &v);
+            fo_lb_ex(n, m, p, mm, lag, jm, tmp, d + 1, release, NULL, &v);
             ++count;
             kids[nk].lb = v;
             kids[nk].job = j;
@@ -342,4 +355,10 @@ int fo_bnb(int n, int m, const int32_t *p, int32_t ub0, int16_t *best_perm,
 done:
     free(mm); free(lag); free(jm); free(stack); free(rows); free(kids); free(tmp); free(used);
     return rc;
+}
+
+/* fo_bnb_ex with the release times of the default reading. */
+int fo_bnb(int n, int m, const int32_t *p, int32_t ub0, int16_t *best_perm,
+           int32_t *best_makespan, int64_t *nodes) {
+    return fo_bnb_ex(n, m, p, ub0, FO_RELEASE_HEADS, NULL, 0, best_perm, best_makespan, nodes);
 }

@@ -219,6 +219,57 @@ def test_trivial_ub_formula_is_not_always_valid():
     assert rc == oracle.FO_ENOTFOUND
 
 
+@pytest.mark.parametrize("release", [oracle.RELEASE_HEADS, oracle.RELEASE_EST])
+@pytest.mark.parametrize("seed", range(4))
+def test_bnb_subtree_optimum_is_the_best_completion(seed, release):
+    """A search started at a prefix covers exactly the schedules that begin
+    with it: its optimum is the brute-force best completion of the prefix
+    (not-found when that exceeds ub0), and the smallest optimum over every
+    prefix of one length is the brute-force optimum of the instance."""
+    rng = np.random.default_rng(4200 + seed)
+    n = int(rng.integers(3, 8))
+    m = int(rng.integers(2, 6))
+    p = rand_instance(rng, n, m)
+    opt, _ = brute.optimum(p)
+    ub0 = opt + int(rng.integers(0, 40))
+    for depth in (1, 2):
+        found = []
+        for prefix in itertools.permutations(range(n), depth):
+            rc, best, perm, nodes = oracle.branch_and_bound(p, ub0, release, prefix)
+            want = brute.best_completion(p, list(prefix))
+            assert nodes >= 1
+            if want <= ub0:
+                assert rc == oracle.FO_OK and best == want, (prefix, best, want)
+                assert perm.tolist()[:depth] == list(prefix)
+                assert brute.makespan(p, perm.tolist()) == best
+                found.append(best)
+            else:
+                assert rc == oracle.FO_ENOTFOUND, prefix
+        assert min(found) == opt
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bnb_with_per_job_release_matches_brute_force(seed):
+    """The search bounded with the per-job release times reaches the
+    brute-force optimum, and reports not-found one below it."""
+    rng = np.random.default_rng(4300 + seed)
+    n = int(rng.integers(1, 8))
+    m = int(rng.integers(2, 6))
+    p = rand_instance(rng, n, m)
+    opt, _ = brute.optimum(p)
+    rc, best, perm, _ = oracle.branch_and_bound(p, brute.makespan(p, range(n)), oracle.RELEASE_EST)
+    assert rc == oracle.FO_OK and best == opt == brute.makespan(p, perm.tolist())
+    rc, _, _, _ = oracle.branch_and_bound(p, opt - 1, oracle.RELEASE_EST)
+    assert rc == oracle.FO_ENOTFOUND
+
+
+def test_bnb_refuses_a_bad_prefix():
+    p = workloads.small_bnb_instance()
+    for bad in ((3, 3), (8,), (-1,)):
+        with pytest.raises(ValueError):
+            oracle.branch_and_bound(p, 1000, oracle.RELEASE_HEADS, bad)
+
+
 # ----------------------------- the per-job reading of the release times (RM)
 @pytest.mark.parametrize("seed", range(10))
 def test_est_pair_values_equal_enumerated_minimum(seed):
@@ -335,3 +386,16 @@ def test_neh_gives_a_valid_schedule_at_least_the_optimum():
         v, seq = neh(p)
         assert sorted(seq) == list(range(n))
         assert v == brute.makespan(p, seq) >= brute.optimum(p)[0]
+
+
+def test_iterated_greedy_gives_a_valid_schedule_at_least_the_optimum():
+    from oracle.ig import iterated_greedy
+    from oracle.neh import neh
+    rng = np.random.default_rng(13)
+    for _ in range(8):
+        n = int(rng.integers(1, 8)); m = int(rng.integers(2, 5))
+        p = rand_instance(rng, n, m)
+        v, seq = iterated_greedy(p, iterations=30, seed=1)
+        assert sorted(seq) == list(range(n))
+        assert v == brute.makespan(p, seq)
+        assert brute.optimum(p)[0] <= v <= neh(p)[0]
