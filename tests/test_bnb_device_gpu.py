@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle.neh import neh
 from oracle import brute
 from paper_1208_3933_gb300 import workloads
 
@@ -86,7 +87,7 @@ def test_serving_searches_reach_the_stored_optimum(gpu_lib, seed):
     rec = json.load(open(GOLDEN))["results"][str(seed)]
     p = dict(workloads.serving_searches())[seed]
     with fsp.Instance(p) as inst:
-        st, best, perm, _ = fsp.fsp_branch_and_bound_device(inst, rec["neh"], expand=256)
+        st, best, perm, _ = fsp.fsp_branch_and_bound_device(inst, neh(p)[0], expand=256)
     assert st == fsp.FSP_OK and best == rec["opt"]
     assert brute.makespan(p, perm.tolist()) == best
 
@@ -139,7 +140,7 @@ def test_best_first_is_deterministic(gpu_lib, seed):
     runs = []
     with fsp.Instance(p) as inst:
         for _ in range(2):
-            st, best, perm, nodes = fsp.fsp_branch_and_bound_device(inst, rec["neh"], expand=256,
+            st, best, perm, nodes = fsp.fsp_branch_and_bound_device(inst, neh(p)[0], expand=256,
                                                                     selection=fsp.FSP_SELECT_BEST_FIRST)
             assert st == fsp.FSP_OK and best == rec["opt"]
             assert brute.makespan(p, perm.tolist()) == best

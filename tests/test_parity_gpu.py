@@ -481,3 +481,83 @@ def test_largest_processing_times(gpu_lib):
         assert inst.info().compact == 0
         got = gpu_bounds(fsp, inst, rows, depths)
     assert np.array_equal(got, oracle_bounds(p, rows, depths))
+
+
+def _every_path(fsp, inst, rows, depths):
+    """Bounds of one pool from every kernel and staging mode that can take the
+    instance, the batched launch and the allocation-free batched entry point."""
+    import torch
+    info = inst.info()
+    cfgs = [None, dict(kernel=2, staging=2, warps_per_block=4, positions_per_tile=64),
+            dict(kernel=2, staging=2, warps_per_block=8, pairs_per_tile=96),
+            dict(kernel=2, staging=3, warps_per_block=4), dict(kernel=2, staging=4, warps_per_block=2),
+            dict(kernel=1, nodes_per_thread=2)]
+    if info.flags:
+        cfgs.pop()  # per-job release times: couple-lanes kernels only
+    out = {str(c): gpu_bounds(fsp, inst, rows, depths, config=c) for c in cfgs}
+    if info.compact:
+        r, d = to_dev(rows, depths)
+        o1 = torch.full((rows.shape[0],), -9, dtype=torch.int32, device="cuda")
+        o2 = torch.full((rows.shape[0],), -9, dtype=torch.int32, device="cuda")
+        with fsp.Batch([(inst, r, d, o1)]) as b:
+            b.launch()
+        fsp.fsp_bound_batch_noalloc([(inst, r, d, o2)])
+        torch.cuda.synchronize()
+        out["batch"] = o1.cpu().numpy()
+        out["noalloc"] = o2.cpu().numpy()
+    return out
+
+
+@pytest.mark.parametrize("case", ["p200to255", "all255", "all255_per_job"])
+def test_fp32_scan_exact_at_its_limits(gpu_lib, case):
+    """The two-word records of compact instances carry the job in the lowest
+    10 mantissa bits of float(s) and the couple-lanes scan runs in fp32.  Its
+    margin is smallest where s >= 4096 (the job bits of jobs near 1023 then
+    add almost 1/2 to s) and the slack grows large: n = 1024 jobs, m = 32
+    machines, times 200..255 (every s of the couple (0, 31) between 6,200
+    and 7,905; with m <= 32 and p <= 255, s never reaches 8,192), the last
+    34 jobs at 255 on machines 1..31, shallow prefixes so long scans run.
+    With all times 255 every Johnson order is a tie and every minimum tail is
+    31 x 255, the largest latency a compact record's int16 row holds.  Every
+    kernel, staging mode and batched entry point must match the oracle bit
+    for bit."""
+    fsp = gpu_lib
+    rng = np.random.default_rng(2024)
+    n, m, N = 1024, 32, 160
+    if case == "p200to255":
+        p = rng.integers(200, 256, size=(n, m), dtype=np.int32)
+        p[990:, 1:] = 255
+    else:
+        p = np.full((n, m), 255, np.int32)
+    rows, depths = workloads.random_pool(rng, n, N, max_depth=n + 1)
+    depths[: N // 2] = rng.integers(0, 64, N // 2)  # long scans
+    depths[-3:] = [0, n - 1, n]
+    per_job = case.endswith("per_job")
+    with fsp.Instance(p, flags=fsp.FSP_INSTANCE_RELEASE_PER_JOB if per_job else 0) as inst:
+        assert inst.info().compact == 1
+        got = _every_path(fsp, inst, rows, depths)
+    want = oracle.Tables(p).lb_pool(rows, depths, threads=THREADS,
+                                    release=oracle.RELEASE_EST if per_job else oracle.RELEASE_HEADS)
+    for k, v in got.items():
+        assert np.array_equal(v, want), (case, k, np.nonzero(v != want)[0][:5])
+
+
+@pytest.mark.parametrize("top", [255, 256])
+def test_compact_and_wide_records_at_the_switch(gpu_lib, top):
+    """Largest processing time 255 keeps the compact two-word records, 256
+    switches to 128-bit records (with m <= 32 a row sum s of 8,192 or more
+    needs a time above 255, so the time decides); both sides of the switch
+    must match the oracle on every path."""
+    fsp = gpu_lib
+    rng = np.random.default_rng(2025 + top)
+    n, m, N = 300, 32, 400
+    p = rng.integers(1, 256, size=(n, m), dtype=np.int32)
+    p[n - 1, :] = 255
+    p[n - 1, m - 1] = top
+    rows, depths = workloads.random_pool(rng, n, N, max_depth=n + 1)
+    with fsp.Instance(p) as inst:
+        assert inst.info().compact == (1 if top == 255 else 0)
+        got = _every_path(fsp, inst, rows, depths)
+    want = oracle_bounds(p, rows, depths)
+    for k, v in got.items():
+        assert np.array_equal(v, want), (top, k, np.nonzero(v != want)[0][:5])

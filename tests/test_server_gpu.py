@@ -38,6 +38,8 @@ def test_each_result_is_the_same_alone_and_in_the_mix(gpu_lib):
     specs = [(20, 5, 700), (50, 10, 3000), (200, 20, 2500), (20, 20, 33), (100, 12, 1500), (7, 3, 1)]
     pools = make_pools(fsp, specs, 1)
     ref = [alone(fsp, *p) for p in pools]
+    for (inst, rows, depths), r in zip(pools, ref):  # the alone results are the oracle's
+        assert np.array_equal(r, oracle.Tables(inst.p).lb_pool(rows, depths, threads=16))
     with fsp.Server(hbm_budget_bytes=64 << 20, slots=3) as srv:
         errors = []
 
@@ -172,7 +174,7 @@ def test_cooperating_searchers_reach_the_optimum(gpu_lib, searchers):
         for seed in (200, 201, 203):
             rec = golden[str(seed)]
             with fsp.Instance(probs[seed]) as inst:
-                st, best, perm, nodes, _ = srv.solve(inst, rec["neh"], searchers=searchers, expand=32)
+                st, best, perm, nodes, _ = srv.solve(inst, neh(probs[seed])[0], searchers=searchers, expand=32)
                 assert st == fsp.FSP_OK and best == rec["opt"], (seed, best, rec["opt"])
                 assert brute.makespan(probs[seed], perm.tolist()) == best
                 assert nodes >= 1
