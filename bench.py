@@ -212,8 +212,10 @@ def run_batched_leg(dev, reps: int = 5):
 
     plain_ms = timed(per_pool)
     batch_pools = [(i, r, d, o) for i, (r, d), o in zip(insts, bufs, outs_b)]
-    tuned_w, _ = fsp.fsp_batch_autotune(batch_pools)
+    tuned_w, tuned_c, _ = fsp.fsp_batch_autotune_ex(batch_pools)
     with fsp.Batch(batch_pools, warps_per_block=tuned_w) as b:
+        tile_only_ms = timed(b.launch_graph)
+    with fsp.Batch(batch_pools, warps_per_block=tuned_w, couples_per_item=tuned_c) as b:
         batch_ms = timed(b.launch_graph)
         q = b.query()
     same = all(torch.equal(a, c) for a, c in zip(outs, outs_b))
@@ -223,16 +225,22 @@ def run_batched_leg(dev, reps: int = 5):
             "batched_nodes_per_s": total / (batch_ms * 1e-3), "plain_nodes_per_s": total / (plain_ms * 1e-3),
             "batched_ms": batch_ms, "plain_ms": plain_ms, "speedup": plain_ms / batch_ms,
             "work_items": q["work_items"], "warps_per_block": q["warps_per_block"],
-            "bit_exact_vs_plain": bool(same), "launch": "one CUDA-graph replay, warps per block autotuned"}
+            "couples_per_item": q["couples_per_item"], "tile_only_ms": tile_only_ms,
+            "tuned_shape": {"warps": tuned_w, "couples_per_item": tuned_c},
+            "bit_exact_vs_plain": bool(same),
+            "launch": "one CUDA-graph replay; warps per block and couples per work item autotuned"}
 
 
-def run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, P: int, reps: int = 10):
+def run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, P: int, dep_h, n_jobs: int, m_mach: int,
+                      peak: float, reps: int = 10):
     """Nodes/s against pool size on the same 200x20 instance (the paper varies
     the pool from 4,096 to 262,144 nodes): each size is a slice of the
     device-resident pool copies, a new slice every launch, timed with CUDA
     events; the default launch shape (batches split by couples while the pool
     leaves SMs idle) beside the same shape with every couple in one work item.
-    Both shapes must give identical bounds."""
+    Both shapes must give identical bounds.  Each size's roofline fraction
+    is the algorithmic integer operations of its launches over their time,
+    against the same ALU peak as the main line."""
     import torch
     total = rows_d[0].shape[0]
     out = []
@@ -254,7 +262,11 @@ def run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, P: int, reps: int 
                                    stream=stream, config=cfg)
             e1.record(stream)
             torch.cuda.synchronize()
-            row[key + "_nodes_per_s"] = N * reps / (e0.elapsed_time(e1) * 1e-3)
+            secs = e0.elapsed_time(e1) * 1e-3
+            row[key + "_nodes_per_s"] = N * reps / secs
+            ops = sum(algorithmic_int_ops(n_jobs, m_mach, dep_h[(i * N) % (total - N + 1):][:N])
+                      for i in range(reps))
+            row[key + "_roofline_frac"] = ops / secs / peak
         a = fsp.fsp_bound_pool(inst, rows_d[0][:N], dep_d[0][:N], stream=stream)
         b = fsp.fsp_bound_pool(inst, rows_d[0][:N], dep_d[0][:N], stream=stream, config=whole)
         torch.cuda.synchronize()
@@ -306,74 +318,196 @@ def run_bnb_leg(seeds=(200, 201, 203, 202), node_limit: int = 50_000_000, expand
     return out
 
 
-def run_served_leg(node_limit: int = 2_000_000, expand: int = 128, seconds: float = 40.0):
-    """The serving loop: 32 DFS searches (n=20, m=5 for seeds 200-215 and
-    m=10 for 216-231, NEH upper bound, node limit per search) plus 16 streams
-    of 200x20 pools (4,096-32,768 nodes, Poisson arrivals) share one server.
-    Served nodes/s and p50/p99 pool latency from the server; the plain rate
-    is the same stream pools bounded one by one through fsp_bound_pool_host."""
+def run_config_leg(fsp, name: str, dev, peak: float, steps: int = 20, warmup: int = 3):
+    """One more bounding configuration at full size -- 20x20 (65,536 nodes,
+    seed 1) or 500x20 (65,536 nodes, seed 2, tiled staging) -- measured as
+    the main line is: launch shape autotuned on the pool beforehand, every
+    launch timed with CUDA events on its stream, the L2 flushed (a 256 MB
+    write) between launches so no launch finds its pool in L2, and the
+    roofline fraction = algorithmic integer operations / kernel time / ALU
+    peak."""
+    import torch
+    from paper_1208_3933_gb300 import workloads
+    w = workloads.named_pool(name)
+    stream = torch.cuda.current_stream(dev)
+    with fsp.Instance(w.p) as inst:
+        r = torch.from_numpy(w.rows).to(dev)
+        d = torch.from_numpy(w.depths).to(dev)
+        out = torch.empty(w.N, dtype=torch.int32, device=dev)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        _, tuned_ms = fsp.fsp_autotune(inst, r, d, out, stream=stream)
+        launch = fsp.fsp_tuned_config(inst, w.N)
+        for _ in range(warmup):
+            fsp.fsp_bound_pool(inst, r, d, out, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(i & 255)
+            ev[i][0].record(stream)
+            fsp.fsp_bound_pool(inst, r, d, out, stream=stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    ops = algorithmic_int_ops(w.n, w.m, w.depths)
+    return {"workload": name, "n": w.n, "m": w.m, "nodes": w.N, "seed": w.seed, "nodes_per_s": w.N / (ms * 1e-3),
+            "kernel_ms_mean": ms, "ops_per_launch": ops, "roofline_frac": ops / (ms * 1e-3) / peak,
+            "launch": launch, "kernel": kernel_name(launch), "autotune_ms": tuned_ms,
+            "l2": "256 MB write between launches"}
+
+
+def load_golden_optima():
+    """Optima of the serving-loop searches stored by the oracle (tests/golden)."""
+    gpath = os.path.join(ROOT, "tests", "golden", "serving_optima.json")
+    if not os.path.exists(gpath):
+        return {}
+    return {int(k): v.get("opt") for k, v in json.load(open(gpath))["results"].items()}
+
+
+def run_served_leg(node_limit: int = 500_000_000, expand: int = 1024, ig_iterations: int = 2000,
+                   rate_hz: float = 100.0, pools_per_stream: int = 8):
+    """The serving loop: 32 depth-first searches (n=20; m=5 for seeds 200-215,
+    m=10 for 216-231) plus 16 streams of 200x20 pools (4,096-32,768 nodes,
+    Poisson arrivals), run twice on identical work:
+      served -- every search and stream submits its pools to one bounding
+                server (continuous batching, admission by device footprint);
+      plain  -- the same searches and streams, each pool bounded by its own
+                plain launch (fsp_bound_pool_host on the client's stream).
+    Each search starts from the library's iterated-greedy schedule (computed
+    once, outside both arms) and is cut only by a stated node budget; the
+    searches are deterministic, so both arms bound the same pools.  Reported:
+    nodes/s of each arm (all nodes of both kinds over the arm's wall time),
+    the server's p50/p99 pool latency, and every search's optimum against the
+    optimum the oracle stored."""
     import threading
 
     import torch
     from paper_1208_3933_gb300 import fsp, workloads
-    golden = {}
-    gpath = os.path.join(ROOT, "tests", "golden", "serving_optima.json")
-    if os.path.exists(gpath):
-        golden = {int(k): v.get("opt") for k, v in json.load(open(gpath))["results"].items()}
+    golden = load_golden_optima()
     searches = workloads.serving_searches()
-    streams = workloads.serving_streams(rate_hz=60.0)
+    streams = workloads.serving_streams(rate_hz=rate_hz, pools_per_stream=pools_per_stream)
     s_insts = {s: fsp.Instance(p) for s, p in searches}
     st_insts = [fsp.Instance(p) for p, _ in streams]
-    pools = [[(t, torch.from_numpy(r).pin_memory().numpy(), torch.from_numpy(d).pin_memory().numpy())
-              for t, r, d in pl] for _, pl in streams]
-    results = {}
-    with fsp.Server(hbm_budget_bytes=4 << 30, slots=3) as srv:
-        t_start = time.perf_counter()
+    t0 = time.perf_counter()
+    ub = {s: fsp.fsp_iterated_greedy(s_insts[s], iterations=ig_iterations, seed=s)[0] for s, _ in searches}
+    ig_s = time.perf_counter() - t0
+
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    pools = [[(t, pinned(r), pinned(d), pinned(np.zeros(d.shape[0], np.int32))) for t, r, d in pl]
+             for _, pl in streams]
+    stream_nodes = sum(d.shape[0] for pl in pools for _, _, d, _ in pl)
+
+    def arm(served: bool):
+        results, lat = {}, []
+        srv = fsp.Server(hbm_budget_bytes=4 << 30, slots=3) if served else None
+        errors = []
 
         def search(seed):
-            ub, _ = fsp.fsp_neh(s_insts[seed])
-            results[seed] = srv.search(s_insts[seed], ub, expand=expand, node_limit=node_limit)
+            try:
+                if served:
+                    results[seed] = srv.search(s_insts[seed], ub[seed], expand=expand, node_limit=node_limit)
+                else:
+                    results[seed] = fsp.fsp_search_plain(s_insts[seed], ub[seed], expand=expand,
+                                                         node_limit=node_limit)
+            except Exception as e:  # reported, never silently dropped
+                errors.append(f"search {seed}: {e}")
 
         def stream(i):
-            t0 = time.perf_counter()
-            reqs = []
-            for t, r, d in pools[i]:
-                delay = t - (time.perf_counter() - t0)
-                if delay > 0:
-                    time.sleep(delay)
-                reqs.append(srv.submit(st_insts[i], r, d))
-            for q in reqs:
-                q.wait(int(seconds * 1e6))
+            try:
+                cs = None if served else torch.cuda.Stream()
+                t_0 = time.perf_counter()
+                reqs = []
+                for t, r, d, o in pools[i]:
+                    delay = t - (time.perf_counter() - t_0)
+                    if delay > 0:
+                        time.sleep(delay)
+                    if served:
+                        reqs.append(srv.submit(st_insts[i], r, d, out=o))
+                    else:
+                        a = time.perf_counter()
+                        fsp.fsp_bound_pool_host(st_insts[i], r, d, o, stream=cs)
+                        lat.append(time.perf_counter() - a)
+                for q in reqs:
+                    if q.wait(600_000_000) != fsp.FSP_OK:
+                        errors.append(f"stream {i}: request failed")
+                    q.release()
+            except Exception as e:
+                errors.append(f"stream {i}: {e}")
 
         threads = [threading.Thread(target=search, args=(s,)) for s, _ in searches]
         threads += [threading.Thread(target=stream, args=(i,)) for i in range(len(streams))]
+        t_start = time.perf_counter()
         for t in threads:
             t.start()
         for t in threads:
-            t.join(seconds * 4)
+            t.join()
         wall = time.perf_counter() - t_start
-        st = srv.stats()
-    finished = {s: r for s, r in results.items() if r[0] == fsp.FSP_OK}
-    verified = sum(1 for s, r in finished.items() if golden.get(s) is not None and golden[s] == r[1])
-    wrong = [s for s, r in finished.items() if golden.get(s) is not None and golden[s] != r[1]]
-    # plain: the stream pools bounded one by one, host buffers in and out
-    stream_nodes = 0
-    t0 = time.perf_counter()
-    for inst, pl in zip(st_insts, pools):
-        for _, r, d in pl:
-            fsp.fsp_bound_pool_host(inst, r, d)
-            stream_nodes += d.shape[0]
-    plain_s = time.perf_counter() - t0
+        stats = srv.stats() if served else None
+        if srv is not None:
+            srv.close()
+        outs = [o.copy() for pl in pools for _, _, _, o in pl]
+        return results, wall, stats, lat, outs, errors
+
+    s_res, s_wall, stats, _, s_outs, s_err = arm(True)
+    p_res, p_wall, _, p_lat, p_outs, p_err = arm(False)
+    per_seed, nodes_search = [], 0
+    for seed, p in searches:
+        st, best, _, nodes = s_res.get(seed, (None, None, None, 0))
+        pst, pbest, _, pnodes = p_res.get(seed, (None, None, None, 0))
+        nodes_search += nodes
+        solved = st in (fsp.FSP_OK, fsp.FSP_ENOTFOUND)
+        opt = (best if st == fsp.FSP_OK else ub[seed]) if solved else None
+        per_seed.append({"seed": seed, "m": int(p.shape[1]), "ub0": ub[seed], "status": "solved" if solved else "cut",
+                         "optimum": opt, "nodes": nodes, "oracle_optimum": golden.get(seed),
+                         "plain_same": (st, best, nodes) == (pst, pbest, pnodes)})
+    total = nodes_search + stream_nodes
+    solved = [r for r in per_seed if r["status"] == "solved"]
+    verified = [r["seed"] for r in solved if r["oracle_optimum"] is not None and r["optimum"] == r["oracle_optimum"]]
+    wrong = [r["seed"] for r in solved if r["oracle_optimum"] is not None and r["optimum"] != r["oracle_optimum"]]
+    unverified = [r["seed"] for r in solved if r["oracle_optimum"] is None]
     for inst in list(s_insts.values()) + st_insts:
         inst.close()
-    return {"workload": "32 DFS searches (20x5, 20x10; seeds 200-231) + 16 Poisson streams of 200x20 pools",
-            "served_nodes_per_s": st["nodes_done"] / st["active_seconds"] if st["active_seconds"] else None,
-            "plain_nodes_per_s": stream_nodes / plain_s, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
-            "pools": st["pools_done"], "nodes": st["nodes_done"], "batches": st["batches"],
-            "mean_pools_per_batch": st["mean_pools_per_batch"], "wall_s": wall,
-            "searches_finished": len(finished), "searches_cut_at_node_limit": len(results) - len(finished),
-            "node_limit_per_search": node_limit, "expand": expand,
-            "optima_verified_vs_oracle": verified, "optima_wrong": wrong}
+    return {"workload": "32 DFS searches (20x5 seeds 200-215, 20x10 seeds 216-231) + 16 Poisson streams of "
+                        "200x20 pools", "node_budget_per_search": node_limit, "expand": expand,
+            "ub0": f"library iterated greedy, {ig_iterations} iterations per search ({ig_s:.1f} s, outside both arms)",
+            "served_nodes_per_s": total / s_wall, "plain_nodes_per_s": total / p_wall,
+            "served_over_plain": p_wall / s_wall, "nodes": total, "search_nodes": nodes_search,
+            "stream_nodes": int(stream_nodes), "served_wall_s": s_wall, "plain_wall_s": p_wall,
+            "p50_us": stats["p50_us"], "p99_us": stats["p99_us"], "pools": stats["pools_done"],
+            "batches": stats["batches"], "mean_pools_per_batch": stats["mean_pools_per_batch"],
+            "plain_stream_pool_p50_us": 1e6 * statistics.median(p_lat) if p_lat else None,
+            "same_work": all(r["plain_same"] for r in per_seed) and all(np.array_equal(a, b)
+                                                                        for a, b in zip(s_outs, p_outs)),
+            "searches_solved": len(solved), "searches_cut": [r["seed"] for r in per_seed if r["status"] == "cut"],
+            "optima_verified_vs_oracle": len(verified), "optima_unverified": unverified, "optima_wrong": wrong,
+            "errors": s_err + p_err, "per_seed": per_seed}
+
+
+def summarise(line: dict) -> dict:
+    """Headline numbers of every leg, compact, for the end of the JSON line."""
+    def r3(x):
+        return None if x is None else float(f"{x:.3g}")
+
+    out = {"pool_200x20": {"nodes_per_s": r3(line["value"]), "frac": r3(line["roofline"]["frac"])}}
+    for c in line.get("configs") or []:
+        out[c["workload"]] = {"nodes_per_s": r3(c["nodes_per_s"]), "frac": r3(c["roofline_frac"])}
+    if line.get("pool_sizes"):
+        out["pool_size_frac"] = {str(r["nodes"]): r3(r["default_roofline_frac"]) for r in line["pool_sizes"]}
+    b = line.get("batched")
+    if b:
+        out["batched"] = {"nodes_per_s": r3(b["batched_nodes_per_s"]), "plain_nodes_per_s": r3(b["plain_nodes_per_s"]),
+                          "speedup": r3(b["speedup"]), "bit_exact": b["bit_exact_vs_plain"],
+                          "shape": b.get("tuned_shape")}
+    v = line.get("served")
+    if v:
+        out["served"] = {"served_nodes_per_s": r3(v["served_nodes_per_s"]),
+                         "plain_nodes_per_s": r3(v["plain_nodes_per_s"]),
+                         "served_over_plain": r3(v["served_over_plain"]), "same_work": v["same_work"],
+                         "p50_us": r3(v["p50_us"]), "p99_us": r3(v["p99_us"]),
+                         "solved": f'{v["searches_solved"]}/32', "verified_vs_oracle": v["optima_verified_vs_oracle"],
+                         "unverified": v["optima_unverified"], "wrong": v["optima_wrong"], "cut": v["searches_cut"],
+                         "node_budget": v["node_budget_per_search"]}
+    return out
 
 
 def dist_setup(args):
@@ -572,14 +706,18 @@ def run_gpu(args, world, rank, local):
     info = inst.info()
     # the extra legs run once, in the single-GPU run
     extra = not (args.nodes or args.no_extra) and world == 1
+    sizes = run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, info.pairs, w.depths, w.n, w.m,
+                              peak) if extra else None
+    configs = [run_config_leg(fsp, nm, dev, peak) for nm in ("pool_20x20", "pool_500x20")] if extra else None
+    bnb = run_bnb_leg() if extra else None
     batched = run_batched_leg(dev) if extra else None
     served = run_served_leg() if extra else None
-    bnb = run_bnb_leg() if extra else None
-    sizes = run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, info.pairs) if extra else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": region_ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+fp32-exact", "data": "synthetic",
+        "dtype_note": "integer bound; the couple scan runs in fp32 on integer values below 2^19 with the job "
+                      "in the low mantissa bits of s, exact (every result equals the oracle's int64)",
         "config": {"workload": WORKLOAD, "n": w.n, "m": w.m, "nodes_per_step_per_gpu": w.N, "seed": w.seed,
                    "p": "U[1,99]", "depth": "U{0..199}", "records": "compact" if info.compact else "wide",
                    "l2": "3 rotating pool copies of 105 MB (inputs larger than the 129 MB L2)",
@@ -602,11 +740,13 @@ def run_gpu(args, world, rank, local):
                 "d2h_bytes_per_step": int(4 * w.N), "bit_exact_vs_device": ok_e2e},
         "gpu_launches": launches,
         "clocks": clocks,
+        "pool_sizes": sizes,
+        "bnb_searches": bnb,
+        "configs": configs,
         "batched": batched,
         "served": served,
-        "bnb_searches": bnb,
-        "pool_sizes": sizes,
     }
+    line["summary"] = summarise(line)  # last key: the end of the line holds every leg's headline
     print(json.dumps(line), flush=True)
     inst.close()
 
@@ -623,6 +763,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served legs")
     ap.add_argument("--leg", default="", choices=["", "batched", "served", "searches"],
                     help="run one extra leg alone (single GPU) and print its JSON line (profiling)")
+    ap.add_argument("--served-expand", type=int, default=0, help="served leg: parents per request (profiling)")
+    ap.add_argument("--served-budget", type=int, default=0, help="served leg: node budget per search (profiling)")
     ap.add_argument("--config", default="",
                     help="force a launch shape, e.g. kernel=2,warps_per_block=14 (profiling); default: autotuned")
     args = ap.parse_args()
@@ -635,7 +777,9 @@ def main():
         build.build()
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
-        leg = {"batched": lambda: run_batched_leg(dev), "served": run_served_leg, "searches": run_bnb_leg}[args.leg]()
+        served_kw = {k: v for k, v in (("expand", args.served_expand), ("node_limit", args.served_budget)) if v}
+        leg = {"batched": lambda: run_batched_leg(dev), "served": lambda: run_served_leg(**served_kw),
+               "searches": run_bnb_leg}[args.leg]()
         print(json.dumps({"leg": args.leg, "result": leg}), flush=True)
         return
     if args.warmup < 3:

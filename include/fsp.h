@@ -320,6 +320,18 @@ typedef struct fsp_batch fsp_batch;
 fsp_status fsp_batch_create(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block,
                             fsp_batch **out);
 
+/* fsp_batch_create with a couple split: a work item is a 32-node batch and a
+ * slice of ceil(couples_per_item / 32) groups of 32 machine couples of its
+ * instance (the pair split of the couple-lanes scan); a pool whose instance
+ * has more groups is cut into that many slices per batch, each slice sets up
+ * its nodes and scans its couples, and the slices meet in an atomic max on
+ * the pool's bounds (zeroed by the launch first; an invalid row is found
+ * invalid by every slice).  couples_per_item = 0: every couple in one item
+ * (fsp_batch_create).  Spreads few or uneven pools over more warps.
+ * Errors as fsp_batch_create (FSP_EINVAL also for couples_per_item < 0). */
+fsp_status fsp_batch_create_ex(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block,
+                               int32_t couples_per_item, fsp_batch **out);
+
 /* Enqueues the whole batch on the stream as one persistent kernel (after a
  * reset of its work counter): each warp claims work items until none is
  * left.  Stream-ordered; launches of one plan must not overlap.
@@ -333,6 +345,9 @@ fsp_status fsp_batch_launch_graph(fsp_batch *batch, void *cuda_stream);
 /* Work items, nodes, warps per block and blocks of a plan (any may be NULL). */
 fsp_status fsp_batch_query(const fsp_batch *batch, int64_t *work_items, int64_t *nodes,
                            int32_t *warps_per_block, int32_t *blocks);
+/* fsp_batch_query plus the plan's couples per work item (0 = all). */
+fsp_status fsp_batch_query_ex(const fsp_batch *batch, int64_t *work_items, int64_t *nodes,
+                              int32_t *warps_per_block, int32_t *blocks, int32_t *couples_per_item);
 
 /* Frees the plan; none of its launches may be in flight.  NULL is a no-op. */
 void fsp_batch_destroy(fsp_batch *batch);
@@ -350,6 +365,16 @@ void fsp_batch_destroy(fsp_batch *batch);
  */
 fsp_status fsp_batch_autotune(const fsp_pool_desc *pools, int32_t count, void *cuda_stream,
                               int32_t *best_warps, float *best_ms);
+
+/* fsp_batch_autotune over both shapes of the plan, the node tile and the
+ * pair split: first the warps per block as above (every couple in one work
+ * item), then the two fastest tiles again with 32, 64, 96 and 128 couples
+ * per work item (fsp_batch_create_ex); the fastest pair is returned.
+ *   best_couples_per_item  (or NULL: the node tile alone is tuned) receives
+ *                          0 or the couples per work item.
+ * Synchronous.  Errors as fsp_batch_autotune. */
+fsp_status fsp_batch_autotune_ex(const fsp_pool_desc *pools, int32_t count, void *cuda_stream,
+                                 int32_t *best_warps, int32_t *best_couples_per_item, float *best_ms);
 
 /* ---------------------------------------------------------------------
  * Bounding server: continuous batching of many clients' pools.
@@ -433,6 +458,10 @@ void fsp_server_destroy(fsp_server *srv);
  *   node_limit  stop after this many bound evaluations (0 = no limit); the
  *           search then returns FSP_ETIMEDOUT with its best incumbent so far;
  *   best_perm (host int16 [n] or NULL), best_makespan, nodes_bounded (or NULL).
+ * srv may be NULL: the same search then bounds each pool by its own plain
+ * launch (fsp_bound_pool_host on a stream of its own), so that the served
+ * and the plain forms can be compared on identical pools (the search is
+ * deterministic: same ub0 and expand, same pools, same result).
  * Synchronous.  Errors: FSP_EINVAL, FSP_ENOMEM, FSP_EBUSY, FSP_EBADNODE,
  * FSP_ENOTFOUND (no schedule of makespan <= ub0), FSP_ETIMEDOUT.
  */
@@ -441,6 +470,19 @@ void fsp_server_destroy(fsp_server *srv);
  * paper's method): a complete schedule whose makespan serves as ub0.
  * perm: host int16 [n] or NULL.  Errors: FSP_EINVAL. */
 fsp_status fsp_neh(const fsp_instance *inst, int16_t *perm, int32_t *makespan);
+
+/* Iterated greedy heuristic (Ruiz and Stuetzle 2007; not part of the
+ * paper's method): from the NEH schedule, `iterations` rounds of removing
+ * four random jobs, reinserting each at its best position and improving the
+ * result by reinsertion until no move helps, accepted like simulated
+ * annealing.  A tighter ub0 than NEH, so a search proves the optimum with
+ * fewer nodes.  Deterministic for a given seed.
+ *   iterations  >= 0 (0 = the NEH schedule);  seed  any value;
+ *   perm  host int16 [n] or NULL: the best schedule found;
+ *   makespan  receives its makespan (recomputed from perm: a valid upper bound).
+ * Synchronous, host only.  Errors: FSP_EINVAL. */
+fsp_status fsp_iterated_greedy(const fsp_instance *inst, int32_t iterations, uint64_t seed, int16_t *perm,
+                               int32_t *makespan);
 fsp_status fsp_server_search(fsp_server *srv, const fsp_instance *inst, int32_t ub0, int32_t expand,
                              int64_t node_limit, int16_t *best_perm, int32_t *best_makespan,
                              int64_t *nodes_bounded);

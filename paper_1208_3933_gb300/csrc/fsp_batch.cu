@@ -39,14 +39,19 @@ __global__ void __launch_bounds__(512, 1)
         if ((int64_t)claim >= nitems) break;
         const int2 it = __ldg(items + claim);
         const LanesArgs &a = pools[it.x];
-        const int64_t x = (int64_t)it.y * 32 + lane;
+        // a pool split by couples: item y = batch * S + slice, the slice
+        // covering couple groups [slice * gper, (slice + 1) * gper)
+        const int S = a.gslices > 1 ? a.gslices : 1;
+        const int batch = S > 1 ? it.y / S : it.y, slice = S > 1 ? it.y - batch * S : 0;
+        const int64_t x = (int64_t)batch * 32 + lane;
         int bterm = 0;
         const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * aq_stride, bterm);
         int lb[32];
 #pragma unroll
         for (int b = 0; b < 32; ++b) lb[b] = 0;
-        const int G = a.G, npad = a.npad, m = a.m;
-        for (int g = 0; g < G; ++g) {
+        const int npad = a.npad, m = a.m;
+        const int g0 = S > 1 ? slice * a.gper : 0, G = S > 1 ? min(a.G, g0 + a.gper) : a.G;
+        for (int g = g0; g < G; ++g) {
             const int kk = __ldg(a.gpairs + 2 * (g * 32 + lane)), ll = __ldg(a.gpairs + 2 * (g * 32 + lane) + 1);
             float u[32];
 #pragma unroll
@@ -56,7 +61,14 @@ __global__ void __launch_bounds__(512, 1)
             couple_epilogue<false>(AQ, aq_stride, m, kk, ll, u, lb);
         }
         const int best = transpose_max(lb, lane);
-        if (x < a.N) a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
+        if (x < a.N) {
+            if (S == 1)
+                a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
+            else if (!valid)
+                a.out[x] = FSP_LB_INVALID;  // every slice finds the row invalid
+            else
+                atomicMax(a.out + x, max(best, bterm));  // out was zeroed; bounds are >= 0
+        }
         __syncwarp();  // the flag and row arrays are rewritten by the next item
     }
 }
@@ -109,9 +121,10 @@ fsp_status enqueue(fsp_batch *b, cudaStream_t s) { return launch_plan(b->d_pools
 
 namespace fspgb {
 
-fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block, int device,
-                      std::vector<LanesArgs> &args, std::vector<int2> &items, PlanParams &pp) {
-    if (count < 0 || (count > 0 && !pools) || warps_per_block < 0 || warps_per_block > 16) return FSP_EINVAL;
+fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block, int32_t couples_per_item,
+                      int device, std::vector<LanesArgs> &args, std::vector<int2> &items, PlanParams &pp) {
+    if (count < 0 || (count > 0 && !pools) || warps_per_block < 0 || warps_per_block > 16 || couples_per_item < 0)
+        return FSP_EINVAL;
     int n_max = 1, m_max = 2, mp = 8;
     for (int32_t i = 0; i < count; ++i) {
         const fsp_pool_desc &p = pools[i];
@@ -122,6 +135,8 @@ fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_p
         mp = std::max(mp, p.inst->mpad);
     }
     pp = PlanParams();
+    pp.couples_per_item = couples_per_item;
+    const int gper = couples_per_item ? (couples_per_item + 31) / 32 : 0;  // couple groups per item
     pp.mp = mp;
     pp.n_max = flag_words(n_max);  // flag words per warp
     pp.stride = (m_max + (m_max + 1) / 2) | 1;
@@ -154,14 +169,24 @@ fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_p
         a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
         a.q32 = inst->compact ? 0 : 1;
         a.wait_limit = 4000000000LL;
+        const int S = (gper && inst->G > gper) ? (inst->G + gper - 1) / gper : 1;
+        a.gper = S > 1 ? gper : inst->G;
+        a.gslices = S;
         const int64_t nb = (p.N + 31) / 32;
-        for (int64_t k = 0; k < nb; ++k) items.push_back(make_int2(i, (int)k));
+        if (nb * S > INT32_MAX) return FSP_EINVAL;
+        for (int64_t k = 0; k < nb * S; ++k) items.push_back(make_int2(i, (int)k));
+        if (S > 1 && p.N > 0) pp.zero.emplace_back(p.out_lb, p.N);
         pp.nodes += p.N;
     }
-    std::stable_sort(items.begin(), items.end(), [&](const int2 &x, const int2 &y) {
-        const int64_t cx = (int64_t)args[x.x].G * args[x.x].npad, cy = (int64_t)args[y.x].G * args[y.x].npad;
-        return cx > cy;
-    });
+    // longest first: couple groups of the item x Johnson positions
+    auto cost = [&](const int2 &w) {
+        const LanesArgs &a = args[w.x];
+        const int S = a.gslices;
+        const int slice = S > 1 ? w.y % S : 0;
+        const int groups = S > 1 ? std::min(a.G - slice * a.gper, a.gper) : a.G;
+        return (int64_t)groups * a.npad;
+    };
+    std::stable_sort(items.begin(), items.end(), [&](const int2 &x, const int2 &y) { return cost(x) > cost(y); });
     pp.nitems = (int64_t)items.size();
     if (pp.nitems > INT32_MAX) return FSP_EINVAL;
     // shared memory: flags [warps][n_max] words, rows [warps][32][stride] ints
@@ -188,6 +213,8 @@ fsp_status launch_plan(const LanesArgs *d_args, const int2 *d_items, int32_t *d_
                        cudaStream_t s) {
     if (pp.nitems == 0) return FSP_OK;
     if (cudaMemsetAsync(d_counter, 0, sizeof(int32_t), s) != cudaSuccess) return FSP_ECUDA;
+    for (const auto &z : pp.zero)
+        if (cudaMemsetAsync(z.first, 0, sizeof(int32_t) * (size_t)z.second, s) != cudaSuccess) return FSP_ECUDA;
     cudaError_t e;
     switch (pp.mp) {
 #define FSP_BATCH_CASE(MPV)                                                                                    \
@@ -213,6 +240,11 @@ fsp_status launch_plan(const LanesArgs *d_args, const int2 *d_items, int32_t *d_
 
 extern "C" fsp_status fsp_batch_create(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block,
                                        fsp_batch **out) {
+    return fsp_batch_create_ex(pools, count, warps_per_block, 0, out);
+}
+
+extern "C" fsp_status fsp_batch_create_ex(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block,
+                                          int32_t couples_per_item, fsp_batch **out) {
     if (!out) return FSP_EINVAL;
     *out = nullptr;
     int dev = -1;
@@ -220,7 +252,7 @@ extern "C" fsp_status fsp_batch_create(const fsp_pool_desc *pools, int32_t count
     std::vector<LanesArgs> args;
     std::vector<int2> items;
     PlanParams pp;
-    fsp_status st = build_plan(pools, count, warps_per_block, dev, args, items, pp);
+    fsp_status st = build_plan(pools, count, warps_per_block, couples_per_item, dev, args, items, pp);
     if (st != FSP_OK) return st;
     fsp_batch *b = new (std::nothrow) fsp_batch();
     if (!b) return FSP_ENOMEM;
@@ -293,6 +325,13 @@ extern "C" fsp_status fsp_batch_launch_graph(fsp_batch *b, void *cuda_stream) {
     return cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? FSP_OK : FSP_ECUDA;
 }
 
+extern "C" fsp_status fsp_batch_query_ex(const fsp_batch *b, int64_t *work_items, int64_t *nodes,
+                                         int32_t *warps_per_block, int32_t *blocks, int32_t *couples_per_item) {
+    if (!b) return FSP_EINVAL;
+    if (couples_per_item) *couples_per_item = b->pp.couples_per_item;
+    return fsp_batch_query(b, work_items, nodes, warps_per_block, blocks);
+}
+
 extern "C" fsp_status fsp_batch_query(const fsp_batch *b, int64_t *work_items, int64_t *nodes,
                                       int32_t *warps_per_block, int32_t *blocks) {
     if (!b) return FSP_EINVAL;
@@ -311,11 +350,36 @@ extern "C" void fsp_batch_destroy(fsp_batch *b) {
     delete b;
 }
 
-// Times plans of the same pools with 16, 12, 8, 6, 4 and 2 warps per block
-// (each on the stream: one warm-up launch, then three timed ones) and
-// reports the fastest.  Every candidate writes the same bounds.
-extern "C" fsp_status fsp_batch_autotune(const fsp_pool_desc *pools, int32_t count, void *cuda_stream,
-                                         int32_t *best_warps, float *best_ms) {
+// Times one plan shape on the stream: one warm-up launch, then three timed
+// ones.  *ms = -1 when the shape does not fit the batch.
+static fsp_status time_plan(const fsp_pool_desc *pools, int32_t count, int W, int cpi, cudaStream_t s,
+                            cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+    *ms = -1.f;
+    fsp_batch *b = nullptr;
+    const fsp_status cs = fsp_batch_create_ex(pools, count, W, cpi, &b);
+    if (cs == FSP_EINVAL) return FSP_OK;  // the shape does not fit this batch
+    if (cs != FSP_OK) return cs;
+    constexpr int kReps = 3;
+    float t = 0.f;
+    fsp_status st = fsp_batch_launch(b, s);
+    if (st == FSP_OK && cudaEventRecord(e0, s) != cudaSuccess) st = FSP_ECUDA;
+    for (int r = 0; r < kReps && st == FSP_OK; ++r) st = fsp_batch_launch(b, s);
+    if (st == FSP_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        st = FSP_ECUDA;
+    cudaStreamSynchronize(s);
+    fsp_batch_destroy(b);
+    if (st == FSP_OK) *ms = t / kReps;
+    return st;
+}
+
+// Node tile first: plans of the same pools with 16, 12, 8, 6, 4 and 2 warps
+// per block, every couple of a batch in one work item; then the couple
+// split: the two fastest tiles again with 32, 64, 96 and 128 couples per
+// work item (pools of more couple groups are split into that many slices).
+// Every candidate writes the same bounds.
+extern "C" fsp_status fsp_batch_autotune_ex(const fsp_pool_desc *pools, int32_t count, void *cuda_stream,
+                                            int32_t *best_warps, int32_t *best_couples_per_item, float *best_ms) {
     if (!pools || count < 1 || !best_warps) return FSP_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -324,31 +388,31 @@ extern "C" fsp_status fsp_batch_autotune(const fsp_pool_desc *pools, int32_t cou
         return FSP_ECUDA;
     }
     fsp_status st = FSP_OK;
-    float best = 1e30f;
-    int bw = 0;
+    std::vector<std::pair<float, int>> tiles;  // (ms, warps)
     for (int W : {16, 12, 8, 6, 4, 2}) {
-        fsp_batch *b = nullptr;
-        const fsp_status cs = fsp_batch_create(pools, count, W, &b);
-        if (cs == FSP_EINVAL) continue;  // the shape does not fit this batch
-        if (cs != FSP_OK) {
-            st = cs;
-            break;
-        }
-        constexpr int kReps = 3;
-        float ms = 0.f;
-        st = fsp_batch_launch(b, s);
-        if (st == FSP_OK && cudaEventRecord(e0, s) != cudaSuccess) st = FSP_ECUDA;
-        for (int r = 0; r < kReps && st == FSP_OK; ++r) st = fsp_batch_launch(b, s);
-        if (st == FSP_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-            st = FSP_ECUDA;
-        cudaStreamSynchronize(s);
-        fsp_batch_destroy(b);
+        float ms = -1.f;
+        st = time_plan(pools, count, W, 0, s, e0, e1, &ms);
         if (st != FSP_OK) break;
-        ms /= kReps;
-        if (ms < best) {
-            best = ms;
-            bw = W;
+        if (ms >= 0.f) tiles.emplace_back(ms, W);
+    }
+    float best = 1e30f;
+    int bw = 0, bc = 0;
+    if (st == FSP_OK && !tiles.empty()) {
+        std::sort(tiles.begin(), tiles.end());
+        best = tiles[0].first;
+        bw = tiles[0].second;
+        if (best_couples_per_item) {
+            for (size_t t = 0; t < std::min<size_t>(2, tiles.size()) && st == FSP_OK; ++t)
+                for (int cpi : {32, 64, 96, 128}) {
+                    float ms = -1.f;
+                    st = time_plan(pools, count, tiles[t].second, cpi, s, e0, e1, &ms);
+                    if (st != FSP_OK) break;
+                    if (ms >= 0.f && ms < best) {
+                        best = ms;
+                        bw = tiles[t].second;
+                        bc = cpi;
+                    }
+                }
         }
     }
     cudaEventDestroy(e0);
@@ -356,7 +420,12 @@ extern "C" fsp_status fsp_batch_autotune(const fsp_pool_desc *pools, int32_t cou
     if (st != FSP_OK) return st;
     if (!bw) return FSP_EINVAL;
     *best_warps = bw;
+    if (best_couples_per_item) *best_couples_per_item = bc;
     if (best_ms) *best_ms = best;
     return FSP_OK;
 }
 
+extern "C" fsp_status fsp_batch_autotune(const fsp_pool_desc *pools, int32_t count, void *cuda_stream,
+                                         int32_t *best_warps, float *best_ms) {
+    return fsp_batch_autotune_ex(pools, count, cuda_stream, best_warps, nullptr, best_ms);
+}

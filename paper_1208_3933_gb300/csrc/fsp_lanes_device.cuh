@@ -71,6 +71,10 @@ __device__ __forceinline__ void warp_transpose32_n(uint32_t (&x)[NV], int lane) 
 
 // Machines of the minima search handled together (MP is a multiple of 4).
 constexpr int kMinimaChunk = 4;
+// Nodes with at most this many unscheduled jobs take their minima by walking
+// those jobs (instances of at most kWalkMaxMP padded machines).
+constexpr int kWalkMinima = 16;
+constexpr int kWalkMaxMP = 20;
 
 // Copies the first 32 entries of every machine's head- and tail-sorted job
 // lists into shared memory ([m][32] each; entries past n read (0,0)).
@@ -115,13 +119,49 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     const int16_t *row = a.nodes + x * (int64_t)n;
     const int dv = valid ? d : 0;
     bool bad = false;
-    auto take = [&](int j) {
+    // membership of job j (clamped into range: an invalid row is discarded)
+    auto mark = [&](int j) {
         const bool inr = (unsigned)j < (unsigned)n;
         const int jj = inr ? j : 0;
         uint32_t *wp = F + (jj >> 5) * 32 + lane;
         const uint32_t bit = 1u << (jj & 31), old = *wp;
         bad |= !inr || (old & bit) != 0u;
         *wp = old | bit;
+        return jj;
+    };
+    // four consecutive jobs: machine k of job t needs job t's machine k-1 and
+    // job t-1's machine k, so the four recurrences run as a wavefront (23
+    // dependent steps for 20 machines instead of 80) and their processing
+    // times are loaded together
+    auto take4 = [&](int j0, int j1, int j2, int j3) {
+        const int4 *p0 = reinterpret_cast<const int4 *>(a.pp + (size_t)mark(j0) * a.mpad);
+        const int4 *p1 = reinterpret_cast<const int4 *>(a.pp + (size_t)mark(j1) * a.mpad);
+        const int4 *p2 = reinterpret_cast<const int4 *>(a.pp + (size_t)mark(j2) * a.mpad);
+        const int4 *p3 = reinterpret_cast<const int4 *>(a.pp + (size_t)mark(j3) * a.mpad);
+        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+#pragma unroll
+        for (int q = 0; q < MP / 4; ++q) {
+            const bool in = 4 * q < a.mpad;
+            const int4 v0 = in ? __ldg(p0 + q) : make_int4(0, 0, 0, 0);
+            const int4 v1 = in ? __ldg(p1 + q) : make_int4(0, 0, 0, 0);
+            const int4 v2 = in ? __ldg(p2 + q) : make_int4(0, 0, 0, 0);
+            const int4 v3 = in ? __ldg(p3 + q) : make_int4(0, 0, 0, 0);
+            const int q0[4] = {v0.x, v0.y, v0.z, v0.w}, q1[4] = {v1.x, v1.y, v1.z, v1.w};
+            const int q2[4] = {v2.x, v2.y, v2.z, v2.w}, q3[4] = {v3.x, v3.y, v3.z, v3.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = 4 * q + e;
+                c0 = __viaddmax_s32(c0, q0[e], C[k] + q0[e]);
+                c1 = __viaddmax_s32(c1, q1[e], c0 + q1[e]);
+                c2 = __viaddmax_s32(c2, q2[e], c1 + q2[e]);
+                c3 = __viaddmax_s32(c3, q3[e], c2 + q3[e]);
+                C[k] = c3;
+                Ps[k] += (q0[e] + q1[e]) + (q2[e] + q3[e]);
+            }
+        }
+    };
+    auto take = [&](int j) {
+        const int jj = mark(j);
         const int4 *pj = reinterpret_cast<const int4 *>(a.pp + (size_t)jj * a.mpad);
         int c = 0;
 #pragma unroll
@@ -146,10 +186,7 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
 #pragma unroll 1
         for (; i + 4 <= dv; i += 4) {
             const int2 nv = i + 8 <= dv ? __ldg(row4 + (i >> 2) + 1) : make_int2(0, 0);
-            take((int)(int16_t)(v.x & 0xFFFF));
-            take(v.x >> 16);
-            take((int)(int16_t)(v.y & 0xFFFF));
-            take(v.y >> 16);
+            take4((int)(int16_t)(v.x & 0xFFFF), v.x >> 16, (int)(int16_t)(v.y & 0xFFFF), v.y >> 16);
             v = nv;
         }
     }
@@ -200,6 +237,52 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
             }
         }
     }
+    // Deep nodes (at most kWalkMinima unscheduled jobs): the release and
+    // latency minima are taken by walking the node's own unscheduled jobs in
+    // its bitmap, min over U of sum_{h<k} p_jh and of sum_{h>k} p_jh, for
+    // every machine at once.  The sorted lists below would find them only
+    // after many rounds, when nearly every listed job is scheduled.  The
+    // minima kept in registers limit this to instances of at most kWalkMaxMP
+    // (padded) machines.
+    const bool walk = MP <= kWalkMaxMP && valid && d < n && n - d <= kWalkMinima;
+    int MH[MP <= kWalkMaxMP ? MP : 1], MQ[MP <= kWalkMaxMP ? MP : 1];
+    if constexpr (MP <= kWalkMaxMP) {
+#pragma unroll
+        for (int k = 0; k < MP; ++k) {
+            MH[k] = INT_MAX;
+            MQ[k] = INT_MAX;
+        }
+        if (walk) {
+            for (int w = 0; w < nw; ++w) {
+                uint32_t un = ~F[w * 32 + lane];
+                if (w == nw - 1 && (n & 31)) un &= (1u << (n & 31)) - 1u;
+                while (un) {
+                    const int j = w * 32 + __ffs(un) - 1;
+                    un &= un - 1u;
+                    const int4 *pj = reinterpret_cast<const int4 *>(a.pp + (size_t)j * a.mpad);
+                    int pv[MP];
+#pragma unroll
+                    for (int q = 0; q < MP / 4; ++q) {
+                        const int4 v = 4 * q < a.mpad ? __ldg(pj + q) : make_int4(0, 0, 0, 0);
+                        pv[4 * q] = v.x;
+                        pv[4 * q + 1] = v.y;
+                        pv[4 * q + 2] = v.z;
+                        pv[4 * q + 3] = v.w;
+                    }
+                    int rowsum = 0;
+#pragma unroll
+                    for (int k = 0; k < MP; ++k) rowsum += pv[k];  // padding columns are zero
+                    int head = 0;
+#pragma unroll
+                    for (int k = 0; k < MP; ++k) {
+                        MH[k] = min(MH[k], head);
+                        MQ[k] = min(MQ[k], rowsum - head - pv[k]);
+                        head += pv[k];
+                    }
+                }
+            }
+        }
+    }
     // (2) the flag words: transposing lane L's bitmap word w gives lane i the
     // bits over nodes of job 32 w + i; F[j] bit b = job j unscheduled in the
     // warp's node b (valid nodes only)
@@ -218,7 +301,7 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     // the first hit's sum is shuffled in.  Round 0 covers the 32 cheapest
     // entries (from the shared-memory copy when given); nodes whose entries
     // were all scheduled go on round by round.
-    const bool settled = !valid || d == n;  // nothing to search for
+    const bool settled = !valid || d == n || walk;  // nothing to search for
     const bool q32 = a.q32 != 0;
     uint32_t open_h = 0, open_t = 0;  // machines still searching (bit k)
     const bool in = lane < n;
@@ -252,8 +335,14 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
                 const int vh = __shfl_sync(kFull, eh[c].y, fh < 0 ? 0 : fh);
                 const int vt = __shfl_sync(kFull, et[c].y, ft < 0 ? 0 : ft);
                 if (k < m) {
-                    const int mh = (!settled && fh >= 0) ? vh : 0;
-                    const int ql = (!settled && ft >= 0) ? vt : 0;
+                    int mh = (!settled && fh >= 0) ? vh : 0;
+                    int ql = (!settled && ft >= 0) ? vt : 0;
+                    if constexpr (MP <= kWalkMaxMP) {
+                        if (walk) {
+                            mh = MH[k];
+                            ql = MQ[k];
+                        }
+                    }
                     if (want_h && !settled && fh < 0)
                         open_h |= 1u << k;  // A_k once a later round finds the minimum
                     else

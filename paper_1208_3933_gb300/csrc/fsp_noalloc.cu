@@ -6,15 +6,18 @@
 // that must not take cudaMalloc's implicit device synchronisation, or code
 // running where allocation is not permitted.  fsp_bound_batch_noalloc gives
 // them the batched bound of fsp_batch_create + fsp_batch_launch without any
-// allocation: the plan (one argument block per pool, the prefix sums of the
-// pools' work items) and the work counter live in the file-scope array below,
-// whose size caps the number of pools per call.
+// allocation.  The plan (one argument block per pool and the prefix sums of
+// the pools' work items, at most FSP_NOALLOC_MAX_POOLS pools) travels to the
+// device inside the kernel's parameter block, so no host buffer is copied
+// and nothing on the host has to outlive the call.  The only device scratch,
+// the work counter the warps claim items from, lives in the file-scope array
+// below.
 //
-// The array is one per device and shared by every call: a call overwrites
-// the previous call's plan and re-zeroes the counter, so calls whose work
-// overlaps on the GPU race with each other.  The first call on a device looks
-// up the array's device address (cudaGetSymbolAddress) with that device
-// current; do that first call outside any stream capture.
+// The array is one per device and shared by every call: a call re-zeroes the
+// counter, so calls whose work overlaps on the GPU race with each other.  The
+// first call on a device looks up the array's device address
+// (cudaGetSymbolAddress) with that device current; do that first call
+// outside any stream capture.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,12 +33,16 @@ namespace {
 
 constexpr int kNoallocMaxPools = FSP_NOALLOC_MAX_POOLS;
 
-// Layout of the scratch array: [pools][LanesArgs] | [pools+1][int64 item
-// offsets] | [int32 counter], each part 256-byte aligned.
-constexpr size_t kArgsBytes = (sizeof(LanesArgs) * kNoallocMaxPools + 255) / 256 * 256;
-constexpr size_t kOffsBytes = (sizeof(int64_t) * (kNoallocMaxPools + 1) + 255) / 256 * 256;
-constexpr size_t kScratchBytes = kArgsBytes + kOffsBytes + 256;
+// The plan of one call, passed by value as the kernel's parameter block
+// (about 14 KB, within the 32,764 bytes a kernel's parameters may take).
+struct NoallocPlan {
+    LanesArgs pools[kNoallocMaxPools];
+    int64_t offs[kNoallocMaxPools + 1];  // work-item prefix sums of the pools
+};
+static_assert(sizeof(NoallocPlan) + 64 <= 32764, "plan exceeds the kernel parameter space");
 
+// Device scratch of the entry point: the work counter (one int32 at offset 0).
+constexpr size_t kScratchBytes = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Work item `claim` of the plan belongs to the pool whose [offs[p], offs[p+1])
@@ -44,7 +51,7 @@ __device__ __forceinline__ int pool_of(const int64_t *offs, int count, int64_t c
     int lo = 0, hi = count - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(offs + mid) <= claim)
+        if (offs[mid] <= claim)
             lo = mid;
         else
             hi = mid - 1;
@@ -54,12 +61,9 @@ __device__ __forceinline__ int pool_of(const int64_t *offs, int count, int64_t c
 
 template <int MP>
 __global__ void __launch_bounds__(512, 1)
-    fsp_lanes_batch_noalloc(const unsigned char *scratch, int count, int64_t nitems, int32_t n_max,
-                            int32_t aq_stride, uint32_t off_aq) {
+    fsp_lanes_batch_noalloc(const __grid_constant__ NoallocPlan plan, int32_t *counter, int count, int64_t nitems,
+                            int32_t n_max, int32_t aq_stride, uint32_t off_aq) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const LanesArgs *pools = reinterpret_cast<const LanesArgs *>(scratch);
-    const int64_t *offs = reinterpret_cast<const int64_t *>(scratch + kArgsBytes);
-    int32_t *counter = reinterpret_cast<int32_t *>(const_cast<unsigned char *>(scratch) + kArgsBytes + kOffsBytes);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *F = reinterpret_cast<uint32_t *>(smem) + (size_t)warp * n_max;
     int32_t *AQ = reinterpret_cast<int32_t *>(smem + off_aq) + (size_t)warp * 32 * aq_stride;
@@ -68,9 +72,9 @@ __global__ void __launch_bounds__(512, 1)
         if (lane == 0) claim = atomicAdd(counter, 1);
         claim = __shfl_sync(kFull, claim, 0);
         if ((int64_t)claim >= nitems) break;
-        const int pi = pool_of(offs, count, claim);
-        const LanesArgs &a = pools[pi];
-        const int64_t x = ((int64_t)claim - __ldg(offs + pi)) * 32 + lane;
+        const int pi = pool_of(plan.offs, count, claim);
+        const LanesArgs &a = plan.pools[pi];
+        const int64_t x = ((int64_t)claim - plan.offs[pi]) * 32 + lane;
         int bterm = 0;
         const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * aq_stride, bterm);
         int lb[32];
@@ -107,13 +111,20 @@ fsp_status scratch_address(int dev, unsigned char **out) {
     return FSP_OK;
 }
 
+// The kernel's dynamic shared-memory limit is raised to the device's opt-in
+// maximum once per device and variant, so concurrent calls never change it
+// under each other; each launch passes its own size.
 template <int MP>
-cudaError_t launch_noalloc(const unsigned char *scratch, int count, int64_t nitems, int n_max, int stride,
-                           uint32_t off_aq, int grid, int threads, size_t smem, cudaStream_t s) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(fsp_lanes_batch_noalloc<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    fsp_lanes_batch_noalloc<MP><<<grid, threads, smem, s>>>(scratch, count, nitems, n_max, stride, off_aq);
+cudaError_t launch_noalloc(int dev, const NoallocPlan &plan, int32_t *counter, int count, int64_t nitems, int n_max,
+                           int stride, uint32_t off_aq, int grid, int threads, size_t smem, cudaStream_t s) {
+    static std::once_flag once[64];
+    static cudaError_t attr_err[64] = {};
+    std::call_once(once[dev], [dev] {
+        attr_err[dev] = cudaFuncSetAttribute(fsp_lanes_batch_noalloc<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             max_smem_per_block(dev));
+    });
+    if (attr_err[dev] != cudaSuccess) return attr_err[dev];
+    fsp_lanes_batch_noalloc<MP><<<grid, threads, smem, s>>>(plan, counter, count, nitems, n_max, stride, off_aq);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -143,24 +154,29 @@ extern "C" fsp_status fsp_bound_batch_noalloc(const fsp_pool_desc *pools, int32_
     fsp_status st = scratch_address(dev, &scratch);
     if (st != FSP_OK) return st;
 
-    // The plan is built on the stack (no heap either): pools ordered by the
-    // cost of one work item, longest first, then their item prefix sums.
+    // The plan is built on the host without allocating: pools ordered by the
+    // cost of one work item, longest first (an insertion sort, stable, on at
+    // most 64 entries), then their item prefix sums.  It is handed to the
+    // kernel by value; the launch copies it, so the one static plan buffer
+    // (14 KB, kept off the caller's stack) is free again when the launch
+    // returns, and a mutex keeps two threads' calls from filling it at once.
     int order[kNoallocMaxPools];
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order, order + count, [&](int x, int y) {
-        const int64_t cx = (int64_t)pools[x].inst->G * pools[x].inst->npad;
-        const int64_t cy = (int64_t)pools[y].inst->G * pools[y].inst->npad;
-        return cx > cy;
-    });
+    auto cost = [&](int i) { return (int64_t)pools[i].inst->G * pools[i].inst->npad; };
+    for (int i = 0; i < count; ++i) {
+        int j = i;
+        for (; j > 0 && cost(order[j - 1]) < cost(i); --j) order[j] = order[j - 1];
+        order[j] = i;
+    }
     const int stride = (m_max + (m_max + 1) / 2) | 1;
-    LanesArgs args[kNoallocMaxPools];
-    int64_t offs[kNoallocMaxPools + 1];
-    std::memset(args, 0, sizeof(LanesArgs) * count);
-    offs[0] = 0;
+    static NoallocPlan plan;
+    static std::mutex plan_mu;
+    std::lock_guard<std::mutex> plan_lock(plan_mu);
+    std::memset(&plan, 0, sizeof plan);
+    plan.offs[0] = 0;
     for (int r = 0; r < count; ++r) {
         const fsp_pool_desc &p = pools[order[r]];
         const fsp_instance *inst = p.inst;
-        LanesArgs &a = args[r];
+        LanesArgs &a = plan.pools[r];
         a.grec = static_cast<const unsigned char *>(inst->t.grec);
         a.gpairs = inst->t.gpairs;
         a.hsort = reinterpret_cast<const int2 *>(inst->t.hsort);
@@ -181,9 +197,9 @@ extern "C" fsp_status fsp_bound_batch_noalloc(const fsp_pool_desc *pools, int32_
         a.aq_stride = stride;
         a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
         a.q32 = inst->compact ? 0 : 1;
-        offs[r + 1] = offs[r] + (p.N + 31) / 32;
+        plan.offs[r + 1] = plan.offs[r] + (p.N + 31) / 32;
     }
-    const int64_t nitems = offs[count];
+    const int64_t nitems = plan.offs[count];
     if (nitems > INT32_MAX) return FSP_EINVAL;
     if (nitems == 0) return FSP_OK;
 
@@ -201,20 +217,21 @@ extern "C" fsp_status fsp_bound_batch_noalloc(const fsp_pool_desc *pools, int32_
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nitems + W - 1) / W, num_sms(dev)));
 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    // pageable sources: each copy has consumed its source when it returns
-    if (cudaMemcpyAsync(scratch, args, sizeof(LanesArgs) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(scratch + kArgsBytes, offs, sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess ||
-        cudaMemsetAsync(scratch + kArgsBytes + kOffsBytes, 0, sizeof(int32_t), s) != cudaSuccess)
-        return FSP_ECUDA;
+    int32_t *counter = reinterpret_cast<int32_t *>(scratch);
+    if (cudaMemsetAsync(counter, 0, sizeof(int32_t), s) != cudaSuccess) return FSP_ECUDA;
     cudaError_t e;
     switch (mp) {
-        case 8: e = launch_noalloc<8>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
-        case 12: e = launch_noalloc<12>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
-        case 16: e = launch_noalloc<16>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
-        case 20: e = launch_noalloc<20>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
-        case 24: e = launch_noalloc<24>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
-        default: e = launch_noalloc<32>(scratch, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
+#define FSP_NOALLOC_CASE(MPV)                                                                                  \
+    case MPV:                                                                                                   \
+        e = launch_noalloc<MPV>(dev, plan, counter, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); \
+        break;
+        FSP_NOALLOC_CASE(8)
+        FSP_NOALLOC_CASE(12)
+        FSP_NOALLOC_CASE(16)
+        FSP_NOALLOC_CASE(20)
+        FSP_NOALLOC_CASE(24)
+#undef FSP_NOALLOC_CASE
+        default: e = launch_noalloc<32>(dev, plan, counter, count, nitems, n_max, stride, off_aq, grid, 32 * W, smem, s); break;
     }
     return e == cudaSuccess ? FSP_OK : FSP_ECUDA;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 #include "fsp_internal.h"
@@ -55,14 +56,20 @@ struct LanesArgs {
 struct PlanParams {
     int64_t nitems = 0, nodes = 0;
     int mp = 8, n_max = 1, stride = 1, warps = 16, grid = 1;
+    int couples_per_item = 0;  // 0: every couple of a node batch in one work item
     uint32_t off_aq = 0;
     size_t smem = 0;
+    // bounds of pools split by couples: zeroed before the kernel, whose
+    // slices then meet in an atomic max
+    std::vector<std::pair<int32_t *, int64_t>> zero;
 };
 
-// Builds a batch plan on the host: per-pool arguments and the 32-node work
-// items ordered longest first (fsp_batch.cu).
-fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block, int device,
-                      std::vector<LanesArgs> &args, std::vector<int2> &items, PlanParams &pp);
+// Builds a batch plan on the host: per-pool arguments and the work items,
+// ordered longest first (fsp_batch.cu).  A work item is a 32-node batch of a
+// pool and, with couples_per_item > 0, a slice of ceil(couples_per_item / 32)
+// of its instance's couple groups.
+fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block, int32_t couples_per_item,
+                      int device, std::vector<LanesArgs> &args, std::vector<int2> &items, PlanParams &pp);
 // Enqueues a plan already copied to the device: counter reset + kernel.
 fsp_status launch_plan(const LanesArgs *d_args, const int2 *d_items, int32_t *d_counter, const PlanParams &pp,
                        cudaStream_t s);

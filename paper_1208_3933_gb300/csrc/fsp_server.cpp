@@ -97,11 +97,19 @@ struct fsp_request {
     const int32_t *depths = nullptr;
     int32_t *out = nullptr;
     int64_t N = 0;
-    size_t bytes = 0, off = 0;
+    size_t bytes = 0, off = 0;    // arena footprint (0: bounded in place)
+    // page-locked client buffers are bounded in place: the kernel reads the
+    // rows and depths and writes the bounds through these device-visible
+    // addresses of the client's own memory, with no copy and no arena space
+    bool in_place = false;
+    const int16_t *dv_nodes = nullptr;
+    const int32_t *dv_depths = nullptr;
+    int32_t *dv_out = nullptr;
     Clock::time_point t_submit;
     int state = kQueued;          // guarded by the server mutex
     fsp_status result = FSP_OK;
     bool released = false;        // the client dropped its handle
+    std::condition_variable cv;   // this request's completion (server mutex)
 };
 
 namespace {
@@ -109,8 +117,7 @@ namespace {
 struct Slot {
     cudaStream_t stream = nullptr;
     std::vector<fsp_request *> reqs;
-    bool busy = false;
-    bool done = false;  // set by the completion callback
+    bool busy = false;  // cleared by the completion callback
     // plan buffers: pinned host staging and device copies
     fspgb::LanesArgs *h_args = nullptr, *d_args = nullptr;
     int2 *h_items = nullptr, *d_items = nullptr;
@@ -129,7 +136,6 @@ struct fsp_server {
     Arena arena;
     std::mutex mu;
     std::condition_variable cv_dispatch;  // queue, slot completion, shutdown
-    std::condition_variable cv_client;    // request completion
     std::deque<fsp_request *> queue;
     std::vector<fsp_request *> live;      // every request not yet freed
     std::vector<Slot> slots;
@@ -145,11 +151,25 @@ struct fsp_server {
 
 namespace {
 
+void finish_request(fsp_server *srv, fsp_request *r, fsp_status result, Clock::time_point now);
+
+// Runs on the CUDA callback thread once a slot's batch (bounds included) has
+// completed: retires its requests at once -- each waiting client is woken by
+// its own request's condition variable -- and frees the slot for the
+// dispatcher.  Host work only: no CUDA call is made here.
 void complete_slot_cb(void *p) {
     Slot *s = static_cast<Slot *>(p);
     fsp_server *srv = s->srv;
     std::lock_guard<std::mutex> g(srv->mu);
-    s->done = true;
+    const auto now = Clock::now();
+    fsp_status st = FSP_OK;
+    for (fsp_request *r : s->reqs) {
+        const fsp_status t = fspgb::take_device_status(r->inst);
+        if (t != FSP_OK) st = t;
+    }
+    for (fsp_request *r : s->reqs) finish_request(srv, r, st, now);
+    s->reqs.clear();
+    s->busy = false;
     srv->cv_dispatch.notify_all();
 }
 
@@ -189,6 +209,14 @@ fsp_status launch_batch(fsp_server *srv, Slot &s) {
     std::vector<fsp_pool_desc> pools;
     std::vector<fsp_request *> wide;
     for (fsp_request *r : s.reqs) {
+        if (r->in_place) {
+            fsp_pool_desc d{r->inst, r->dv_nodes, r->dv_depths, r->dv_out, r->N};
+            if (r->inst->compact)
+                pools.push_back(d);
+            else
+                wide.push_back(r);
+            continue;
+        }
         unsigned char *base = srv->arena_mem + r->off;
         const int n = r->inst->n;
         int16_t *d_nodes = reinterpret_cast<int16_t *>(base);
@@ -208,8 +236,8 @@ fsp_status launch_batch(fsp_server *srv, Slot &s) {
     std::vector<fspgb::LanesArgs> args;
     std::vector<int2> items;
     fspgb::PlanParams pp;
-    fsp_status rc = fspgb::build_plan(pools.data(), (int32_t)pools.size(), srv->cfg.warps_per_block, srv->device,
-                                      args, items, pp);
+    fsp_status rc = fspgb::build_plan(pools.data(), (int32_t)pools.size(), srv->cfg.warps_per_block, 0,
+                                      srv->device, args, items, pp);
     if (rc != FSP_OK) return rc;
     if (!grow(s, args.size(), items.size())) return FSP_ENOMEM;
     if (!args.empty()) std::memcpy(s.h_args, args.data(), sizeof(fspgb::LanesArgs) * args.size());
@@ -228,13 +256,18 @@ fsp_status launch_batch(fsp_server *srv, Slot &s) {
         const int16_t *d_nodes = reinterpret_cast<const int16_t *>(base);
         const int32_t *d_dep = reinterpret_cast<const int32_t *>(base + align_up(sizeof(int16_t) * r->N * n, 256));
         int32_t *d_out = const_cast<int32_t *>(d_dep) + align_up(sizeof(int32_t) * r->N, 256) / sizeof(int32_t);
+        if (r->in_place) {
+            d_nodes = r->dv_nodes;
+            d_dep = r->dv_depths;
+            d_out = r->dv_out;
+        }
         if (r->N > 0) {
             rc = fspgb::launch_bound(r->inst, d_nodes, d_dep, r->N, d_out, st, nullptr);
             if (rc != FSP_OK) return rc;
         }
     }
     for (fsp_request *r : s.reqs) {
-        if (r->N == 0) continue;
+        if (r->N == 0 || r->in_place) continue;
         const unsigned char *base = srv->arena_mem + r->off;
         const int32_t *d_out = reinterpret_cast<const int32_t *>(
             base + align_up(sizeof(int16_t) * r->N * r->inst->n, 256) + align_up(sizeof(int32_t) * r->N, 256));
@@ -257,7 +290,7 @@ void free_request(fsp_server *srv, fsp_request *r) {
 
 void finish_request(fsp_server *srv, fsp_request *r, fsp_status result, Clock::time_point now) {
     // server mutex held
-    if (r->state == kAdmitted) srv->arena.release(r->off, r->bytes);
+    if (r->state == kAdmitted && r->bytes) srv->arena.release(r->off, r->bytes);
     r->state = kDone;
     r->result = result;
     if (result == FSP_OK) {
@@ -268,31 +301,17 @@ void finish_request(fsp_server *srv, fsp_request *r, fsp_status result, Clock::t
         srv->any_done = true;
         srv->t_last = now;
     }
-    if (r->released) free_request(srv, r);
+    if (r->released)
+        free_request(srv, r);
+    else
+        r->cv.notify_all();
 }
 
 void dispatcher_main(fsp_server *srv) {
     cudaSetDevice(srv->device);
     std::unique_lock<std::mutex> lk(srv->mu);
     for (;;) {
-        // retire completed slots
-        const auto now = Clock::now();
-        bool retired = false;
-        for (Slot &s : srv->slots) {
-            if (s.busy && s.done) {
-                fsp_status st = FSP_OK;
-                for (fsp_request *r : s.reqs) {
-                    const fsp_status t = fspgb::take_device_status(r->inst);
-                    if (t != FSP_OK) st = t;
-                }
-                for (fsp_request *r : s.reqs) finish_request(srv, r, st, now);
-                s.reqs.clear();
-                s.busy = false;
-                s.done = false;
-                retired = true;
-            }
-        }
-        if (retired) srv->cv_client.notify_all();
+        // completed slots are retired by their completion callback
         bool in_flight = false;
         for (Slot &s : srv->slots) in_flight |= s.busy;
         if (srv->stopping && srv->queue.empty() && !in_flight) break;
@@ -308,7 +327,7 @@ void dispatcher_main(fsp_server *srv) {
             while (!srv->queue.empty() && (int)take.size() < srv->cfg.max_batch_pools) {
                 fsp_request *r = srv->queue.front();
                 size_t off = 0;
-                if (!srv->arena.alloc(r->bytes, &off)) break;  // in order: wait for memory
+                if (r->bytes && !srv->arena.alloc(r->bytes, &off)) break;  // in order: wait for memory
                 r->off = off;
                 r->state = kAdmitted;
                 srv->queue.pop_front();
@@ -317,7 +336,6 @@ void dispatcher_main(fsp_server *srv) {
             if (!take.empty()) {
                 free_slot->reqs = take;
                 free_slot->busy = true;
-                free_slot->done = false;
                 lk.unlock();
                 const fsp_status st = launch_batch(srv, *free_slot);
                 lk.lock();
@@ -332,7 +350,6 @@ void dispatcher_main(fsp_server *srv) {
                     free_slot->reqs.clear();
                     free_slot->busy = false;
                     srv->fatal = st;
-                    srv->cv_client.notify_all();
                 }
                 continue;
             }
@@ -392,10 +409,28 @@ extern "C" fsp_status fsp_server_submit(fsp_server *srv, const fsp_instance *ins
     *req = nullptr;
     if (!srv || !inst || N < 0 || (N > 0 && (!nodes || !depths || !out_lb))) return FSP_EINVAL;
     if (inst->device != srv->device) return FSP_EINVAL;
-    const size_t bytes = align_up(sizeof(int16_t) * N * inst->n, 256) + 2 * align_up(sizeof(int32_t) * N, 256) + 256;
+    // page-locked (pinned or registered) buffers are read and written in place
+    auto device_view = [](const void *h, void **d) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+            cudaGetLastError();  // not a CUDA-known pointer: clear the sticky-free error
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+        *d = a.devicePointer;
+        return true;
+    };
+    void *dvn = nullptr, *dvd = nullptr, *dvo = nullptr;
+    const bool in_place = N > 0 && device_view(nodes, &dvn) && device_view(depths, &dvd) && device_view(out_lb, &dvo);
+    const size_t bytes =
+        in_place ? 0 : align_up(sizeof(int16_t) * N * inst->n, 256) + 2 * align_up(sizeof(int32_t) * N, 256) + 256;
     if (bytes > srv->arena_size) return FSP_EBUSY;  // can never be admitted
     fsp_request *r = new (std::nothrow) fsp_request();
     if (!r) return FSP_ENOMEM;
+    r->in_place = in_place;
+    r->dv_nodes = static_cast<const int16_t *>(dvn);
+    r->dv_depths = static_cast<const int32_t *>(dvd);
+    r->dv_out = static_cast<int32_t *>(dvo);
     r->srv = srv;
     r->inst = inst;
     r->nodes = nodes;
@@ -428,8 +463,8 @@ extern "C" fsp_status fsp_request_wait(fsp_request *r, int64_t timeout_us) {
     std::unique_lock<std::mutex> lk(srv->mu);
     auto ready = [&] { return r->state == kDone || r->state == kCancelled; };
     if (timeout_us < 0) {
-        srv->cv_client.wait(lk, ready);
-    } else if (!srv->cv_client.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+        r->cv.wait(lk, ready);
+    } else if (!r->cv.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
         return FSP_ETIMEDOUT;
     }
     return r->state == kCancelled ? FSP_EBUSY : r->result;
@@ -443,7 +478,7 @@ extern "C" fsp_status fsp_request_cancel(fsp_request *r) {
     auto it = std::find(srv->queue.begin(), srv->queue.end(), r);
     if (it != srv->queue.end()) srv->queue.erase(it);
     r->state = kCancelled;
-    srv->cv_client.notify_all();
+    r->cv.notify_all();
     return FSP_OK;
 }
 
@@ -535,47 +570,100 @@ struct SNode {
 
 }  // namespace
 
-extern "C" fsp_status fsp_server_search(fsp_server *srv, const fsp_instance *inst, int32_t ub0, int32_t expand,
-                                        int64_t node_limit, int16_t *best_perm, int32_t *best_makespan,
-                                        int64_t *nodes_bounded) {
-    if (!srv || !inst || expand < 1 || node_limit < 0) return FSP_EINVAL;
-    const int n = inst->n;
-    const size_t cap = (size_t)expand * n;  // children of `expand` parents
+namespace {
+
+// Open nodes of one depth-first search, stored flat: node i has bound lb[i],
+// depth d[i] and its prefix in rows[i * n, i * n + d[i]).  No allocation per
+// node; the arrays grow geometrically.
+struct FlatStack {
+    int n = 0;
+    std::vector<int32_t> lb, d;
+    std::vector<int16_t> rows;
+    size_t size() const { return lb.size(); }
+    bool empty() const { return lb.empty(); }
+    void push(int32_t l, int32_t dd, const int16_t *prefix) {
+        lb.push_back(l);
+        d.push_back(dd);
+        rows.insert(rows.end(), prefix, prefix + n);
+    }
+    void pop() {
+        lb.pop_back();
+        d.pop_back();
+        rows.resize(rows.size() - (size_t)n);
+    }
+    const int16_t *row(size_t i) const { return rows.data() + i * (size_t)n; }
+};
+
+// One depth-first search whose pools are bounded by the server, or, with no
+// server, each by its own plain launch (fsp_bound_pool_host on a private
+// stream): the same search, the same pools, so the two can be compared on
+// identical work.
+struct SearchState {
+    fsp_server *srv = nullptr;
+    const fsp_instance *inst = nullptr;
+    cudaStream_t stream = nullptr;  // plain mode only
     int16_t *h_rows = nullptr;
     int32_t *h_dep = nullptr, *h_out = nullptr;
-    if (cudaMallocHost((void **)&h_rows, sizeof(int16_t) * cap * n) != cudaSuccess ||
-        cudaMallocHost((void **)&h_dep, sizeof(int32_t) * cap) != cudaSuccess ||
-        cudaMallocHost((void **)&h_out, sizeof(int32_t) * cap) != cudaSuccess) {
+
+    ~SearchState() {
         if (h_rows) cudaFreeHost(h_rows);
         if (h_dep) cudaFreeHost(h_dep);
-        return FSP_ENOMEM;
+        if (h_out) cudaFreeHost(h_out);
+        if (stream) cudaStreamDestroy(stream);
     }
-    auto bound = [&](int64_t cnt) -> fsp_status {
-        fsp_request *req = nullptr;
-        fsp_status st = fsp_server_submit(srv, inst, h_rows, h_dep, cnt, h_out, &req);
-        if (st != FSP_OK) return st;
-        st = fsp_request_wait(req, 600000000LL);  // ten minutes: a stuck server ends the search
-        if (st == FSP_ETIMEDOUT) fsp_request_cancel(req);
-        fsp_request_release(req);
+    fsp_status init(size_t cap, int n) {
+        if (!srv && cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) return FSP_ECUDA;
+        if (cudaMallocHost((void **)&h_rows, sizeof(int16_t) * cap * n) != cudaSuccess ||
+            cudaMallocHost((void **)&h_dep, sizeof(int32_t) * cap) != cudaSuccess ||
+            cudaMallocHost((void **)&h_out, sizeof(int32_t) * cap) != cudaSuccess)
+            return FSP_ENOMEM;
+        return FSP_OK;
+    }
+    fsp_status bound(int64_t cnt) {
+        fsp_status st;
+        if (srv) {
+            fsp_request *req = nullptr;
+            st = fsp_server_submit(srv, inst, h_rows, h_dep, cnt, h_out, &req);
+            if (st != FSP_OK) return st;
+            st = fsp_request_wait(req, 600000000LL);  // ten minutes: a stuck server ends the search
+            if (st == FSP_ETIMEDOUT) fsp_request_cancel(req);
+            fsp_request_release(req);
+        } else {
+            st = fsp_bound_pool_host(inst, h_rows, h_dep, cnt, h_out, stream);
+        }
         if (st != FSP_OK) return st;
         for (int64_t i = 0; i < cnt; ++i)
             if (h_out[i] == FSP_LB_INVALID) return FSP_EBADNODE;
         return FSP_OK;
-    };
+    }
+};
+
+}  // namespace
+
+extern "C" fsp_status fsp_server_search(fsp_server *srv, const fsp_instance *inst, int32_t ub0, int32_t expand,
+                                        int64_t node_limit, int16_t *best_perm, int32_t *best_makespan,
+                                        int64_t *nodes_bounded) {
+    if (!inst || expand < 1 || node_limit < 0) return FSP_EINVAL;
+    const int n = inst->n;
+    const size_t cap = std::max<size_t>((size_t)expand * n, 1);  // children of `expand` parents
+    SearchState S;
+    S.srv = srv;
+    S.inst = inst;
+    fsp_status st = S.init(cap, n);
+    if (st != FSP_OK) return st;
     int64_t UB = (int64_t)ub0 + 1, count = 0;
     bool found = false;
-    std::vector<int16_t> best(n, 0);
-    std::vector<SNode> stack;
-    fsp_status st;
+    std::vector<int16_t> best(n, 0), zero(n, 0);
+    FlatStack stack, parents;
+    stack.n = parents.n = n;
     // the root
-    std::memset(h_rows, 0, sizeof(int16_t) * n);
-    h_dep[0] = 0;
-    st = bound(1);
+    std::memset(S.h_rows, 0, sizeof(int16_t) * n);
+    S.h_dep[0] = 0;
+    st = S.bound(1);
     if (st == FSP_OK) {
         ++count;
-        if (h_out[0] < UB) stack.push_back(SNode{h_out[0], 0, std::vector<int16_t>(n, 0)});
+        if (S.h_out[0] < UB) stack.push(S.h_out[0], 0, zero.data());
     }
-    std::vector<SNode> parents;
     std::vector<int> first(expand + 1);
     std::vector<char> used(n);
     struct Kid {
@@ -589,61 +677,59 @@ extern "C" fsp_status fsp_server_search(fsp_server *srv, const fsp_instance *ins
             break;
         }
         // selection: the top `expand` live nodes of the stack
-        parents.clear();
+        parents.lb.clear();
+        parents.d.clear();
+        parents.rows.clear();
         while (!stack.empty() && (int)parents.size() < expand) {
-            SNode nd = std::move(stack.back());
-            stack.pop_back();
-            if (nd.lb < UB) parents.push_back(std::move(nd));
+            const size_t t = stack.size() - 1;
+            if (stack.lb[t] < UB) parents.push(stack.lb[t], stack.d[t], stack.row(t));
+            stack.pop();
         }
         if (parents.empty()) break;
         // branching: all children of all selected parents form one pool
         int64_t cnt = 0;
         for (size_t p = 0; p < parents.size(); ++p) {
             first[p] = (int)cnt;
-            const SNode &nd = parents[p];
+            const int d = parents.d[p];
+            const int16_t *prow = parents.row(p);
             std::fill(used.begin(), used.end(), 0);
-            for (int i = 0; i < nd.d; ++i) used[nd.row[i]] = 1;
+            for (int i = 0; i < d; ++i) used[prow[i]] = 1;
             for (int j = 0; j < n; ++j) {
                 if (used[j]) continue;
-                int16_t *r = h_rows + (size_t)cnt * n;
-                std::memcpy(r, nd.row.data(), sizeof(int16_t) * nd.d);
-                std::memset(r + nd.d, 0, sizeof(int16_t) * (n - nd.d));
-                r[nd.d] = (int16_t)j;
-                h_dep[cnt] = nd.d + 1;
+                int16_t *r = S.h_rows + (size_t)cnt * n;
+                std::memcpy(r, prow, sizeof(int16_t) * n);
+                r[d] = (int16_t)j;
+                S.h_dep[cnt] = d + 1;
                 ++cnt;
             }
         }
         first[parents.size()] = (int)cnt;
-        st = bound(cnt);
+        st = S.bound(cnt);
         if (st != FSP_OK) break;
         count += cnt;
         // leaves first: a bounded complete schedule is an incumbent at once
         for (int64_t i = 0; i < cnt; ++i)
-            if (h_dep[i] == n && h_out[i] < UB) {
-                UB = h_out[i];
+            if (S.h_dep[i] == n && S.h_out[i] < UB) {
+                UB = S.h_out[i];
                 found = true;
-                std::memcpy(best.data(), h_rows + (size_t)i * n, sizeof(int16_t) * n);
+                std::memcpy(best.data(), S.h_rows + (size_t)i * n, sizeof(int16_t) * n);
             }
         // elimination and depth-first order: the first selected parent's
         // children end on top, each parent's children by (LB, job)
         for (int p = (int)parents.size() - 1; p >= 0; --p) {
-            const SNode &nd = parents[p];
-            if (nd.d + 1 == n) continue;
+            const int d = parents.d[p];
+            if (d + 1 == n) continue;
             kids.clear();
             for (int i = first[p]; i < first[p + 1]; ++i)
-                if (h_out[i] < UB) kids.push_back(Kid{h_out[i], h_rows[(size_t)i * n + nd.d]});
-            std::sort(kids.begin(), kids.end(),
-                      [](const Kid &x, const Kid &y) { return x.lb != y.lb ? x.lb < y.lb : x.job < y.job; });
-            for (int t = (int)kids.size() - 1; t >= 0; --t) {
-                SNode c{kids[t].lb, nd.d + 1, nd.row};
-                c.row[nd.d] = (int16_t)kids[t].job;
-                stack.push_back(std::move(c));
-            }
+                if (S.h_out[i] < UB) kids.push_back(Kid{S.h_out[i], i});
+            std::sort(kids.begin(), kids.end(), [&](const Kid &x, const Kid &y) {
+                const int jx = S.h_rows[(size_t)x.job * n + d], jy = S.h_rows[(size_t)y.job * n + d];
+                return x.lb != y.lb ? x.lb < y.lb : jx < jy;
+            });
+            for (int t = (int)kids.size() - 1; t >= 0; --t)
+                stack.push(kids[t].lb, d + 1, S.h_rows + (size_t)kids[t].job * n);
         }
     }
-    cudaFreeHost(h_rows);
-    cudaFreeHost(h_dep);
-    cudaFreeHost(h_out);
     if (st != FSP_OK) return st;
     if (nodes_bounded) *nodes_bounded = count;
     if (found) {

@@ -121,6 +121,10 @@ def load():
                               ctypes.POINTER(ctypes.c_float)], i32),
             "fsp_tuned_config": ([vp, i64, ctypes.POINTER(fsp_launch_config)], i32),
             "fsp_batch_create": ([ctypes.POINTER(fsp_pool_desc), i32, i32, ctypes.POINTER(vp)], i32),
+            "fsp_batch_create_ex": ([ctypes.POINTER(fsp_pool_desc), i32, i32, i32, ctypes.POINTER(vp)], i32),
+            "fsp_batch_query_ex": ([vp, i64p, i64p, i32p, i32p, i32p], i32),
+            "fsp_batch_autotune_ex": ([ctypes.POINTER(fsp_pool_desc), i32, vp, i32p, i32p,
+                                       ctypes.POINTER(ctypes.c_float)], i32),
             "fsp_batch_launch": ([vp, vp], i32),
             "fsp_batch_launch_graph": ([vp, vp], i32),
             "fsp_batch_query": ([vp, i64p, i64p, i32p, i32p], i32),
@@ -140,6 +144,7 @@ def load():
             "fsp_server_search": ([vp, vp, i32, i32, i64, i16p, i32p, i64p], i32),
             "fsp_server_solve": ([vp, vp, i32, i32, i32, i64, i16p, i32p, i64p, i64p], i32),
             "fsp_neh": ([vp, i16p, i32p], i32),
+            "fsp_iterated_greedy": ([vp, i32, ctypes.c_uint64, i16p, i32p], i32),
             "fsp_status_string": ([i32], ctypes.c_char_p),
             "fsp_version": ([], ctypes.c_char_p),
             "fsp_kernel_launches": ([], i64),
@@ -361,7 +366,7 @@ class Batch:
     """Owns one fsp_batch plan over pools given as (instance, nodes, depths,
     out) with torch CUDA tensors; keeps them alive while the plan exists."""
 
-    def __init__(self, pools, warps_per_block: int = 0):
+    def __init__(self, pools, warps_per_block: int = 0, couples_per_item: int = 0):
         lib = load()
         self._keep = list(pools)
         descs = (fsp_pool_desc * max(1, len(pools)))()
@@ -369,7 +374,8 @@ class Batch:
             N = _check_pool(inst, nodes, depths, out)
             descs[i] = fsp_pool_desc(inst.handle.value, nodes.data_ptr(), depths.data_ptr(), out.data_ptr(), N)
         h = ctypes.c_void_p()
-        _check(lib.fsp_batch_create(descs, len(pools), int(warps_per_block), ctypes.byref(h)), "fsp_batch_create")
+        _check(lib.fsp_batch_create_ex(descs, len(pools), int(warps_per_block), int(couples_per_item),
+                                       ctypes.byref(h)), "fsp_batch_create_ex")
         self._h = h
 
     def launch(self, stream=None):
@@ -380,10 +386,11 @@ class Batch:
 
     def query(self) -> dict:
         items, nodes = ctypes.c_int64(), ctypes.c_int64()
-        warps, blocks = ctypes.c_int32(), ctypes.c_int32()
-        _check(load().fsp_batch_query(self._h, ctypes.byref(items), ctypes.byref(nodes), ctypes.byref(warps),
-                                      ctypes.byref(blocks)), "fsp_batch_query")
-        return dict(work_items=items.value, nodes=nodes.value, warps_per_block=warps.value, blocks=blocks.value)
+        warps, blocks, cpi = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().fsp_batch_query_ex(self._h, ctypes.byref(items), ctypes.byref(nodes), ctypes.byref(warps),
+                                         ctypes.byref(blocks), ctypes.byref(cpi)), "fsp_batch_query_ex")
+        return dict(work_items=items.value, nodes=nodes.value, warps_per_block=warps.value, blocks=blocks.value,
+                    couples_per_item=cpi.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -403,8 +410,8 @@ class Batch:
         self.close()
 
 
-def fsp_batch_create(pools, warps_per_block: int = 0) -> Batch:
-    return Batch(pools, warps_per_block)
+def fsp_batch_create(pools, warps_per_block: int = 0, couples_per_item: int = 0) -> Batch:
+    return Batch(pools, warps_per_block, couples_per_item)
 
 
 def fsp_batch_autotune(pools, stream=None):
@@ -419,6 +426,20 @@ def fsp_batch_autotune(pools, stream=None):
     _check(lib.fsp_batch_autotune(descs, len(pools), _stream_handle(stream), ctypes.byref(w), ctypes.byref(ms)),
            "fsp_batch_autotune")
     return int(w.value), float(ms.value)
+
+
+def fsp_batch_autotune_ex(pools, stream=None):
+    """Fastest (warps_per_block, couples_per_item) for a batch of (instance,
+    nodes, depths, out) pools; returns (warps, couples per item, ms)."""
+    lib = load()
+    descs = (fsp_pool_desc * max(1, len(pools)))()
+    for i, (inst, nodes, depths, out) in enumerate(pools):
+        N = _check_pool(inst, nodes, depths, out)
+        descs[i] = fsp_pool_desc(inst.handle.value, nodes.data_ptr(), depths.data_ptr(), out.data_ptr(), N)
+    w, c, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(lib.fsp_batch_autotune_ex(descs, len(pools), _stream_handle(stream), ctypes.byref(w), ctypes.byref(c),
+                                     ctypes.byref(ms)), "fsp_batch_autotune_ex")
+    return int(w.value), int(c.value), float(ms.value)
 
 
 FSP_NOALLOC_MAX_POOLS = 64
@@ -559,4 +580,29 @@ def fsp_neh(inst: Instance):
     mk = ctypes.c_int32(0)
     _check(load().fsp_neh(inst.handle, perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), ctypes.byref(mk)),
            "fsp_neh")
+    return int(mk.value), perm
+
+
+def fsp_search_plain(inst: Instance, ub0: int, expand: int = 64, node_limit: int = 0):
+    """fsp_server_search with no server: the same depth-first search, each
+    pool bounded by its own plain launch (fsp_bound_pool_host).  Returns
+    (status, best_makespan, best_perm, nodes_bounded)."""
+    perm = np.zeros(inst.n, np.int16)
+    best = ctypes.c_int32(0)
+    nodes = ctypes.c_int64(0)
+    st = load().fsp_server_search(None, inst.handle, int(ub0), int(expand), int(node_limit),
+                                  perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), ctypes.byref(best),
+                                  ctypes.byref(nodes))
+    if st not in (FSP_OK, FSP_ENOTFOUND, FSP_ETIMEDOUT):
+        raise FspError(st, "fsp_server_search")
+    return st, int(best.value), perm, int(nodes.value)
+
+
+def fsp_iterated_greedy(inst: Instance, iterations: int = 2000, seed: int = 0):
+    """Iterated greedy heuristic schedule: (makespan, perm)."""
+    perm = np.zeros(inst.n, np.int16)
+    mk = ctypes.c_int32(0)
+    _check(load().fsp_iterated_greedy(inst.handle, int(iterations), int(seed),
+                                      perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), ctypes.byref(mk)),
+           "fsp_iterated_greedy")
     return int(mk.value), perm

@@ -4,22 +4,27 @@ found by the CPU oracle's branch-and-bound.  Calls only oracle/ (plus the
 seeded input generator).
 
 Method per seed:
-  - ub0 = the best of the oracle's NEH schedule and three seeded runs of its
-    iterated greedy heuristic (each value is the makespan of a real
-    schedule, so ub0 >= the optimum and the search cannot miss it);
+  - the incumbent starts as the best of the oracle's NEH schedule and three
+    seeded runs of its iterated greedy heuristic (real schedules, so the
+    incumbent's makespan is never below the optimum);
   - the tree is cut at depth 2: one oracle search per ordered pair of first
-    jobs (n (n - 1) subtrees), every node bounded with the per-job release
-    times, each asked for a schedule of makespan <= ub0 - 1 (the schedule
-    behind ub0 is the incumbent, so nodes whose bound reaches ub0 are cut
-    at once); the subtrees of all depth-2 prefixes cover every schedule, so
-    the smallest subtree optimum is the instance's optimum, and when no
-    subtree finds one the optimum is ub0 itself;
-  - the subtree searches of all seeds share one process pool, so a hard seed
-    uses every core.
-A seed whose searches do not all finish within the time limit keeps its
-earlier entry (or null: unverified).
+    jobs (n (n - 1) subtrees, taken in increasing order of their root bound),
+    every node bounded with the per-job release times;
+  - each subtree search is started with the incumbent known at that moment,
+    U, and asked for a schedule of makespan <= U - 1 (nodes whose bound
+    reaches U are cut at once); a schedule it finds becomes the incumbent
+    for the subtrees started later;
+  - the subtrees of all depth-2 prefixes cover every schedule, so when all
+    are done the incumbent is optimal: a better schedule would lie in some
+    subtree, whose search was started with an incumbent above it and so
+    would have returned it.
+The subtree searches of all seeds share one process pool (seeds in the order
+given), so a hard seed uses every core.  A seed whose searches do not all
+finish within the time limit keeps its earlier entry (or null: unverified).
+With --checkpoint FILE, finished subtrees are recorded there and a restart
+skips them.
 
-    python tests/golden/make_serving_optima.py [seconds] [workers] [seed ...]
+    python tests/golden/make_serving_optima.py [--checkpoint FILE] [seconds] [workers] [seed ...]
 """
 import json
 import multiprocessing as mp
@@ -42,28 +47,32 @@ def upper_bound(args):
 
 
 def subtree(args):
-    seed, p, ub0, prefix = args
+    seed, p, ub, prefix = args
     import oracle
     t0 = time.time()
-    rc, best, perm, nodes = oracle.branch_and_bound(p, ub0 - 1, oracle.RELEASE_EST, prefix)
-    return seed, rc == oracle.FO_OK, best, perm.tolist(), nodes, time.time() - t0
+    rc, best, perm, nodes = oracle.branch_and_bound(p, ub - 1, oracle.RELEASE_EST, prefix)
+    return seed, prefix, ub, rc == oracle.FO_OK, best, perm.tolist(), nodes, time.time() - t0
 
 
 def main():
-    limit = float(sys.argv[1]) if len(sys.argv) > 1 else 3600.0
-    workers = int(sys.argv[2]) if len(sys.argv) > 2 else os.cpu_count() or 1
-    only = {int(s) for s in sys.argv[3:]}
+    argv = sys.argv[1:]
+    ckpt_path = None
+    if argv[:1] == ["--checkpoint"]:
+        ckpt_path, argv = argv[1], argv[2:]
+    limit = float(argv[0]) if len(argv) > 0 else 3600.0
+    workers = int(argv[1]) if len(argv) > 1 else os.cpu_count() or 1
+    order = [int(s) for s in argv[2:]]
     from paper_1208_3933_gb300 import workloads
     import oracle
     from oracle.neh import neh
     from oracle.brute import makespan
     oracle.build()
-    jobs = [(s, p) for s, p in workloads.serving_searches() if not only or s in only]
-    results = {}
-    if os.path.exists(OUT):
-        results = json.load(open(OUT))["results"]
-    for s, p in workloads.serving_searches():
+    probs = dict(workloads.serving_searches())
+    order = order or sorted(probs)
+    results = json.load(open(OUT))["results"] if os.path.exists(OUT) else {}
+    for s, p in probs.items():
         results.setdefault(str(s), {"m": int(p.shape[1]), "opt": None})
+    ckpt = json.load(open(ckpt_path)) if ckpt_path and os.path.exists(ckpt_path) else {}
 
     def save():
         json.dump({"what": "optima of the serving-loop searches from the CPU oracle's branch-and-bound",
@@ -72,47 +81,78 @@ def main():
     t_end = time.time() + limit
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
-        ub = {}
-        for s, p in jobs:
-            v, seq = neh(p)
-            ub[s] = (v, "neh", list(seq))
-        for seed, v, seq in pool.imap_unordered(
-                upper_bound, [(s, p, r) for s, p in jobs for r in range(IG_RUNS)]):
-            p = dict(jobs)[seed]
-            assert v == makespan(p, seq) and sorted(seq) == list(range(p.shape[0]))
-            if v < ub[seed][0]:
-                ub[seed] = (v, "iterated greedy", list(seq))
-        tasks = []
-        for s, p in jobs:
-            n = p.shape[0]
-            tasks += [(s, p, ub[s][0], (a, b)) for a in range(n) for b in range(n) if a != b]
-        left = {s: 0 for s, _ in jobs}
-        for t in tasks:
-            left[t[0]] += 1
-        acc = {s: {"best": None, "perm": None, "nodes": 0, "seconds": 0.0} for s, _ in jobs}
-        it = pool.imap_unordered(subtree, tasks)
-        while any(left.values()):
-            try:
-                seed, ok, best, perm, nodes, secs = it.next(timeout=max(1.0, t_end - time.time()))
-            except mp.TimeoutError:
+        inc = {}  # seed -> (makespan, sequence, where from)
+        for s in order:
+            v, seq = neh(probs[s])
+            inc[s] = (v, list(seq), "neh")
+        for seed, v, seq in pool.imap_unordered(upper_bound,
+                                                [(s, probs[s], r) for s in order for r in range(IG_RUNS)]):
+            assert v == makespan(probs[seed], seq) and sorted(seq) == list(range(probs[seed].shape[0]))
+            if v < inc[seed][0]:
+                inc[seed] = (v, list(seq), "iterated greedy")
+        start = {s: inc[s] for s in order}
+        acc = {s: {"nodes": 0, "seconds": 0.0, "left": 0} for s in order}
+        queue = []
+        for s in order:
+            p, n = probs[s], probs[s].shape[0]
+            t = oracle.Tables(p)
+            prefixes = [(a, b) for a in range(n) for b in range(n) if a != b]
+            done = ckpt.get(str(s), {})
+            for pre in prefixes:
+                rec = done.get(f"{pre[0]},{pre[1]}")
+                if rec:  # restart: a subtree finished earlier
+                    acc[s]["nodes"] += rec["nodes"]
+                    acc[s]["seconds"] += rec["seconds"]
+                    if rec["best"] is not None and rec["best"] < inc[s][0]:
+                        inc[s] = (rec["best"], rec["perm"], "subtree search")
+            todo = [pre for pre in prefixes if f"{pre[0]},{pre[1]}" not in done]
+            todo.sort(key=lambda pre: (t.lb(list(pre), release=oracle.RELEASE_EST), pre))
+            acc[s]["left"] = len(todo)
+            queue += [(s, pre) for pre in todo]
+
+        def finish(s):
+            p = probs[s]
+            best, perm, how = inc[s]
+            assert best == makespan(p, perm) and sorted(perm) == list(range(p.shape[0]))
+            results[str(s)] = {"m": int(p.shape[1]), "neh": neh(p)[0], "start": start[s][0],
+                               "start_from": start[s][2], "opt": best, "perm": list(map(int, perm)),
+                               "oracle_nodes": acc[s]["nodes"], "cpu_seconds": round(acc[s]["seconds"], 1),
+                               "method": "depth-2 subtrees, per-job release times, shared incumbent"}
+            save()
+            print(s, best, acc[s]["nodes"], round(acc[s]["seconds"]), flush=True)
+
+        for s in order:
+            if acc[s]["left"] == 0:
+                finish(s)
+        pending = []
+        qi = 0
+        while pending or qi < len(queue):
+            while qi < len(queue) and len(pending) < workers:
+                s, pre = queue[qi]
+                qi += 1
+                pending.append(pool.apply_async(subtree, ((s, probs[s], inc[s][0], pre),)))
+            if time.time() > t_end:
                 break
-            a = acc[seed]
-            a["nodes"] += nodes
-            a["seconds"] += secs
-            if ok and (a["best"] is None or best < a["best"]):
-                a["best"], a["perm"] = best, perm
-            left[seed] -= 1
-            if left[seed] == 0:
-                p = dict(jobs)[seed]
-                if a["best"] is None:  # no schedule below ub0: the ub0 schedule is optimal
-                    a["best"], a["perm"] = ub[seed][0], ub[seed][2]
-                assert a["best"] == makespan(p, a["perm"]) and a["best"] <= ub[seed][0]
-                results[str(seed)] = {"m": int(p.shape[1]), "ub0": ub[seed][0], "ub0_from": ub[seed][1],
-                                      "opt": a["best"], "perm": a["perm"], "oracle_nodes": a["nodes"],
-                                      "cpu_seconds": round(a["seconds"], 1),
-                                      "method": "depth-2 subtrees, per-job release times"}
-                save()
-                print(seed, results[str(seed)]["opt"], a["nodes"], round(a["seconds"]), flush=True)
+            ready = [f for f in pending if f.ready()]
+            if not ready:
+                time.sleep(0.05)
+                continue
+            for f in ready:
+                pending.remove(f)
+                seed, pre, ub, ok, best, perm, nodes, secs = f.get()
+                a = acc[seed]
+                a["nodes"] += nodes
+                a["seconds"] += secs
+                a["left"] -= 1
+                if ok and best < inc[seed][0]:
+                    inc[seed] = (best, perm, "subtree search")
+                if ckpt_path:
+                    ckpt.setdefault(str(seed), {})[f"{pre[0]},{pre[1]}"] = {
+                        "ub": ub, "best": best if ok else None, "perm": perm if ok else None,
+                        "nodes": nodes, "seconds": round(secs, 2)}
+                    json.dump(ckpt, open(ckpt_path, "w"))
+                if a["left"] == 0:
+                    finish(seed)
         pool.terminate()
     save()
 

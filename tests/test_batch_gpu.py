@@ -144,3 +144,68 @@ def test_batch_autotune_and_every_node_tile_agree(gpu_lib):
             assert np.array_equal(o.cpu().numpy(), want), W
     for inst in insts:
         inst.close()
+
+
+@pytest.mark.parametrize("cpi", [1, 32, 64, 96, 190])
+def test_couple_sliced_batches_match_oracle(gpu_lib, cpi):
+    """Plans split by couples (32 to 190 couples per work item, rounded up to
+    whole groups of 32): pools of more groups are cut into slices that meet
+    in an atomic max on zeroed bounds; pools of one group stay whole.  Mixed
+    instances (m = 5, 12, 20, 27), invalid rows (every slice must agree on
+    them), ragged and empty pools, per-job release times; plain and graph
+    launches, the graph replayed twice; all equal to the oracle."""
+    import torch
+    fsp = gpu_lib
+    rng = np.random.default_rng(700 + cpi)
+    specs = [(40, 20, 700, 0), (33, 27, 333, 0), (23, 5, 90, 0), (70, 12, 257, 0), (20, 20, 0, 0),
+             (50, 20, 401, fsp.FSP_INSTANCE_RELEASE_PER_JOB)]
+    insts, pools, wants = [], [], []
+    for n, m, N, flags in specs:
+        p = rng.integers(1, 100, (n, m), dtype=np.int32)
+        rows, depths = workloads.random_pool(rng, n, N, max_depth=n + 1)
+        if N > 60:
+            depths[[3, 50]] = [-1, n + 1]
+            rows[7, :2] = [5, 5]
+            depths[7] = max(int(depths[7]), 2)
+        inst = fsp.Instance(p, flags=flags)
+        insts.append(inst)
+        pools.append((inst, dev(rows.reshape(N, n)), dev(depths), torch.full((N,), -7, dtype=torch.int32,
+                                                                               device="cuda")))
+        rel = oracle.RELEASE_EST if flags else oracle.RELEASE_HEADS
+        wants.append(oracle.Tables(p).lb_pool(rows.reshape(N, n), depths, threads=16, release=rel))
+    with fsp.Batch(pools, warps_per_block=4, couples_per_item=cpi) as b:
+        assert b.query()["couples_per_item"] == cpi
+        b.launch()
+        torch.cuda.synchronize()
+        for (_, _, _, o), want in zip(pools, wants):
+            assert np.array_equal(o.cpu().numpy(), want), cpi
+            o.fill_(-7)
+        b.launch_graph()
+        b.launch_graph()
+        torch.cuda.synchronize()
+        for (_, _, _, o), want in zip(pools, wants):
+            assert np.array_equal(o.cpu().numpy(), want), cpi
+    for inst in insts:
+        inst.close()
+
+
+def test_batch_autotune_ex_picks_tile_and_couple_split(gpu_lib):
+    """fsp_batch_autotune_ex returns one of the timed (warps, couples per
+    item) pairs, and the plan it picks writes the oracle's bounds."""
+    import torch
+    fsp = gpu_lib
+    ws = small_batch(range(130, 136), 600)
+    insts = [fsp.Instance(w.p) for w in ws]
+    outs = [torch.empty(w.N, dtype=torch.int32, device="cuda") for w in ws]
+    pools = [(inst, dev(w.rows), dev(w.depths), o) for inst, w, o in zip(insts, ws, outs)]
+    W, cpi, ms = fsp.fsp_batch_autotune_ex(pools)
+    assert W in (16, 12, 8, 6, 4, 2) and cpi in (0, 32, 64, 96, 128) and ms > 0
+    for o in outs:
+        o.fill_(-7)
+    with fsp.Batch(pools, warps_per_block=W, couples_per_item=cpi) as b:
+        b.launch_graph()
+        torch.cuda.synchronize()
+    for w, o in zip(ws, outs):
+        assert np.array_equal(o.cpu().numpy(), oracle.Tables(w.p).lb_pool(w.rows, w.depths, threads=16))
+    for inst in insts:
+        inst.close()

@@ -60,3 +60,33 @@ def test_twelve_job_search(gpu_lib):
     ost, obest, _, onodes = oracle.branch_and_bound(p, ub0)
     assert st == ost == fsp.FSP_OK and best == obest and nodes == onodes
     assert brute.makespan(p, perm.tolist()) == best
+
+
+def test_iterated_greedy_upper_bound(gpu_lib):
+    """The library's iterated greedy schedule is a permutation whose makespan
+    (by the textbook recurrence) is the value returned, never above NEH's and
+    never below the optimum: the brute-force optimum on 8-job instances, the
+    oracle's stored optima on the 20-job serving searches."""
+    import json
+    import os
+    fsp = gpu_lib
+    rng = np.random.default_rng(77)
+    for t in range(6):
+        n, m = 8, int(rng.integers(2, 7))
+        p = rng.integers(1, 100, (n, m), dtype=np.int32)
+        opt, _ = brute.optimum(p)
+        with fsp.Instance(p) as inst:
+            neh_v, _ = fsp.fsp_neh(inst)
+            v, perm = fsp.fsp_iterated_greedy(inst, iterations=200, seed=t)
+            assert sorted(perm.tolist()) == list(range(n))
+            assert v == brute.makespan(p, perm.tolist())
+            assert opt <= v <= neh_v
+            assert fsp.fsp_iterated_greedy(inst, iterations=200, seed=t)[0] == v  # deterministic
+            assert fsp.fsp_iterated_greedy(inst, iterations=0, seed=t)[0] == neh_v
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "serving_optima.json")))["results"]
+    probs = dict(workloads.serving_searches())
+    for seed in (202, 209, 216, 218):
+        with fsp.Instance(probs[seed]) as inst:
+            v, perm = fsp.fsp_iterated_greedy(inst, iterations=1000, seed=1)
+        assert v == brute.makespan(probs[seed], perm.tolist())
+        assert golden[str(seed)]["opt"] is None or v >= golden[str(seed)]["opt"]

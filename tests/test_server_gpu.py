@@ -208,3 +208,63 @@ def test_server_with_per_job_release_instances(gpu_lib):
             req.release()
     for inst, _, _, _ in insts:
         inst.close()
+
+
+def test_page_locked_pools_are_bounded_in_place(gpu_lib):
+    """Requests whose rows, depths and bounds all live in page-locked host
+    memory are bounded in place (no copy, no arena space) and batched with
+    staged requests of pageable memory; every result equals the oracle's.
+    A server whose arena holds none of the page-locked pools still serves
+    them."""
+    import torch
+    fsp = gpu_lib
+    specs = [(20, 10, 900), (200, 20, 1200), (20, 5, 40), (60, 20, 700), (7, 3, 1)]
+    pools = make_pools(fsp, specs, 9)
+    pinned = []
+    for inst, rows, depths in pools:
+        r = torch.from_numpy(rows).pin_memory().numpy()
+        d = torch.from_numpy(depths).pin_memory().numpy()
+        o = torch.full((depths.shape[0],), -5, dtype=torch.int32).pin_memory().numpy()
+        pinned.append((inst, r, d, o))
+    want = [oracle.Tables(inst.p).lb_pool(rows, depths, threads=16) for inst, rows, depths in pools]
+    with fsp.Server(hbm_budget_bytes=64 << 10, slots=2) as srv:
+        for rep in range(3):
+            reqs = [srv.submit(inst, r, d, out=o) for inst, r, d, o in pinned]
+            small = [srv.submit(inst, rows[:5], depths[:5]) for inst, rows, depths in pools]
+            for q, (_, _, _, o), w in zip(reqs, pinned, want):
+                assert q.wait(60_000_000) == fsp.FSP_OK
+                assert np.array_equal(o, w)
+                q.release()
+            for q, w in zip(small, want):
+                assert q.wait(60_000_000) == fsp.FSP_OK
+                assert np.array_equal(q.out, w[:5])
+                q.release()
+            for _, _, _, o in pinned:
+                o.fill(-5)
+        assert srv.stats()["arena_bytes_used"] == 0
+    for inst, _, _ in pools:
+        inst.close()
+
+
+@pytest.mark.parametrize("seed,m", [(200, 5), (203, 5), (210, 5)])
+def test_plain_search_is_the_served_search(gpu_lib, seed, m):
+    """fsp_server_search without a server bounds every pool by its own plain
+    launch: the same search, so the same optimum, node count and schedule
+    as through the server, and the optimum the oracle stored."""
+    import json
+    import os
+    fsp = gpu_lib
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "serving_optima.json")))["results"]
+    p = dict(workloads.serving_searches())[seed]
+    assert p.shape[1] == m
+    from oracle import brute
+    with fsp.Instance(p) as inst, fsp.Server() as srv:
+        ub0, _ = fsp.fsp_iterated_greedy(inst, iterations=500, seed=3)
+        served = srv.search(inst, ub0, expand=64)
+        plain = fsp.fsp_search_plain(inst, ub0, expand=64)
+    assert served[0] == plain[0] and served[1] == plain[1] and served[3] == plain[3]
+    assert np.array_equal(served[2], plain[2])
+    opt = served[1] if served[0] == fsp.FSP_OK else ub0  # not found below ub0: ub0 is optimal
+    assert opt == golden[str(seed)]["opt"]
+    if served[0] == fsp.FSP_OK:
+        assert brute.makespan(p, served[2].tolist()) == opt
