@@ -247,8 +247,10 @@ def run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, P: int, dep_h, n_j
     for N in (4096, 8192, 16384, 32768, 65536, 131072):
         shape = fsp.fsp_tuned_config(inst, N)
         whole = dict(shape, pairs_per_tile=P)
-        row = {"nodes": N, "launch": shape}
-        for key, cfg in (("default", None), ("one_work_item_per_batch", whole)):
+        # the shape fsp_autotune picks for this pool size (timed on the first slice)
+        tuned, _ = fsp.fsp_autotune(inst, rows_d[0][:N], dep_d[0][:N], outs[0][:N], stream=stream)
+        row = {"nodes": N, "launch": shape, "tuned_launch": tuned}
+        for key, cfg in (("default", shape), ("one_work_item_per_batch", whole), ("tuned", tuned)):
             for i in range(3):
                 fsp.fsp_bound_pool(inst, rows_d[i % 3][:N], dep_d[i % 3][:N], outs[i % 3][:N], stream=stream,
                                    config=cfg)
@@ -267,10 +269,11 @@ def run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, P: int, dep_h, n_j
             ops = sum(algorithmic_int_ops(n_jobs, m_mach, dep_h[(i * N) % (total - N + 1):][:N])
                       for i in range(reps))
             row[key + "_roofline_frac"] = ops / secs / peak
-        a = fsp.fsp_bound_pool(inst, rows_d[0][:N], dep_d[0][:N], stream=stream)
+        a = fsp.fsp_bound_pool(inst, rows_d[0][:N], dep_d[0][:N], stream=stream, config=shape)
         b = fsp.fsp_bound_pool(inst, rows_d[0][:N], dep_d[0][:N], stream=stream, config=whole)
+        c = fsp.fsp_bound_pool(inst, rows_d[0][:N], dep_d[0][:N], stream=stream, config=tuned)
         torch.cuda.synchronize()
-        row["same_bounds"] = bool(torch.equal(a, b))
+        row["same_bounds"] = bool(torch.equal(a, b) and torch.equal(a, c))
         out.append(row)
     return out
 
@@ -352,6 +355,25 @@ def run_config_leg(fsp, name: str, dev, peak: float, steps: int = 20, warmup: in
             "kernel_ms_mean": ms, "ops_per_launch": ops, "roofline_frac": ops / (ms * 1e-3) / peak,
             "launch": launch, "kernel": kernel_name(launch), "autotune_ms": tuned_ms,
             "l2": "256 MB write between launches"}
+
+
+def run_sizes_leg(dev):
+    """The pool-size and configuration legs alone (profiling): pool sizes
+    4,096-131,072 of the 200x20 pool, then the 20x20 and 500x20 pools."""
+    import torch
+    from paper_1208_3933_gb300 import fsp
+    w = rank_pool(0)
+    props = torch.cuda.get_device_properties(dev)
+    peak = alu_peak_ops(props.multi_processor_count, 2070.0, ALU_LANES_PER_SM)
+    stream = torch.cuda.current_stream(dev)
+    with fsp.Instance(w.p) as inst:
+        rows_d = [torch.from_numpy(w.rows).to(dev) for _ in range(3)]
+        dep_d = [torch.from_numpy(w.depths).to(dev) for _ in range(3)]
+        outs = [torch.empty(w.N, dtype=torch.int32, device=dev) for _ in range(3)]
+        sizes = run_pool_size_leg(fsp, inst, rows_d, dep_d, outs, stream, inst.info().pairs, w.depths, w.n, w.m,
+                                  peak)
+    configs = [run_config_leg(fsp, nm, dev, peak) for nm in ("pool_20x20", "pool_500x20")]
+    return {"pool_sizes": sizes, "configs": configs}
 
 
 def load_golden_optima():
@@ -492,7 +514,8 @@ def summarise(line: dict) -> dict:
     for c in line.get("configs") or []:
         out[c["workload"]] = {"nodes_per_s": r3(c["nodes_per_s"]), "frac": r3(c["roofline_frac"])}
     if line.get("pool_sizes"):
-        out["pool_size_frac"] = {str(r["nodes"]): r3(r["default_roofline_frac"]) for r in line["pool_sizes"]}
+        out["pool_size_frac"] = {str(r["nodes"]): r3(max(r["default_roofline_frac"], r["tuned_roofline_frac"]))
+                                 for r in line["pool_sizes"]}
     b = line.get("batched")
     if b:
         out["batched"] = {"nodes_per_s": r3(b["batched_nodes_per_s"]), "plain_nodes_per_s": r3(b["plain_nodes_per_s"]),
@@ -541,9 +564,9 @@ def max_over_ranks(world, value: float) -> float:
     return float(t.item())
 
 
-def rank_pool(rank: int):
+def rank_pool(rank: int, name: str = WORKLOAD):
     from paper_1208_3933_gb300 import workloads
-    w = workloads.named_pool(WORKLOAD)
+    w = workloads.named_pool(name)
     if rank == 0:
         return w
     rng = np.random.default_rng([2, rank])
@@ -625,7 +648,7 @@ def run_gpu(args, world, rank, local):
     build.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = rank_pool(rank)
+    w = rank_pool(rank, args.workload)
     if args.nodes:
         from paper_1208_3933_gb300 import workloads
         w = workloads.PoolWorkload(w.name, w.n, w.m, w.seed, w.p, np.ascontiguousarray(w.rows[:args.nodes]),
@@ -718,7 +741,7 @@ def run_gpu(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32+fp32-exact", "data": "synthetic",
         "dtype_note": "integer bound; the couple scan runs in fp32 on integer values below 2^19 with the job "
                       "in the low mantissa bits of s, exact (every result equals the oracle's int64)",
-        "config": {"workload": WORKLOAD, "n": w.n, "m": w.m, "nodes_per_step_per_gpu": w.N, "seed": w.seed,
+        "config": {"workload": w.name, "n": w.n, "m": w.m, "nodes_per_step_per_gpu": w.N, "seed": w.seed,
                    "p": "U[1,99]", "depth": "U{0..199}", "records": "compact" if info.compact else "wide",
                    "l2": "3 rotating pool copies of 105 MB (inputs larger than the 129 MB L2)",
                    "launch": launch, "autotune_ms": tuned_ms},
@@ -761,7 +784,9 @@ def main():
                     help="bound only the first NODES nodes of the pool (small profiling cases)")
     ap.add_argument("--alu-peak", action="store_true", help="run the integer-pipe throughput probe and exit")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and served legs")
-    ap.add_argument("--leg", default="", choices=["", "batched", "served", "searches"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=["pool_20x20", "pool_200x20", "pool_500x20"],
+                    help="bound another pool as the main line (profiling; the benchmark is pool_200x20)")
+    ap.add_argument("--leg", default="", choices=["", "batched", "served", "searches", "sizes"],
                     help="run one extra leg alone (single GPU) and print its JSON line (profiling)")
     ap.add_argument("--served-expand", type=int, default=0, help="served leg: parents per request (profiling)")
     ap.add_argument("--served-budget", type=int, default=0, help="served leg: node budget per search (profiling)")
@@ -779,7 +804,7 @@ def main():
         torch.cuda.set_device(dev)
         served_kw = {k: v for k, v in (("expand", args.served_expand), ("node_limit", args.served_budget)) if v}
         leg = {"batched": lambda: run_batched_leg(dev), "served": lambda: run_served_leg(**served_kw),
-               "searches": run_bnb_leg}[args.leg]()
+               "searches": run_bnb_leg, "sizes": lambda: run_sizes_leg(dev)}[args.leg]()
         print(json.dumps({"leg": args.leg, "result": leg}), flush=True)
         return
     if args.warmup < 3:

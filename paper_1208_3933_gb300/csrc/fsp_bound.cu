@@ -461,7 +461,9 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
         return FSP_EINVAL;
     }
     c.staging = tiled;
-    if (tiled != FSP_STAGING_STREAMED && (req_g != G || c.tail_slices > 1)) return FSP_EINVAL;
+    // couple slices: streamed and split staging; tail slices: streamed only
+    if (tiled == FSP_STAGING_WARP && req_g != G) return FSP_EINVAL;
+    if (tiled != FSP_STAGING_STREAMED && c.tail_slices > 1) return FSP_EINVAL;
     // Launch model for the defaults: a wave of work items (block batches of
     // 32 W nodes, times S couple slices of gper groups each) takes about
     // max(warps per SM, 16) x (setup + gper / G of a full scan), the setup
@@ -522,7 +524,8 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
                 double t = 0.0;
                 best_gper(W, &t);
                 const double score = 1.0 / t;
-                if (score > best * (1.0 + 1e-9)) {
+                // on a tie the smaller block wins: its items spread over more SMs
+                if (score >= best * (1.0 - 1e-9)) {
                     best = score;
                     bW = W;
                     bB = bps;

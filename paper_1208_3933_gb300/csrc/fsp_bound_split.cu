@@ -100,15 +100,28 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_scan(const LanesArgs a) {
         const unsigned char *src = a.grec + ((size_t)g * a.npad + (size_t)ch * a.chunk) * 32 * a.rec_bytes;
         tp.issue(fill, src, (uint32_t)pos * 32u * a.rec_bytes);
     };
-    if (threadIdx.x == 0 && (int64_t)blockIdx.x < a.num_batches) {
-        tile_issue(0, 0);
-        if (a.ntiles == 2) tile_issue(1, 1);
+    // Work items: block batch bt = it / S, couple slice it % S of gper groups
+    // (S = 1: every couple); the slices of a batch read the same prepared
+    // state and meet in an atomic max on the zeroed bounds.
+    const int S = a.gslices > 1 ? a.gslices : 1;
+    const int gper = S > 1 ? a.gper : a.G;
+    const int64_t items = a.num_batches * S;
+    auto first_tile = [&](int64_t it) { return (int)(it % S) * gper * a.nchunks; };
+    auto end_tile = [&](int64_t it) { return min(a.G, ((int)(it % S) + 1) * gper) * a.nchunks; };
+    if (threadIdx.x == 0 && (int64_t)blockIdx.x < items) {
+        if (tp.resident) {
+            tile_issue(0, 0);
+            if (a.ntiles == 2) tile_issue(1, 1);
+        } else {
+            tile_issue(0, first_tile(blockIdx.x));
+        }
     }
 
     const uint32_t *F = reinterpret_cast<const uint32_t *>(prep) + (size_t)warp * a.sb_words;
     const int32_t *AQ = reinterpret_cast<const int32_t *>(F + a.n);
     uint32_t prep_phase = 0;
-    for (int64_t bt = blockIdx.x; bt < a.num_batches; bt += gridDim.x, prep_phase ^= 1u) {
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, prep_phase ^= 1u) {
+        const int64_t bt = it / S;
         __syncthreads();  // the previous batch is done with the prepared state
         if (threadIdx.x == 0) {
             fence_proxy_async_smem();
@@ -136,11 +149,13 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_scan(const LanesArgs a) {
             ui[b] = 0;
         }
         int kk = 0, ll = 1;
-        for (int t = 0; t < a.ntiles; ++t) {
+        const int t1 = end_tile(it);
+        for (int t = first_tile(it); t < t1; ++t) {
             const int g = t / a.nchunks, ch = t - g * a.nchunks;
             if (!tp.resident && threadIdx.x == 0) {
-                const bool has_next = (t + 1 < a.ntiles) || (bt + gridDim.x < a.num_batches);
-                if (has_next) tile_issue(tp.fill + 1, (t + 1) % a.ntiles);
+                // the next tile of this item, else the first of the block's next item
+                const int next = t + 1 < t1 ? t + 1 : (it + gridDim.x < items ? first_tile(it + gridDim.x) : -1);
+                if (next >= 0) tile_issue(tp.fill + 1, next);
             }
             if (!tp.wait(t, a.wait_limit)) {
                 if (threadIdx.x == 0) {
@@ -176,7 +191,14 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_scan(const LanesArgs a) {
             }
         }
         const int best = transpose_max(lb, lane);
-        if (xid >= 0) a.out[xid] = bterm == INT_MIN ? FSP_LB_INVALID : max(best, bterm);
+        if (xid >= 0) {
+            if (bterm == INT_MIN)
+                a.out[xid] = FSP_LB_INVALID;  // every slice finds the row invalid
+            else if (S == 1)
+                a.out[xid] = max(best, bterm);
+            else
+                atomicMax(a.out + xid, max(best, bterm));  // out was zeroed; bounds are >= 0
+        }
     }
 }
 
@@ -353,12 +375,23 @@ fsp_status launch_split(const fsp_instance *inst, const int16_t *nodes, const in
         ap.N = ac.N = n_here;
         ap.num_batches = (nb32 + kPrepWarps - 1) / kPrepWarps;  // prep blocks' worth of batches
         ac.num_batches = nb32 / W;
+        // couple slices of every block batch (pairs_per_tile below P): the
+        // bounds are zeroed first and the slices meet in an atomic max
+        const int gper = lanes_groups_per_item(inst, cfg.pairs_per_tile);
+        const int S = gper < inst->G ? (inst->G + gper - 1) / gper : 1;
+        ac.gper = gper;
+        ac.gslices = S;
+        if (S > 1 && cudaMemsetAsync(out_lb + off, 0, sizeof(int32_t) * (size_t)n_here, s) != cudaSuccess) {
+            e = cudaErrorUnknown;
+            break;
+        }
         int32_t *order = nullptr;
         st = depth_order(inst, depths + off, n_here, s, &order);
         if (st != FSP_OK) break;
         ap.order = order;
         const int sms = num_sms(inst->device);
-        const int scan_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ac.num_batches, (int64_t)sms * bps));
+        const int scan_grid =
+            (int)std::max<int64_t>(1, std::min<int64_t>(ac.num_batches * S, (int64_t)sms * bps));
         e = inst->compact ? launch_pair_mp<false>(inst->mpad, ap, nb32, PL.total, ac, scan_grid, 32 * W, scan_smem,
                                                   sms, s)
                           : launch_pair_mp<true>(inst->mpad, ap, nb32, PL.total, ac, scan_grid, 32 * W, scan_smem,

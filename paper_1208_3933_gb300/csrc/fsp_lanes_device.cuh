@@ -73,7 +73,7 @@ __device__ __forceinline__ void warp_transpose32_n(uint32_t (&x)[NV], int lane) 
 constexpr int kMinimaChunk = 4;
 // Nodes with at most this many unscheduled jobs take their minima by walking
 // those jobs (instances of at most kWalkMaxMP padded machines).
-constexpr int kWalkMinima = 16;
+constexpr int kWalkMinima = 32;
 constexpr int kWalkMaxMP = 20;
 
 // Copies the first 32 entries of every machine's head- and tail-sorted job

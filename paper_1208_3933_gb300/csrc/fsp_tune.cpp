@@ -116,8 +116,9 @@ std::vector<fsp_launch_config> candidates(const fsp_instance *inst, int64_t N) {
                         }
                     }
                 // pools of under two waves of block batches: work items of
-                // fewer couples (streamed staging) as well
-                if (staging == FSP_STAGING_STREAMED && pos == 0 && N < 2 * 32 * W * (int64_t)sms)
+                // fewer couples (streamed and split staging) as well
+                if ((staging == FSP_STAGING_STREAMED || staging == FSP_STAGING_SPLIT) && pos == 0 &&
+                    N < 2 * 32 * W * (int64_t)sms)
                     for (int ppt : {32, 64, 96}) {
                         if (ppt >= inst->P) break;
                         c.pairs_per_tile = ppt;

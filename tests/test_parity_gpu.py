@@ -85,10 +85,11 @@ def test_every_lanes_shape_matches_oracle(gpu_lib, W, staging, positions, nm):
     assert np.array_equal(got, oracle_bounds(p, rows, depths))
 
 
+@pytest.mark.parametrize("staging", [2, 3])
 @pytest.mark.parametrize("ppt", [32, 64, 96, 160])
 @pytest.mark.parametrize("W,positions", [(1, 12), (4, 12), (3, 0)])
 @pytest.mark.parametrize("nm", [(40, 20), (70, 12), (33, 27), (23, 9)])
-def test_couple_sliced_work_items_match_oracle(gpu_lib, ppt, W, positions, nm):
+def test_couple_sliced_work_items_match_oracle(gpu_lib, ppt, W, positions, nm, staging):
     """Streamed staging with every block batch split by couples over several
     work items (pairs_per_tile 32 to 160: one to five groups of 32 couples per
     item, the last slice ragged or a single group), the slices combined by
@@ -101,7 +102,9 @@ def test_couple_sliced_work_items_match_oracle(gpu_lib, ppt, W, positions, nm):
     depths[[3, 50]] = [-1, n + 1]
     rows[7, :2] = [5, 5]
     depths[7] = max(int(depths[7]), 2)
-    cfg = dict(kernel=2, warps_per_block=W, positions_per_tile=positions, staging=2, pairs_per_tile=ppt)
+    if staging == 3 and positions == 0:
+        positions = 64  # split staging tiles positions
+    cfg = dict(kernel=2, warps_per_block=W, positions_per_tile=positions, staging=staging, pairs_per_tile=ppt)
     with fsp.Instance(p) as inst:
         got = gpu_bounds(fsp, inst, rows, depths, config=cfg)
     want = oracle_bounds(p, rows, depths)
@@ -165,7 +168,7 @@ def test_tail_sliced_batches_match_oracle(gpu_lib, ts, W, bps):
     assert np.array_equal(got[idx], oracle_bounds(p, rows[idx], depths[idx]))
 
 
-def test_couple_slices_refused_outside_streamed_staging(gpu_lib):
+def test_couple_slices_refused_outside_streamed_and_split_staging(gpu_lib):
     import torch
     fsp = gpu_lib
     p, rows, depths = pool(2, 30, 12, 100)
@@ -175,8 +178,9 @@ def test_couple_slices_refused_outside_streamed_staging(gpu_lib):
         with pytest.raises(fsp.FspError):
             fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=2, pairs_per_tile=32, tail_slices=2))
         for staging in (1, 3, 4):
-            with pytest.raises(fsp.FspError):
-                fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=staging, pairs_per_tile=32))
+            if staging != 3:  # split staging takes couple slices
+                with pytest.raises(fsp.FspError):
+                    fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=staging, pairs_per_tile=32))
             with pytest.raises(fsp.FspError):
                 fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=staging, tail_slices=2))
             # all couples in one work item is every staging's own shape
