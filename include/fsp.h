@@ -133,8 +133,8 @@ fsp_status fsp_instance_create(const int32_t *p, int32_t n, int32_t m, fsp_insta
 
 /* Options of fsp_instance_create_ex.
  *   FSP_INSTANCE_RELEASE_PER_JOB  the release time of machine k (the RM row
- *     of the figure "Pseudo-code implementing the LB function", lines
- *     (06)-(07)) is read per job, as Section II-D names RM "the matrix of the
+ *     of the figure "Pseudo-code implementing the LB function", where a
+ *     couple's scan starts) is read per job, as Section II-D names RM "the matrix of the
  *     earliest starting times of jobs": r_k = min over unscheduled j of
  *     est_jk, with est_j0 = C(sigma,0) and est_jk = max(C(sigma,k),
  *     est_j,k-1 + p_j,k-1); r_k = C(sigma,k) when no job is left.  It is

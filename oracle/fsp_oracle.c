@@ -29,7 +29,7 @@
  *     unscheduled j of the earliest start of j on machine k after the prefix;
  *   - LB starts at 0 (the pseudo-code's maxInteger start cannot be meant);
  *   - the couple loop, the filtered Johnson scan and the two-machine update
- *     follow the pseudo-code in its order, lines (03) to (19).
+ *     follow the LB pseudo-code of Section II-D in its order.
  *
  * All arithmetic is in int64_t; results are returned as int32_t.
  */
@@ -110,7 +110,7 @@ int fo_tables(int n, int m, const int32_t *p, int32_t *mm, int32_t *lag, int32_t
  * unscheduled set U is every other job.  Returns FO_EBADNODE (and leaves
  * *lb untouched) if d is outside [0,n], a prefix job is outside [0,n) or
  * appears twice.  pair_out, if not NULL, receives the value of every couple
- * (timeOnM2 after line (18) of the pseudo-code).
+ * (timeOnM2 once the pseudo-code has added the latency of M2).
  */
 int fo_lb_ex(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *lag,
              const int32_t *jm, const int16_t *row, int32_t d, int release,
@@ -147,8 +147,8 @@ int fo_lb_ex(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *l
             /* RM read as the earliest starting time of each unscheduled job j
                on each machine k after the prefix (Section II-D names RM "the
                matrix of the earliest starting times of jobs", indexed by
-               machine and job, and the pseudo-code takes its minimum over j,
-               lines (06)-(07)): est_j0 = C(sigma,0),
+               machine and job, and the pseudo-code takes its minimum over j
+               when it starts a couple): est_j0 = C(sigma,0),
                est_jk = max(C(sigma,k), est_j,k-1 + p_j,k-1);
                release of machine k = min over U of est_jk. */
             for (int k = 0; k < m; ++k) R[k] = -1;
@@ -180,16 +180,16 @@ int fo_lb_ex(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *l
             if (release != FO_RELEASE_EST || nu == 0) R[k] = C[k] > mh ? C[k] : mh;
             Q[k] = mq;
         }
-        /* The couple loop of the pseudo-code, lines (03)-(19). */
+        /* The couple loop of the LB pseudo-code (Section II-D). */
         int64_t LB = 0;
         int P = fo_num_pairs(m);
         for (int c = 0; c < P; ++c) {
             int M1 = mm[2 * c], M2 = mm[2 * c + 1];
-            int64_t t1 = R[M1]; /* timeOnM1, line (06) */
-            int64_t t2 = R[M2]; /* timeOnM2, line (07) */
+            int64_t t1 = R[M1]; /* timeOnM1 at the couple's start */
+            int64_t t2 = R[M2]; /* timeOnM2 at the couple's start */
             for (int i = 0; i < n; ++i) {
                 int job = jm[(size_t)c * n + i];
-                if (sched[job]) continue; /* line (10): only unscheduled jobs */
+                if (sched[job]) continue; /* only unscheduled jobs */
                 t1 = t1 + p[job * m + M1];
                 int64_t lg = lag[(size_t)c * n + job];
                 if (t2 > t1 + lg)
@@ -197,9 +197,9 @@ int fo_lb_ex(int n, int m, const int32_t *p, const int32_t *mm, const int32_t *l
                 else
                     t2 = t1 + lg + p[job * m + M2];
             }
-            t2 += Q[M2];           /* line (18) */
+            t2 += Q[M2];           /* latency of M2 */
             if (pair_out) pair_out[c] = t2;
-            if (t2 > LB) LB = t2;  /* line (19) */
+            if (t2 > LB) LB = t2;  /* max over couples */
         }
         *lb_out = (int32_t)LB;
     }

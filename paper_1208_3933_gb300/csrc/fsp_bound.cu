@@ -16,16 +16,16 @@
 //   4. for every machine l: q_l = min_{j in U} sum_{h>l} p_jh (QM) and the
 //      term A_l + q_l;
 //   5. for every couple (k,l): the filtered Johnson scan, run on the slack
-//      u = timeOnM2 - timeOnM1 of the pseudo-code.  Lines (11)-(15) update
+//      u = timeOnM2 - timeOnM1 of the pseudo-code.  Its two-machine update is
 //      timeOnM1 += p_jk; timeOnM2 = max(timeOnM2, timeOnM1 + lag_j) + p_jl,
 //      which is u <- max(u + delta_j, s_j) with delta_j = p_jl - p_jk and
 //      s_j = lag_j + p_jl.  That map composes to u_end = max(u_0 + S_l - S_k,
 //      F(0)), where F(0) is the scan started from u = 0, and since
-//      u_0 = r_l - r_k >= 0 the couple's value (line (18)) is
+//      u_0 = r_l - r_k >= 0 the couple's value (timeOnM2 plus the latency) is
 //          max(A_l + q_l, A_k + q_l + F(0)).
 //      The scan therefore needs neither release time: it starts at 0 and
 //      is the only O(n) loop per couple;
-//   6. LB = max over all terms (line (19)), or FSP_LB_INVALID for a bad row.
+//   6. LB = max over all terms, or FSP_LB_INVALID for a bad row.
 // Scheduled jobs and padding entries leave u unchanged: for a scheduled job
 // the update is skipped, and padding records (delta = s = 0) map u >= 0 to
 // itself.

@@ -323,10 +323,10 @@ MUTANTS = {
     "dropped lag": ("for (int h = k + 1; h < l; ++h) lg += p[j * m + h];", ""),
     "set 2 ascending": ("items[j].key = -b;", "items[j].key = b;"),
     "set test reversed": ("if (p[j * m + k] <= p[j * m + l]) {", "if (p[j * m + k] >= p[j * m + l]) {"),
-    "no latency": ("t2 += Q[M2];           /* line (18) */", ""),
+    "no latency": ("t2 += Q[M2];           /* latency of M2 */", ""),
     "release without heads": ("R[k] = C[k] > mh ? C[k] : mh;", "R[k] = C[k];"),
     "machines swapped in update": ("t2 += p[job * m + M2];", "t2 += p[job * m + M1];"),
-    "scheduled jobs not filtered": ("if (sched[job]) continue; /* line (10): only unscheduled jobs */", ""),
+    "scheduled jobs not filtered": ("if (sched[job]) continue; /* only unscheduled jobs */", ""),
     "est: machine availability ignored": ("est = C[k] > ready ? C[k] : ready;", "est = ready;"),
     "est: time of the wrong machine": ("int64_t ready = est + p[j * m + k - 1];", "int64_t ready = est + p[j * m + k];"),
     "est: largest start kept": ("if (R[k] < 0 || est < R[k]) R[k] = est;", "if (R[k] < 0 || est > R[k]) R[k] = est;"),
