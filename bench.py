@@ -67,7 +67,7 @@ def kernel_name(cfg) -> str:
     if not cfg or cfg.get("kernel") == 1:
         return "fsp_bound_kernel (node-lockstep)"
     return {1: "fsp_lanes_resident", 2: "fsp_lanes_streamed", 3: "fsp_lanes_scan (after fsp_lanes_prep)",
-            4: "fsp_lanes_warp"}.get(cfg.get("staging"), "fsp_lanes_streamed")
+            4: "fsp_lanes_warp", 5: "fsp_lanes_global"}.get(cfg.get("staging"), "fsp_lanes_streamed")
 
 
 def read_traffic(n_nodes: int):

@@ -91,18 +91,24 @@ typedef struct fsp_instance_info {
  * pool the library keeps; about (n + 48 m + 64) * 4 bytes per 32 nodes, at
  * most 2^20 nodes' worth per call) and a scan kernel streams the tiles; or
  * warp: every warp streams the tiles through its own ring of buffers and the
- * warps of a block work independently. */
+ * warps of a block work independently; or global: no tiles, every warp reads
+ * its couples' records from global memory (L2/L1) through a ring of register
+ * loads, and each warp takes its own work items (a 32-node batch and a slice
+ * of the couples), so a small pool can occupy every SM (32-bit records only;
+ * blocks_per_sm up to 16 / warps_per_block). */
 #define FSP_STAGING_AUTO 0
 #define FSP_STAGING_RESIDENT 1
 #define FSP_STAGING_STREAMED 2
 #define FSP_STAGING_SPLIT 3
 #define FSP_STAGING_WARP 4
+#define FSP_STAGING_GLOBAL 5
 typedef struct fsp_launch_config {
     int32_t kernel;              /* FSP_KERNEL_* */
     int32_t nodes_per_thread;    /* lockstep: K in {1,2,4,8} */
-    int32_t blocks_per_sm;       /* resident blocks per SM (1 or 2; lanes: streamed/split/warp staging) */
+    int32_t blocks_per_sm;       /* resident blocks per SM (1 or 2; lanes: streamed/split/warp staging;
+                                    global staging: 1..16 / warps_per_block) */
     int32_t pairs_per_tile;      /* lockstep: couples staged in shared memory at a time;
-                                    lanes, streamed: couples per work item, rounded up to whole
+                                    lanes, streamed and global: couples per work item, rounded up to whole
                                     groups of 32 (fewer than all: a block batch is split by
                                     couples over several work items, for pools too small to
                                     occupy every SM); other stagings: all couples.  0 = chosen
@@ -312,7 +318,9 @@ typedef struct fsp_batch fsp_batch;
  * must be the device of every instance.
  *   pools  host array of `count` descriptors (copied; the device buffers they
  *          name must stay valid while the batch is launched);
- *   warps_per_block  1..16, or 0 to choose;
+ *   warps_per_block  1..16, or 0 to choose (16, or for a plan of fewer than
+ *          16 work items per SM the fewest warps that give every item its
+ *          own warp with at most one block per SM);
  *   out    receives the plan.
  * Every instance must use 32-bit Johnson records (fsp_instance_info.compact).
  * Errors: FSP_EINVAL, FSP_ENOMEM, FSP_ECUDA.

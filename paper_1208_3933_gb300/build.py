@@ -33,7 +33,7 @@ def sources():
 
 
 def _newest_input() -> float:
-    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     files.append(os.path.join(ROOT, "include", "fsp.h"))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)

@@ -191,7 +191,15 @@ fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_p
     if (pp.nitems > INT32_MAX) return FSP_EINVAL;
     // shared memory: flags [warps][n_max] words, rows [warps][32][stride] ints
     const int smem_optin = max_smem_per_block(device);
-    int W = warps_per_block ? warps_per_block : 16;
+    // Unless the caller fixes the node tile, a plan of fewer than 16 items
+    // per SM takes the fewest warps per block that still put every item in
+    // flight at once on at most one block per SM: the warps of one block sit
+    // on different schedulers, so every warp runs its setup and scan without
+    // sharing a scheduler, and no SM stays idle while another holds 16 warps
+    // (a 140-item search batch in 16-warp blocks ran on 9 of 152 SMs).
+    const int64_t sms = std::max(1, num_sms(device));
+    int W = warps_per_block ? warps_per_block
+                            : (int)std::min<int64_t>(16, std::max<int64_t>(1, (pp.nitems + sms - 1) / sms));
     for (; W >= 1; --W) {
         const uint32_t off_aq = (uint32_t)align_up((size_t)W * pp.n_max * 4, 128);
         const size_t total = align_up(off_aq + (size_t)W * 32 * pp.stride * 4, 128);

@@ -403,10 +403,33 @@ fsp_status resolve_lockstep(const fsp_instance *inst, int64_t N, const DeviceLim
 
 fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits &d, fsp_launch_config &c) {
     if (c.warps_per_block < 0 || c.warps_per_block > 16 || c.positions_per_tile < 0 ||
-        (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 4 || c.blocks_per_sm < 0 || c.blocks_per_sm > 2 ||
-        c.pairs_per_tile < 0 || c.tail_slices < 0)
+        (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 5 || c.blocks_per_sm < 0 ||
+        c.blocks_per_sm > (c.staging == FSP_STAGING_GLOBAL ? 16 : 2) || c.pairs_per_tile < 0 || c.tail_slices < 0)
         return FSP_EINVAL;
     const int G = inst->G;
+    if (c.staging == FSP_STAGING_GLOBAL) {
+        // Warps independent, records from L2/L1: every work item (a 32-node
+        // batch and a slice of the couples) gets a warp of its own when the
+        // pool is small.  Defaults: 4 warps per block, as many blocks per SM
+        // as make 16 warps, and couple slices enough to give the grid's warps
+        // an item each (at most G).
+        if (!inst->compact || c.tail_slices > 1 || c.positions_per_tile) return FSP_EINVAL;
+        if (!c.warps_per_block) c.warps_per_block = c.blocks_per_sm ? std::max(1, 16 / c.blocks_per_sm) : 4;
+        if (!c.blocks_per_sm) c.blocks_per_sm = std::max(1, 16 / c.warps_per_block);
+        if (c.warps_per_block * c.blocks_per_sm > 16) return FSP_EINVAL;
+        int gper = lanes_groups_per_item(inst, c.pairs_per_tile);
+        if (!c.pairs_per_tile) {
+            const int64_t batches = (std::max<int64_t>(N, 1) + 31) / 32;
+            const int64_t warps = (int64_t)d.num_sms * c.warps_per_block * c.blocks_per_sm;
+            const int64_t S = std::min<int64_t>(G, std::max<int64_t>(1, (warps + batches - 1) / batches));
+            gper = (int)((G + S - 1) / S);
+        }
+        c.pairs_per_tile = gper >= G ? inst->P : gper * 32;
+        c.tail_slices = 1;
+        c.positions_per_tile = 0;
+        size_t smem = 0;
+        return lanes_layout(inst, c, &smem);
+    }
     // pairs per work item: only streamed staging splits a batch by couples
     const int req_g = lanes_groups_per_item(inst, c.pairs_per_tile);
     auto resolved_ppt = [&](int gper) { return gper >= G ? inst->P : gper * 32; };

@@ -50,6 +50,7 @@
 #include <mutex>
 
 #include "fsp_internal.h"
+#include "fsp_batch_scan.cuh"
 #include "fsp_lanes_device.cuh"
 #include "fsp_ptx.cuh"
 
@@ -252,6 +253,55 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
     }
 }
 
+// ---------------------------------------------------------------- global
+// No shared-memory tiles: every warp reads its couple groups' records from
+// global memory (L2/L1) through the register ring of scan_compact_global, so
+// the warps of a block never wait for each other and a pool too small to fill
+// the GPU with block batches can give each work item a warp of its own.  Work
+// item it = 32-node batch it / S, couple slice it % S (S = gslices, slices of
+// gper groups); the grid's T warps take items w, w + T, w + 2T, ... in order.
+template <int MP>
+__global__ void __launch_bounds__(512, 1) fsp_lanes_global(const LanesArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * flag_words(a.n);
+    int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
+    const int64_t S = a.gslices > 1 ? a.gslices : 1;
+    const int64_t items = a.num_batches * S;
+    const int64_t T = (int64_t)gridDim.x * W;
+    for (int64_t it = (int64_t)blockIdx.x * W + warp; it < items; it += T) {
+        const int64_t bt = it / S;
+        const int sl = (int)(it - bt * S);
+        const int64_t x = node_at(a, bt * 32 + lane);
+        int bterm = 0;
+        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm);
+        int lb[32];
+#pragma unroll
+        for (int b = 0; b < 32; ++b) lb[b] = 0;
+        const int g0 = S > 1 ? sl * a.gper : 0, g1 = S > 1 ? min(a.G, g0 + a.gper) : a.G;
+        for (int g = g0; g < g1; ++g) {
+            const int kk = __ldg(a.gpairs + 2 * (g * 32 + lane)), ll = __ldg(a.gpairs + 2 * (g * 32 + lane) + 1);
+            float u[32];
+#pragma unroll
+            for (int b = 0; b < 32; ++b) u[b] = 0.f;
+            const uint2 *R = reinterpret_cast<const uint2 *>(a.grec) + (size_t)g * a.npad * 32 + lane;
+            scan_compact_global(R, a.npad, F, u);
+            couple_epilogue<false>(AQ, a.aq_stride, a.m, kk, ll, u, lb);
+        }
+        const int best = transpose_max(lb, lane);
+        if (x < a.N) {
+            if (S == 1)
+                a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
+            else if (!valid)
+                a.out[x] = FSP_LB_INVALID;  // every slice finds the row invalid
+            else
+                atomicMax(a.out + x, max(best, bterm));  // out was zeroed; bounds are >= 0
+        }
+        __syncwarp();  // the flag and row arrays are rewritten by the next item
+    }
+}
+
 // ---------------------------------------------------------------- host side
 namespace {
 
@@ -323,6 +373,38 @@ cudaError_t launch_lanes_mp(const LanesArgs &a, int mp, bool resident, int grid,
     }
 }
 
+// Global staging: flag words and node rows of every warp, nothing else.
+LanesLayout global_layout_for(const fsp_instance *inst, int warps) {
+    LanesLayout L = {};
+    L.off_flags = 0;
+    L.off_aq = (uint32_t)align_up((size_t)warps * flag_words(inst->n) * 4, 128);
+    L.aq_stride = aq_stride_for(inst->m, !inst->compact);
+    L.total = align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
+    return L;
+}
+
+template <int MP>
+cudaError_t launch_global_variant(const LanesArgs &a, int grid, int threads, size_t smem, cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] { attr_err = set_smem_attr(fsp_lanes_global<MP>); });
+    if (attr_err != cudaSuccess) return attr_err;
+    note_launches(1);
+    fsp_lanes_global<MP><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_global_mp(const LanesArgs &a, int mp, int grid, int threads, size_t smem, cudaStream_t s) {
+    switch (mp) {
+        case 8: return launch_global_variant<8>(a, grid, threads, smem, s);
+        case 12: return launch_global_variant<12>(a, grid, threads, smem, s);
+        case 16: return launch_global_variant<16>(a, grid, threads, smem, s);
+        case 20: return launch_global_variant<20>(a, grid, threads, smem, s);
+        case 24: return launch_global_variant<24>(a, grid, threads, smem, s);
+        default: return launch_global_variant<32>(a, grid, threads, smem, s);
+    }
+}
+
 }  // namespace
 
 int lanes_groups_per_item(const fsp_instance *inst, int pairs_per_tile) {
@@ -335,6 +417,16 @@ fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, si
     if (c.staging == FSP_STAGING_WARP) return warp_layout(inst, c, smem_bytes);
     const int W = c.warps_per_block;
     const int bps = c.blocks_per_sm ? c.blocks_per_sm : 1;
+    if (c.staging == FSP_STAGING_GLOBAL) {
+        // compact records only (the register ring holds two-word records)
+        if (!inst->compact || W < 1 || W > 16 || bps < 1 || W * bps > 16) return FSP_EINVAL;
+        const LanesLayout L = global_layout_for(inst, W);
+        const size_t budget = std::min((size_t)max_smem_per_block(inst->device),
+                                       (size_t)max_smem_per_sm(inst->device) / bps - 1024);
+        if (L.total > budget) return FSP_EINVAL;
+        *smem_bytes = L.total;
+        return FSP_OK;
+    }
     if (W < 1 || W > 16 || bps < 1 || bps > 2 || W * bps > 16) return FSP_EINVAL;
     const bool resident = c.staging == FSP_STAGING_RESIDENT;
     if (!resident && (c.positions_per_tile < 4 || (c.positions_per_tile & 3))) return FSP_EINVAL;
@@ -350,6 +442,58 @@ fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, si
     return FSP_OK;
 }
 
+namespace {
+
+fsp_status launch_global(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
+                         int32_t *out_lb, void *stream, const fsp_launch_config &cfg, size_t smem) {
+    const int W = cfg.warps_per_block;
+    const int bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 1;
+    const LanesLayout L = global_layout_for(inst, W);
+    LanesArgs a = {};
+    a.grec = static_cast<const unsigned char *>(inst->t.grec);
+    a.gpairs = inst->t.gpairs;
+    a.hsort = reinterpret_cast<const int2 *>(inst->t.hsort);
+    a.tsort = reinterpret_cast<const int2 *>(inst->t.tsort);
+    a.ptot = inst->t.ptot;
+    a.pp = inst->t.pp;
+    a.nodes = nodes;
+    a.depths = depths;
+    a.out = out_lb;
+    a.status = inst->dev_status;
+    a.N = N;
+    a.n = inst->n;
+    a.m = inst->m;
+    a.G = inst->G;
+    a.npad = inst->npad;
+    a.mpad = inst->mpad;
+    a.rec_bytes = (uint32_t)inst->grec_bytes;
+    a.off_flags = L.off_flags;
+    a.off_aq = L.off_aq;
+    a.aq_stride = L.aq_stride;
+    a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
+    a.q32 = 0;
+    a.wait_limit = 4000000000LL;
+    a.num_batches = (N + 31) / 32;
+    a.gper = lanes_groups_per_item(inst, cfg.pairs_per_tile);
+    a.gslices = (inst->G + a.gper - 1) / a.gper;
+    const int64_t items = a.num_batches * a.gslices;
+    const int64_t slots = (int64_t)num_sms(inst->device) * bps;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((items + W - 1) / W, slots));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // couple slices combine by atomic max into zeroed bounds
+    if (a.gslices > 1 && cudaMemsetAsync(out_lb, 0, sizeof(int32_t) * (size_t)N, s) != cudaSuccess)
+        return FSP_ECUDA;
+    int32_t *order = nullptr;
+    fsp_status st = depth_order(inst, depths, N, s, &order);
+    if (st != FSP_OK) return st;
+    a.order = order;
+    const cudaError_t e = launch_global_mp(a, inst->mpad, grid, 32 * W, smem, s);
+    const cudaError_t ef = order ? cudaFreeAsync(order, s) : cudaSuccess;
+    return (e == cudaSuccess && ef == cudaSuccess) ? FSP_OK : FSP_ECUDA;
+}
+
+}  // namespace
+
 fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
                         int32_t *out_lb, void *stream, const fsp_launch_config &cfg) {
     if (cfg.staging == FSP_STAGING_SPLIT) return launch_split(inst, nodes, depths, N, out_lb, stream, cfg);
@@ -357,6 +501,7 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     size_t smem = 0;
     fsp_status st = lanes_layout(inst, cfg, &smem);
     if (st != FSP_OK) return st;
+    if (cfg.staging == FSP_STAGING_GLOBAL) return launch_global(inst, nodes, depths, N, out_lb, stream, cfg, smem);
     const int W = cfg.warps_per_block;
     const bool resident = cfg.staging == FSP_STAGING_RESIDENT;
     const int chunk = resident ? inst->npad : std::min(cfg.positions_per_tile, inst->npad);

@@ -132,6 +132,18 @@ std::vector<fsp_launch_config> candidates(const fsp_instance *inst, int64_t N) {
                     }
             }
     }
+    // global staging (warps independent, records from L2/L1): node tiles of
+    // 1-16 warps, couple slices chosen from the pool size or fixed
+    for (int W : {16, 8, 4, 2, 1})
+        for (int ppt : {0, 32, 64, 96, 1 << 30}) {
+            if (ppt && ppt < (1 << 30) && ppt >= inst->P) continue;
+            fsp_launch_config c = {};
+            c.kernel = FSP_KERNEL_LANES;
+            c.staging = FSP_STAGING_GLOBAL;
+            c.warps_per_block = W;
+            c.pairs_per_tile = ppt == (1 << 30) ? inst->P : ppt;
+            add(c);
+        }
     for (int K : {8, 4, 2, 1})
         for (int bps : {1, 2}) {
             fsp_launch_config c = {};

@@ -54,6 +54,7 @@ FSP_STAGING_RESIDENT = 1
 FSP_STAGING_STREAMED = 2
 FSP_STAGING_SPLIT = 3
 FSP_STAGING_WARP = 4
+FSP_STAGING_GLOBAL = 5
 
 
 class fsp_launch_config(ctypes.Structure):

@@ -112,6 +112,63 @@ def test_couple_sliced_work_items_match_oracle(gpu_lib, ppt, W, positions, nm, s
     assert got[3] == got[50] == got[7] == fsp.FSP_LB_INVALID
 
 
+@pytest.mark.parametrize("ppt", [0, 32, 64, 160, 1000])
+@pytest.mark.parametrize("W,bps", [(1, 0), (4, 0), (3, 5), (16, 1)])
+@pytest.mark.parametrize("nm", [(40, 20), (70, 12), (33, 27), (23, 9), (200, 20)])
+def test_global_staging_matches_oracle(gpu_lib, ppt, W, bps, nm):
+    """Global staging: no shared-memory record tiles, every warp reads its
+    couples' records through the register ring and takes its own work items
+    (a 32-node batch and a couple slice: one to five groups of 32 couples,
+    the last slice ragged, or all couples; 0 = slices chosen from the pool
+    size); pools of a few warps' worth up to several per warp of the grid,
+    with a ragged last batch and invalid rows that every slice must agree
+    on."""
+    fsp = gpu_lib
+    n, m = nm
+    p, rows, depths = pool(700 + n + m, n, m, 32 * W * 7 + 19)
+    depths[[3, 50]] = [-1, n + 1]
+    rows[7, :2] = [5, 5]
+    depths[7] = max(int(depths[7]), 2)
+    cfg = dict(kernel=2, staging=5, warps_per_block=W, blocks_per_sm=bps, pairs_per_tile=ppt)
+    with fsp.Instance(p) as inst:
+        got = gpu_bounds(fsp, inst, rows, depths, config=cfg)
+    want = oracle_bounds(p, rows, depths)
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+    assert got[3] == got[50] == got[7] == fsp.FSP_LB_INVALID
+
+
+def test_global_staging_depth_order_release_and_refusals(gpu_lib):
+    """Global staging on a depth-ordered pool (n >= 64, N >= 8,192), sliced
+    and whole, with per-job release times; refused for 128-bit records and
+    for shapes outside its limits."""
+    fsp = gpu_lib
+    w = workloads.named_pool("pool_200x20", N=9000)
+    idx = np.random.default_rng(5).choice(w.N, 300, replace=False)
+    with fsp.Instance(w.p) as inst:
+        a = gpu_bounds(fsp, inst, w.rows, w.depths, config=dict(kernel=2, staging=5, pairs_per_tile=64))
+        b = gpu_bounds(fsp, inst, w.rows, w.depths, config=dict(kernel=2, staging=5, warps_per_block=8,
+                                                                pairs_per_tile=190))
+        c = gpu_bounds(fsp, inst, w.rows, w.depths, config=dict(kernel=2, staging=2, warps_per_block=8))
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+        assert np.array_equal(a[idx], oracle_bounds(w.p, w.rows[idx], w.depths[idx]))
+        r, d = to_dev(w.rows[:100], w.depths[:100])
+        for bad in (dict(kernel=2, staging=5, warps_per_block=8, blocks_per_sm=3),
+                    dict(kernel=2, staging=5, positions_per_tile=8), dict(kernel=2, staging=5, tail_slices=2)):
+            with pytest.raises(fsp.FspError):
+                fsp.fsp_bound_pool(inst, r, d, config=bad)
+    with fsp.Instance(w.p, flags=fsp.FSP_INSTANCE_RELEASE_PER_JOB) as inst:
+        got = gpu_bounds(fsp, inst, w.rows[:3000], w.depths[:3000], config=dict(kernel=2, staging=5,
+                                                                                  warps_per_block=2))
+    want = oracle.Tables(w.p).lb_pool(w.rows[:3000], w.depths[:3000], threads=THREADS, release=oracle.RELEASE_EST)
+    assert np.array_equal(got, want)
+    p, rows, depths = pool(9, 45, 11, 170, hi=20000)
+    with fsp.Instance(p) as inst:
+        assert inst.info().compact == 0
+        r, d = to_dev(rows, depths)
+        with pytest.raises(fsp.FspError):
+            fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=5))
+
+
 def test_couple_slices_with_depth_order_release_and_wide_records(gpu_lib):
     """Couple slices on a depth-ordered pool (n >= 64, N >= 8,192), with
     per-job release times, and with 128-bit records; the default shape of a
@@ -498,6 +555,9 @@ def _every_path(fsp, inst, rows, depths):
             dict(kernel=1, nodes_per_thread=2)]
     if info.flags:
         cfgs.pop()  # per-job release times: couple-lanes kernels only
+    if info.compact:  # global staging reads two-word records only
+        cfgs += [dict(kernel=2, staging=5, warps_per_block=4), dict(kernel=2, staging=5, warps_per_block=1,
+                                                                    pairs_per_tile=32)]
     out = {str(c): gpu_bounds(fsp, inst, rows, depths, config=c) for c in cfgs}
     if info.compact:
         r, d = to_dev(rows, depths)
