@@ -105,8 +105,9 @@ typedef struct fsp_instance_info {
 typedef struct fsp_launch_config {
     int32_t kernel;              /* FSP_KERNEL_* */
     int32_t nodes_per_thread;    /* lockstep: K in {1,2,4,8} */
-    int32_t blocks_per_sm;       /* resident blocks per SM (1 or 2; lanes: streamed/split/warp staging;
-                                    global staging: 1..16 / warps_per_block) */
+    int32_t blocks_per_sm;       /* resident blocks per SM (lockstep 1 or 2; lanes: streamed staging
+                                    1..8, split/warp staging 1 or 2, global staging 1..16; at most
+                                    16 warps per SM) */
     int32_t pairs_per_tile;      /* lockstep: couples staged in shared memory at a time;
                                     lanes, streamed and global: couples per work item, rounded up to whole
                                     groups of 32 (fewer than all: a block batch is split by

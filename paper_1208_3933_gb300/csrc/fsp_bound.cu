@@ -404,7 +404,7 @@ fsp_status resolve_lockstep(const fsp_instance *inst, int64_t N, const DeviceLim
 fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits &d, fsp_launch_config &c) {
     if (c.warps_per_block < 0 || c.warps_per_block > 16 || c.positions_per_tile < 0 ||
         (c.positions_per_tile & 3) || c.staging < 0 || c.staging > 5 || c.blocks_per_sm < 0 ||
-        c.blocks_per_sm > (c.staging == FSP_STAGING_GLOBAL ? 16 : 2) || c.pairs_per_tile < 0 || c.tail_slices < 0)
+        c.blocks_per_sm > (c.staging == FSP_STAGING_GLOBAL ? 16 : 8) || c.pairs_per_tile < 0 || c.tail_slices < 0)
         return FSP_EINVAL;
     const int G = inst->G;
     if (c.staging == FSP_STAGING_GLOBAL) {

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
 // the GPU with block batches can give each work item a warp of its own.  Work
 // item it = 32-node batch it / S, couple slice it % S (S = gslices, slices of
 // gper groups); the grid's T warps take items w, w + T, w + 2T, ... in order.
-template <int MP>
+template <int MP, bool PS>
 __global__ void __launch_bounds__(512, 1) fsp_lanes_global(const LanesArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -270,12 +270,18 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_global(const LanesArgs a) {
     const int64_t S = a.gslices > 1 ? a.gslices : 1;
     const int64_t items = a.num_batches * S;
     const int64_t T = (int64_t)gridDim.x * W;
+    // PS: the block's shared-memory copy of the processing times
+    int32_t *ptab = PS ? reinterpret_cast<int32_t *>(smem + a.off_ptab) : nullptr;
+    if (PS) {
+        load_ptab(a, ptab);
+        __syncthreads();
+    }
     for (int64_t it = (int64_t)blockIdx.x * W + warp; it < items; it += T) {
         const int64_t bt = it / S;
         const int sl = (int)(it - bt * S);
         const int64_t x = node_at(a, bt * 32 + lane);
         int bterm = 0;
-        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm);
+        const bool valid = lanes_setup<MP, PS>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, nullptr, nullptr, ptab);
         int lb[32];
 #pragma unroll
         for (int b = 0; b < 32; ++b) lb[b] = 0;
@@ -309,15 +315,32 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct LanesLayout {
     uint32_t off_cache, off_tables, tile_stride, off_flags, off_aq;
+    uint32_t off_ptab;  // shared-memory copy of the processing times (0 = none)
     int32_t aq_stride;
     size_t total;
 };
 
+// Global staging copies the processing-time rows (pp, [n][mpad] int32) to
+// shared memory when they fit the block's budget beside the warps' flag words
+// and rows (at most 64 KB):
+// the setup's prefix recurrence, walks and release times then read a row in
+// one shared-memory latency instead of an L1 miss.
+constexpr size_t kPtabMaxBytes = 64 * 1024;
+void add_ptab(LanesLayout &L, const fsp_instance *inst, size_t budget) {
+    const size_t bytes = (size_t)inst->n * inst->mpad * 4;
+    const size_t off = align_up(L.total, 128);
+    L.off_ptab = 0;
+    if (bytes <= kPtabMaxBytes && off + bytes <= budget) {
+        L.off_ptab = (uint32_t)off;
+        L.total = align_up(off + bytes, 128);
+    }
+}
+
 // ints per node row: A_k as int32, then q_l as int16 (compact records) or int32
 int aq_stride_for(int m, bool q32) { return (m + (q32 ? m : (m + 1) / 2)) | 1; }
 
-LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident, int chunk) {
-    LanesLayout L;
+LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident, int chunk, size_t budget) {
+    LanesLayout L = {};
     L.off_cache = (uint32_t)align_up(16 + (size_t)inst->G * 64, 128);
     L.off_tables = (uint32_t)align_up(L.off_cache + (size_t)inst->m * 32 * 8 * 2, 128);
     const size_t group_bytes = (size_t)inst->npad * 32 * inst->grec_bytes;
@@ -331,6 +354,7 @@ LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident,
     L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)warps * flag_words(inst->n) * 4, 128);
     L.aq_stride = aq_stride_for(inst->m, !inst->compact);
     L.total = align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
+    (void)budget;  // the tiled kernels read the processing times from global memory
     return L;
 }
 
@@ -374,23 +398,38 @@ cudaError_t launch_lanes_mp(const LanesArgs &a, int mp, bool resident, int grid,
 }
 
 // Global staging: flag words and node rows of every warp, nothing else.
-LanesLayout global_layout_for(const fsp_instance *inst, int warps) {
+LanesLayout global_layout_for(const fsp_instance *inst, int warps, size_t budget) {
     LanesLayout L = {};
     L.off_flags = 0;
     L.off_aq = (uint32_t)align_up((size_t)warps * flag_words(inst->n) * 4, 128);
     L.aq_stride = aq_stride_for(inst->m, !inst->compact);
     L.total = align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
+    add_ptab(L, inst, budget);
     return L;
+}
+
+// Shared memory a block may take: the opt-in maximum, or an equal share of
+// the SM for several blocks per SM.
+size_t lanes_budget(const fsp_instance *inst, int bps) {
+    return bps <= 1 ? (size_t)max_smem_per_block(inst->device)
+                    : std::min((size_t)max_smem_per_block(inst->device),
+                               (size_t)max_smem_per_sm(inst->device) / bps - 1024);
 }
 
 template <int MP>
 cudaError_t launch_global_variant(const LanesArgs &a, int grid, int threads, size_t smem, cudaStream_t s) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] { attr_err = set_smem_attr(fsp_lanes_global<MP>); });
+    std::call_once(once, [] {
+        attr_err = set_smem_attr(fsp_lanes_global<MP, false>);
+        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_global<MP, true>);
+    });
     if (attr_err != cudaSuccess) return attr_err;
     note_launches(1);
-    fsp_lanes_global<MP><<<grid, threads, smem, s>>>(a);
+    if (a.off_ptab)
+        fsp_lanes_global<MP, true><<<grid, threads, smem, s>>>(a);
+    else
+        fsp_lanes_global<MP, false><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -420,21 +459,20 @@ fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, si
     if (c.staging == FSP_STAGING_GLOBAL) {
         // compact records only (the register ring holds two-word records)
         if (!inst->compact || W < 1 || W > 16 || bps < 1 || W * bps > 16) return FSP_EINVAL;
-        const LanesLayout L = global_layout_for(inst, W);
-        const size_t budget = std::min((size_t)max_smem_per_block(inst->device),
-                                       (size_t)max_smem_per_sm(inst->device) / bps - 1024);
+        const size_t budget = lanes_budget(inst, bps);
+        const LanesLayout L = global_layout_for(inst, W, budget);
         if (L.total > budget) return FSP_EINVAL;
         *smem_bytes = L.total;
         return FSP_OK;
     }
-    if (W < 1 || W > 16 || bps < 1 || bps > 2 || W * bps > 16) return FSP_EINVAL;
     const bool resident = c.staging == FSP_STAGING_RESIDENT;
+    // up to 8 blocks per SM for streamed staging (small node tiles of small
+    // pools), 2 otherwise
+    if (W < 1 || W > 16 || bps < 1 || bps > (resident ? 2 : 8) || W * bps > 16) return FSP_EINVAL;
     if (!resident && (c.positions_per_tile < 4 || (c.positions_per_tile & 3))) return FSP_EINVAL;
     const int chunk = resident ? inst->npad : std::min(c.positions_per_tile, inst->npad);
-    const LanesLayout L = lanes_layout_for(inst, W, resident, chunk);
-    const size_t budget = bps == 1 ? (size_t)max_smem_per_block(inst->device)
-                                   : std::min((size_t)max_smem_per_block(inst->device),
-                                              (size_t)max_smem_per_sm(inst->device) / 2 - 1024);
+    const size_t budget = lanes_budget(inst, bps);
+    const LanesLayout L = lanes_layout_for(inst, W, resident, chunk, budget);
     if (L.total > budget) return FSP_EINVAL;
     // the resident copy completes on one mbarrier: its byte count must fit the transaction counter
     if (resident && (size_t)inst->npad * 32 * inst->grec_bytes * inst->G >= (1u << 20)) return FSP_EINVAL;
@@ -448,7 +486,7 @@ fsp_status launch_global(const fsp_instance *inst, const int16_t *nodes, const i
                          int32_t *out_lb, void *stream, const fsp_launch_config &cfg, size_t smem) {
     const int W = cfg.warps_per_block;
     const int bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 1;
-    const LanesLayout L = global_layout_for(inst, W);
+    const LanesLayout L = global_layout_for(inst, W, lanes_budget(inst, bps));
     LanesArgs a = {};
     a.grec = static_cast<const unsigned char *>(inst->t.grec);
     a.gpairs = inst->t.gpairs;
@@ -469,6 +507,7 @@ fsp_status launch_global(const fsp_instance *inst, const int16_t *nodes, const i
     a.rec_bytes = (uint32_t)inst->grec_bytes;
     a.off_flags = L.off_flags;
     a.off_aq = L.off_aq;
+    a.off_ptab = L.off_ptab;
     a.aq_stride = L.aq_stride;
     a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
     a.q32 = 0;
@@ -505,7 +544,8 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     const int W = cfg.warps_per_block;
     const bool resident = cfg.staging == FSP_STAGING_RESIDENT;
     const int chunk = resident ? inst->npad : std::min(cfg.positions_per_tile, inst->npad);
-    const LanesLayout L = lanes_layout_for(inst, W, resident, chunk);
+    const LanesLayout L = lanes_layout_for(inst, W, resident, chunk,
+                                           lanes_budget(inst, cfg.blocks_per_sm ? cfg.blocks_per_sm : 1));
     LanesArgs a = {};
     a.grec = static_cast<const unsigned char *>(inst->t.grec);
     a.gpairs = inst->t.gpairs;

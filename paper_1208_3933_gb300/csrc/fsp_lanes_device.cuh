@@ -90,12 +90,19 @@ __device__ __forceinline__ void load_sorted_heads(const LanesArgs &a, int2 *hcac
 // (bit b: job j unscheduled in the warp's node b; F holds 32 * ceil(n / 32)
 // words, which first hold the lanes' membership bitmaps), the lane's row
 // (A_k = r_k + S_k as int32, then q_l, see store_q) and the one-machine term
-// max_{l>=1} (A_l + q_l).  Returns whether the row is valid.
-template <int MP>
+// max_{l>=1} (A_l + q_l).  Returns whether the row is valid.  With PS the
+// processing-time rows are read from ptab, the block's shared-memory copy of
+// pp ([n][mpad]), instead of global memory.
+template <int MP, bool PS = false>
 __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int lane, uint32_t *F, int32_t *myrow,
                                             int &bterm, const int2 *hcache = nullptr,
-                                            const int2 *tcache = nullptr) {
+                                            const int2 *tcache = nullptr, const int32_t *ptab = nullptr) {
     const int n = a.n, m = a.m, nw = (n + 31) >> 5;
+    // row q-th int4 of job j's processing times
+    auto prow = [&](int j) {
+        return reinterpret_cast<const int4 *>((PS ? ptab : a.pp) + (size_t)j * a.mpad);
+    };
+    auto pld = [&](const int4 *r, int q) { return PS ? r[q] : __ldg(r + q); };
     bool valid = false;
     int d = 0;
     if (x < a.N) {
@@ -104,8 +111,10 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     }
     // (1) one pass over the prefix.  Membership: each lane marks its node's
     // jobs in a private bitmap (word w of lane L at F[32 w + L], so the 32
-    // lanes never share a word); a job outside [0,n) or marked twice
-    // invalidates the row.  Recurrence: C(sigma,k) by the flow-shop recurrence
+    // lanes never share a word) with an atomic OR whose result is not read,
+    // so the marks form no chain of dependent shared-memory reads; a job
+    // outside [0,n) invalidates the row, and so does a job marked twice,
+    // found afterwards as fewer marked bits than the depth.  Recurrence: C(sigma,k) by the flow-shop recurrence
     // and the prefix column sums, one step max(c + p, C_k + p) = a single
     // fused add-max.  An invalid row still runs the loop on clamped jobs; its
     // result is discarded.
@@ -123,10 +132,8 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     auto mark = [&](int j) {
         const bool inr = (unsigned)j < (unsigned)n;
         const int jj = inr ? j : 0;
-        uint32_t *wp = F + (jj >> 5) * 32 + lane;
-        const uint32_t bit = 1u << (jj & 31), old = *wp;
-        bad |= !inr || (old & bit) != 0u;
-        *wp = old | bit;
+        bad |= !inr;
+        atomicOr(F + (jj >> 5) * 32 + lane, 1u << (jj & 31));
         return jj;
     };
     // four consecutive jobs: machine k of job t needs job t's machine k-1 and
@@ -134,18 +141,18 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     // dependent steps for 20 machines instead of 80) and their processing
     // times are loaded together
     auto take4 = [&](int j0, int j1, int j2, int j3) {
-        const int4 *p0 = reinterpret_cast<const int4 *>(a.pp + (size_t)mark(j0) * a.mpad);
-        const int4 *p1 = reinterpret_cast<const int4 *>(a.pp + (size_t)mark(j1) * a.mpad);
-        const int4 *p2 = reinterpret_cast<const int4 *>(a.pp + (size_t)mark(j2) * a.mpad);
-        const int4 *p3 = reinterpret_cast<const int4 *>(a.pp + (size_t)mark(j3) * a.mpad);
+        const int4 *p0 = prow(mark(j0));
+        const int4 *p1 = prow(mark(j1));
+        const int4 *p2 = prow(mark(j2));
+        const int4 *p3 = prow(mark(j3));
         int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
 #pragma unroll
         for (int q = 0; q < MP / 4; ++q) {
             const bool in = 4 * q < a.mpad;
-            const int4 v0 = in ? __ldg(p0 + q) : make_int4(0, 0, 0, 0);
-            const int4 v1 = in ? __ldg(p1 + q) : make_int4(0, 0, 0, 0);
-            const int4 v2 = in ? __ldg(p2 + q) : make_int4(0, 0, 0, 0);
-            const int4 v3 = in ? __ldg(p3 + q) : make_int4(0, 0, 0, 0);
+            const int4 v0 = in ? pld(p0, q) : make_int4(0, 0, 0, 0);
+            const int4 v1 = in ? pld(p1, q) : make_int4(0, 0, 0, 0);
+            const int4 v2 = in ? pld(p2, q) : make_int4(0, 0, 0, 0);
+            const int4 v3 = in ? pld(p3, q) : make_int4(0, 0, 0, 0);
             const int q0[4] = {v0.x, v0.y, v0.z, v0.w}, q1[4] = {v1.x, v1.y, v1.z, v1.w};
             const int q2[4] = {v2.x, v2.y, v2.z, v2.w}, q3[4] = {v3.x, v3.y, v3.z, v3.w};
 #pragma unroll
@@ -161,13 +168,12 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
         }
     };
     auto take = [&](int j) {
-        const int jj = mark(j);
-        const int4 *pj = reinterpret_cast<const int4 *>(a.pp + (size_t)jj * a.mpad);
+        const int4 *pj = prow(mark(j));
         int c = 0;
 #pragma unroll
         for (int q = 0; q < MP / 4; ++q) {
             // columns past the instance's own padding read as zeros (no branch)
-            const int4 v = 4 * q < a.mpad ? __ldg(pj + q) : make_int4(0, 0, 0, 0);
+            const int4 v = 4 * q < a.mpad ? pld(pj, q) : make_int4(0, 0, 0, 0);
             const int pv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -192,8 +198,13 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     }
 #pragma unroll 1
     for (; i < dv; ++i) take(__ldg(row + i));
-    valid = valid && !bad;
     __syncwarp();
+    {  // a job marked twice leaves fewer marked bits than the depth
+        int cnt = 0;
+        for (int w = 0; w < nw; ++w) cnt += __popc(F[w * 32 + lane]);
+        bad |= cnt != dv;
+    }
+    valid = valid && !bad;
     // S_k = ptot_k - prefix sum of machine k, kept in the lane's row until
     // A_k = r_k + S_k replaces it
 #pragma unroll
@@ -219,11 +230,11 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
                 while (un) {
                     const int j = w * 32 + __ffs(un) - 1;
                     un &= un - 1u;
-                    const int4 *pj = reinterpret_cast<const int4 *>(a.pp + (size_t)j * a.mpad);
+                    const int4 *pj = prow(j);
                     int est = C[0], prev = 0;
 #pragma unroll
                     for (int q = 0; q < MP / 4; ++q) {
-                        const int4 v = 4 * q < a.mpad ? __ldg(pj + q) : make_int4(0, 0, 0, 0);
+                        const int4 v = 4 * q < a.mpad ? pld(pj, q) : make_int4(0, 0, 0, 0);
                         const int pv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
@@ -259,11 +270,11 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
                 while (un) {
                     const int j = w * 32 + __ffs(un) - 1;
                     un &= un - 1u;
-                    const int4 *pj = reinterpret_cast<const int4 *>(a.pp + (size_t)j * a.mpad);
+                    const int4 *pj = prow(j);
                     int pv[MP];
 #pragma unroll
                     for (int q = 0; q < MP / 4; ++q) {
-                        const int4 v = 4 * q < a.mpad ? __ldg(pj + q) : make_int4(0, 0, 0, 0);
+                        const int4 v = 4 * q < a.mpad ? pld(pj, q) : make_int4(0, 0, 0, 0);
                         pv[4 * q] = v.x;
                         pv[4 * q + 1] = v.y;
                         pv[4 * q + 2] = v.z;
@@ -306,11 +317,30 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     uint32_t open_h = 0, open_t = 0;  // machines still searching (bit k)
     const bool in = lane < n;
     constexpr int CH = kMinimaChunk;
+    // A warp whose nodes all have their minima already (walked, complete or
+    // invalid) skips the list search: round 0 would only confirm them.
+    const bool all_settled = __all_sync(kFull, settled);
+    if (all_settled) {
+#pragma unroll
+        for (int k = 0; k < MP; ++k) {
+            if (k < m) {
+                int mh = 0, ql = 0;
+                if constexpr (MP <= kWalkMaxMP) {
+                    if (walk) {
+                        mh = MH[k];
+                        ql = MQ[k];
+                    }
+                }
+                myrow[k] = (per_job ? R[k] : max(C[k], mh)) + myrow[k];
+                store_q(myrow, m, k, ql, q32);
+            }
+        }
+    }
     // Machines are taken kMinimaChunk at a time: their list entries and flag
     // words are loaded together and their transposes interleaved.
 #pragma unroll
     for (int k0 = 0; k0 < MP; k0 += CH) {
-        if (k0 < m) {
+        if (!all_settled && k0 < m) {
             int2 eh[CH], et[CH];
             uint32_t w[2 * CH];
 #pragma unroll
@@ -401,6 +431,16 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     for (int l = 1; l < m; ++l) bterm = max(bterm, myrow[l] + load_q(myrow, m, l, q32));
     __syncwarp();
     return valid;
+}
+
+// Copies pp ([n][mpad] int32, mpad a multiple of 4) into the block's
+// shared-memory table; every thread of the block takes part, the caller
+// synchronises before the table is read.
+__device__ __forceinline__ void load_ptab(const LanesArgs &a, int32_t *ptab) {
+    const int4 *src = reinterpret_cast<const int4 *>(a.pp);
+    int4 *dst = reinterpret_cast<int4 *>(ptab);
+    const int nq = a.n * a.mpad / 4;
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
 // One slack update of the 32 nodes for a couple-lanes record r (the

@@ -132,6 +132,23 @@ std::vector<fsp_launch_config> candidates(const fsp_instance *inst, int64_t N) {
                     }
             }
     }
+    // small pools: streamed staging with node tiles of 1-4 warps and several
+    // blocks per SM, couple slices of one or two groups
+    if (N < 2 * 32 * 16 * (int64_t)sms)
+        for (int W : {1, 2, 4})
+            for (int bps : {4, 8})
+                for (int pos : {64, 32})
+                    for (int ppt : {32, 64}) {
+                        if (W * bps > 16 || ppt >= inst->P) continue;
+                        fsp_launch_config c = {};
+                        c.kernel = FSP_KERNEL_LANES;
+                        c.staging = FSP_STAGING_STREAMED;
+                        c.warps_per_block = W;
+                        c.blocks_per_sm = bps;
+                        c.positions_per_tile = pos;
+                        c.pairs_per_tile = ppt;
+                        add(c);
+                    }
     // global staging (warps independent, records from L2/L1): node tiles of
     // 1-16 warps, couple slices chosen from the pool size or fixed
     for (int W : {16, 8, 4, 2, 1})

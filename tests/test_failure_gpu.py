@@ -33,8 +33,10 @@ def test_bad_launch_shapes_are_refused(gpu_lib):
     rows, depths = workloads.random_pool(rng, 40, 100, max_depth=41)
     r, d = torch.from_numpy(rows).cuda(), torch.from_numpy(depths).cuda()
     with fsp.Instance(p) as inst:
-        for cfg in (dict(kernel=3), dict(kernel=2, warps_per_block=17), dict(kernel=2, staging=5),
-                    dict(kernel=2, staging=2, positions_per_tile=6), dict(kernel=2, blocks_per_sm=3)):
+        for cfg in (dict(kernel=3), dict(kernel=2, warps_per_block=17), dict(kernel=2, staging=6),
+                    dict(kernel=2, staging=2, positions_per_tile=6), dict(kernel=2, blocks_per_sm=9),
+                    dict(kernel=2, staging=5, warps_per_block=4, blocks_per_sm=5),
+                    dict(kernel=2, staging=1, blocks_per_sm=3), dict(kernel=2, staging=3, blocks_per_sm=3)):
             with pytest.raises(fsp.FspError) as e:
                 fsp.fsp_bound_pool(inst, r, d, config=cfg)
             assert e.value.status == fsp.FSP_EINVAL, cfg
