@@ -53,9 +53,9 @@ __global__ void __launch_bounds__(512, 1)
         const int g0 = S > 1 ? slice * a.gper : 0, G = S > 1 ? min(a.G, g0 + a.gper) : a.G;
         for (int g = g0; g < G; ++g) {
             const int kk = __ldg(a.gpairs + 2 * (g * 32 + lane)), ll = __ldg(a.gpairs + 2 * (g * 32 + lane) + 1);
-            float u[32];
+            int u[32];
 #pragma unroll
-            for (int b = 0; b < 32; ++b) u[b] = 0.f;
+            for (int b = 0; b < 32; ++b) u[b] = 0;
             const uint2 *R = reinterpret_cast<const uint2 *>(a.grec) + (size_t)g * npad * 32 + lane;
             scan_compact_global(R, npad, F, u);
             couple_epilogue<false>(AQ, aq_stride, m, kk, ll, u, lb);

@@ -12,7 +12,7 @@ namespace fspgb {
 // applied, so each load's latency (longer than a shared-memory read's) is
 // covered by the updates before it is needed.
 constexpr int kScanAhead = 4;
-__device__ __forceinline__ void scan_compact_global(const uint2 *R, int npos, const uint32_t *F, float (&u)[32]) {
+__device__ __forceinline__ void scan_compact_global(const uint2 *R, int npos, const uint32_t *F, int (&u)[32]) {
     uint2 buf[kScanAhead];
 #pragma unroll
     for (int t = 0; t < kScanAhead; ++t) buf[t] = t < npos ? __ldg(R + t * 32) : make_uint2(0u, 0u);

@@ -407,6 +407,14 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
         c.blocks_per_sm > (c.staging == FSP_STAGING_GLOBAL ? 16 : 8) || c.pairs_per_tile < 0 || c.tail_slices < 0)
         return FSP_EINVAL;
     const int G = inst->G;
+    // nodes per warp (nodes_per_thread for this kernel): 32, or 56 in two
+    // sets of 28 (streamed staging, compact records)
+    const int sets = lanes_node_sets(c);
+    if (!sets) return FSP_EINVAL;
+    if (sets == 2 && ((c.staging && c.staging != FSP_STAGING_STREAMED) || !inst->compact || c.tail_slices > 1))
+        return FSP_EINVAL;
+    const int npw = sets == 2 ? 56 : 32;
+    c.nodes_per_thread = npw;
     if (c.staging == FSP_STAGING_GLOBAL) {
         // Warps independent, records from L2/L1: every work item (a 32-node
         // batch and a slice of the couples) gets a warp of its own when the
@@ -506,7 +514,7 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     };
     auto model_time = [&](int W, int gper) {
         const int64_t slots = (int64_t)d.num_sms * c.blocks_per_sm;
-        const int64_t batches = (std::max<int64_t>(N, 1) + 32 * W - 1) / (32 * W);
+        const int64_t batches = (std::max<int64_t>(N, 1) + (int64_t)npw * W - 1) / ((int64_t)npw * W);
         const double occ = std::max(W * c.blocks_per_sm, 16) * (c.blocks_per_sm == 1 ? 1.2 : 1.0);
         if (gper < G) {
             const double items = (double)batches * std::ceil((double)G / gper);

@@ -13,12 +13,11 @@
 // over all couples for node b, combined with the one-machine terms
 // max_l (A_l + q_l).
 //
-// With compact records (two fp32 words: s carrying the job in its low
-// mantissa bits, and delta) every slack is an integer below 2^24 plus a
-// fraction below 1 (fsp_lanes_device.cuh), so the scan runs in fp32: the add
-// goes to the FMA pipe and only the max to the integer ALU pipe, and the
-// truncated result is exact.  128-bit records (large processing times) use
-// the int32 path.
+// With compact records (two int32 words: 1024 s + j and 1024 delta) the scan
+// keeps every slack scaled by 1024 with a job in its low bits and runs one
+// fused integer add-max per entry (fsp_lanes_device.cuh); the epilogue's
+// shift by 10 gives the exact integer slack.  128-bit records (large
+// processing times) use the plain int32 path.
 //
 // Per node the shared memory holds one flag bit per job and a row with A_k
 // (int32) and q_l (int16 with compact records, whose tails stay below 2^15;
@@ -110,9 +109,9 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) 
         for (int g = 0; g < a.G; ++g) {
             const int kk = sgp[2 * (g * 32 + lane)], ll = sgp[2 * (g * 32 + lane) + 1];
             if (!WIDE) {
-                float u[32];
+                int u[32];
 #pragma unroll
-                for (int b = 0; b < 32; ++b) u[b] = 0.f;
+                for (int b = 0; b < 32; ++b) u[b] = 0;
                 scan_compact(reinterpret_cast<const uint2 *>(tables + g * group_bytes) + lane, a.npad, F, u);
                 couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, u, lb);
             } else {
@@ -189,12 +188,12 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
         int bterm = 0;
         const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
         int lb[32];
-        float uf[32];
+        int uf[32];
         int ui[32];
 #pragma unroll
         for (int b = 0; b < 32; ++b) {
             lb[b] = 0;
-            uf[b] = 0.f;
+            uf[b] = 0;
             ui[b] = 0;
         }
         int kk = 0, ll = 1;
@@ -218,7 +217,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
             if (ch == 0) {
 #pragma unroll
                 for (int b = 0; b < 32; ++b) {
-                    uf[b] = 0.f;
+                    uf[b] = 0;
                     ui[b] = 0;
                 }
                 kk = sgp[2 * (g * 32 + lane)];
@@ -248,6 +247,140 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
                 a.out[x] = FSP_LB_INVALID;  // every slice finds the row invalid
             else
                 atomicMax(a.out + x, max(best, bterm));  // out was zeroed; bounds are >= 0
+        }
+        __syncwarp();  // the flag and row arrays are rewritten by the next batch
+    }
+}
+
+// ------------------------------------------------------ streamed, two sets
+// The streamed kernel with two node sets of 28 per warp (compact records):
+// a block batch is 56 W nodes; every record read serves 56 nodes, and each
+// flag word yields its 28 predicates from four byte-wise conversions.  A
+// warp sets up its two sets one after the other (lane = node, lanes 7, 15,
+// 23 and 31 idle), and the couple values of each group are reduced over the
+// lanes at once, so no per-node maxima are carried across groups.
+template <int MP>
+__global__ void __launch_bounds__(512, 1) fsp_lanes_streamed2(const LanesArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint8_t *sgp = smem + 16;
+    int2 *hcache = reinterpret_cast<int2 *>(smem + a.off_cache);
+    int2 *tcache = hcache + a.m * 32;
+    const int nfw = flag_words(a.n);
+    uint32_t *F0 = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * 2 * nfw;
+    uint32_t *F1 = F0 + nfw;
+    int32_t *AQ0 = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 2 * 32 * a.aq_stride;
+    int32_t *AQ1 = AQ0 + 32 * a.aq_stride;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    for (int i = threadIdx.x; i < a.G * 64; i += blockDim.x) sgp[i] = a.gpairs[i];
+    load_sorted_heads(a, hcache, tcache);
+    __syncthreads();
+
+    TilePipe tp{bar, smem + a.off_tables, a.tile_stride, a.ntiles <= 2};
+    auto tile_issue = [&](uint32_t fill, int t) {
+        const int g = t / a.nchunks, ch = t - g * a.nchunks;
+        const int pos = min(a.chunk, a.npad - ch * a.chunk);
+        const unsigned char *src = a.grec + ((size_t)g * a.npad + (size_t)ch * a.chunk) * 32 * a.rec_bytes;
+        tp.issue(fill, src, (uint32_t)pos * 32u * a.rec_bytes);
+    };
+    // work items as in fsp_lanes_streamed, block batches of 56 W nodes
+    const uint32_t S = a.gslices > 1 ? (uint32_t)a.gslices : 1u;
+    const int64_t full = S > 1 ? a.full_batches : a.num_batches;
+    const int gper = S > 1 ? a.gper : a.G;
+    const int64_t items = full + (a.num_batches - full) * S;
+    auto slice_of = [&](int64_t it) { return it < full ? -1 : (int)((uint32_t)(it - full) % S); };
+    auto first_tile = [&](int sl) { return sl < 0 ? 0 : sl * gper * a.nchunks; };
+    if (threadIdx.x == 0 && (int64_t)blockIdx.x < items) {
+        if (tp.resident) {
+            tile_issue(0, 0);
+            if (a.ntiles == 2) tile_issue(1, 1);
+        } else {
+            tile_issue(0, first_tile(slice_of(blockIdx.x)));
+        }
+    }
+    // lane -> node of each set: lanes 7, 15, 23, 31 hold no node
+    const bool real = (kSet28 >> lane) & 1u;
+    const int r28 = set28_slot(lane);
+
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int sl = slice_of(it);
+        const int64_t bt = sl < 0 ? it : full + (int64_t)((uint32_t)(it - full) / S);
+        const int64_t base = bt * (int64_t)(56 * W) + warp * 56;
+        const int64_t x0 = real ? node_at(a, base + r28) : a.N;
+        const int64_t x1 = real ? node_at(a, base + 28 + r28) : a.N;
+        bool valid0 = false, valid1 = false;
+        int bterm0 = 0, bterm1 = 0;
+#pragma unroll 1
+        for (int set = 0; set < 2; ++set) {
+            int bt_ = 0;
+            const bool v = lanes_setup<MP>(a, set ? x1 : x0, lane, set ? F1 : F0,
+                                           (set ? AQ1 : AQ0) + lane * a.aq_stride, bt_, hcache, tcache);
+            if (set) {
+                valid1 = v;
+                bterm1 = bt_;
+            } else {
+                valid0 = v;
+                bterm0 = bt_;
+            }
+        }
+        int M0 = 0, M1 = 0;
+        int u[56];
+#pragma unroll
+        for (int b = 0; b < 56; ++b) u[b] = 0;
+        int kk = 0, ll = 1;
+        const int t1 = sl < 0 ? a.ntiles : min(a.G, (sl + 1) * gper) * a.nchunks;
+        for (int t = first_tile(sl); t < t1; ++t) {
+            const int g = t / a.nchunks, ch = t - g * a.nchunks;
+            if (!tp.resident && threadIdx.x == 0) {
+                const int next = t + 1 < t1 ? t + 1
+                                 : (it + gridDim.x < items ? first_tile(slice_of(it + gridDim.x)) : -1);
+                if (next >= 0) tile_issue(tp.fill + 1, next);
+            }
+            if (!tp.wait(t, a.wait_limit)) {
+                if (threadIdx.x == 0) {
+                    report_status(a.status, (int32_t)FSP_ETIMEDOUT);
+                    tp.drain(a.wait_limit);
+                }
+                return;
+            }
+            const unsigned char *tb = tp.buf + tp.current(t) * tp.stride;
+            if (ch == 0) {
+#pragma unroll
+                for (int b = 0; b < 56; ++b) u[b] = 0;
+                kk = sgp[2 * (g * 32 + lane)];
+                ll = sgp[2 * (g * 32 + lane) + 1];
+            }
+            const int npos = min(a.chunk, a.npad - ch * a.chunk);
+            scan_compact2(reinterpret_cast<const uint2 *>(tb) + lane, npos, F0, F1, u);
+            if (ch == a.nchunks - 1) {
+                M0 = max(M0, set28_group_max<0>(AQ0, a.aq_stride, a.m, kk, ll, u, lane));
+                M1 = max(M1, set28_group_max<28>(AQ1, a.aq_stride, a.m, kk, ll, u, lane));
+            }
+            if (!tp.resident) {
+                __syncthreads();
+                ++tp.fill;
+            }
+        }
+#pragma unroll
+        for (int set = 0; set < 2; ++set) {
+            const int64_t x = set ? x1 : x0;
+            const bool valid = set ? valid1 : valid0;
+            const int best = max(set ? M1 : M0, set ? bterm1 : bterm0);
+            if (x < a.N) {
+                if (sl < 0)
+                    a.out[x] = valid ? best : FSP_LB_INVALID;
+                else if (!valid)
+                    a.out[x] = FSP_LB_INVALID;  // every slice finds the row invalid
+                else
+                    atomicMax(a.out + x, best);  // out was zeroed; bounds are >= 0
+            }
         }
         __syncwarp();  // the flag and row arrays are rewritten by the next batch
     }
@@ -288,9 +421,9 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_global(const LanesArgs a) {
         const int g0 = S > 1 ? sl * a.gper : 0, g1 = S > 1 ? min(a.G, g0 + a.gper) : a.G;
         for (int g = g0; g < g1; ++g) {
             const int kk = __ldg(a.gpairs + 2 * (g * 32 + lane)), ll = __ldg(a.gpairs + 2 * (g * 32 + lane) + 1);
-            float u[32];
+            int u[32];
 #pragma unroll
-            for (int b = 0; b < 32; ++b) u[b] = 0.f;
+            for (int b = 0; b < 32; ++b) u[b] = 0;
             const uint2 *R = reinterpret_cast<const uint2 *>(a.grec) + (size_t)g * a.npad * 32 + lane;
             scan_compact_global(R, a.npad, F, u);
             couple_epilogue<false>(AQ, a.aq_stride, a.m, kk, ll, u, lb);
@@ -339,7 +472,9 @@ void add_ptab(LanesLayout &L, const fsp_instance *inst, size_t budget) {
 // ints per node row: A_k as int32, then q_l as int16 (compact records) or int32
 int aq_stride_for(int m, bool q32) { return (m + (q32 ? m : (m + 1) / 2)) | 1; }
 
-LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident, int chunk, size_t budget) {
+// sets: node sets per warp (1: 32 nodes; 2: two sets of 28, streamed only)
+LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident, int chunk, size_t budget,
+                             int sets = 1) {
     LanesLayout L = {};
     L.off_cache = (uint32_t)align_up(16 + (size_t)inst->G * 64, 128);
     L.off_tables = (uint32_t)align_up(L.off_cache + (size_t)inst->m * 32 * 8 * 2, 128);
@@ -351,9 +486,9 @@ LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident,
         L.tile_stride = (uint32_t)align_up((size_t)chunk * 32 * inst->grec_bytes, 128);
         L.off_flags = L.off_tables + 2 * L.tile_stride;
     }
-    L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)warps * flag_words(inst->n) * 4, 128);
+    L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)warps * sets * flag_words(inst->n) * 4, 128);
     L.aq_stride = aq_stride_for(inst->m, !inst->compact);
-    L.total = align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
+    L.total = align_up(L.off_aq + (size_t)warps * sets * 32 * L.aq_stride * 4, 128);
     (void)budget;  // the tiled kernels read the processing times from global memory
     return L;
 }
@@ -367,33 +502,36 @@ cudaError_t set_smem_attr(K kernel) {
 }
 
 template <bool WIDE, int MP>
-cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int grid, int threads, size_t smem,
+cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int sets, int grid, int threads, size_t smem,
                                  cudaStream_t s) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
         attr_err = set_smem_attr(fsp_lanes_resident<WIDE, MP>);
         if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP>);
+        if (!WIDE && attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed2<MP>);
     });
     if (attr_err != cudaSuccess) return attr_err;
     note_launches(1);
     if (resident)
         fsp_lanes_resident<WIDE, MP><<<grid, threads, smem, s>>>(a);
+    else if (!WIDE && sets == 2)
+        fsp_lanes_streamed2<MP><<<grid, threads, smem, s>>>(a);
     else
         fsp_lanes_streamed<WIDE, MP><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <bool WIDE>
-cudaError_t launch_lanes_mp(const LanesArgs &a, int mp, bool resident, int grid, int threads, size_t smem,
+cudaError_t launch_lanes_mp(const LanesArgs &a, int mp, bool resident, int sets, int grid, int threads, size_t smem,
                             cudaStream_t s) {
     switch (mp) {
-        case 8: return launch_lanes_variant<WIDE, 8>(a, resident, grid, threads, smem, s);
-        case 12: return launch_lanes_variant<WIDE, 12>(a, resident, grid, threads, smem, s);
-        case 16: return launch_lanes_variant<WIDE, 16>(a, resident, grid, threads, smem, s);
-        case 20: return launch_lanes_variant<WIDE, 20>(a, resident, grid, threads, smem, s);
-        case 24: return launch_lanes_variant<WIDE, 24>(a, resident, grid, threads, smem, s);
-        default: return launch_lanes_variant<WIDE, 32>(a, resident, grid, threads, smem, s);
+        case 8: return launch_lanes_variant<WIDE, 8>(a, resident, sets, grid, threads, smem, s);
+        case 12: return launch_lanes_variant<WIDE, 12>(a, resident, sets, grid, threads, smem, s);
+        case 16: return launch_lanes_variant<WIDE, 16>(a, resident, sets, grid, threads, smem, s);
+        case 20: return launch_lanes_variant<WIDE, 20>(a, resident, sets, grid, threads, smem, s);
+        case 24: return launch_lanes_variant<WIDE, 24>(a, resident, sets, grid, threads, smem, s);
+        default: return launch_lanes_variant<WIDE, 32>(a, resident, sets, grid, threads, smem, s);
     }
 }
 
@@ -446,6 +584,11 @@ cudaError_t launch_global_mp(const LanesArgs &a, int mp, int grid, int threads, 
 
 }  // namespace
 
+int lanes_node_sets(const fsp_launch_config &c) {
+    if (c.nodes_per_thread == 0 || c.nodes_per_thread == 32) return 1;
+    return c.nodes_per_thread == 56 ? 2 : 0;
+}
+
 int lanes_groups_per_item(const fsp_instance *inst, int pairs_per_tile) {
     if (pairs_per_tile <= 0 || pairs_per_tile >= inst->P) return inst->G;
     return std::min(inst->G, (pairs_per_tile + 31) / 32);
@@ -470,9 +613,12 @@ fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, si
     // pools), 2 otherwise
     if (W < 1 || W > 16 || bps < 1 || bps > (resident ? 2 : 8) || W * bps > 16) return FSP_EINVAL;
     if (!resident && (c.positions_per_tile < 4 || (c.positions_per_tile & 3))) return FSP_EINVAL;
+    // nodes per warp: 32, or 56 (two sets of 28: streamed staging, compact records)
+    const int sets = lanes_node_sets(c);
+    if (sets < 1 || (sets == 2 && (resident || !inst->compact))) return FSP_EINVAL;
     const int chunk = resident ? inst->npad : std::min(c.positions_per_tile, inst->npad);
     const size_t budget = lanes_budget(inst, bps);
-    const LanesLayout L = lanes_layout_for(inst, W, resident, chunk, budget);
+    const LanesLayout L = lanes_layout_for(inst, W, resident, chunk, budget, sets);
     if (L.total > budget) return FSP_EINVAL;
     // the resident copy completes on one mbarrier: its byte count must fit the transaction counter
     if (resident && (size_t)inst->npad * 32 * inst->grec_bytes * inst->G >= (1u << 20)) return FSP_EINVAL;
@@ -544,8 +690,10 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     const int W = cfg.warps_per_block;
     const bool resident = cfg.staging == FSP_STAGING_RESIDENT;
     const int chunk = resident ? inst->npad : std::min(cfg.positions_per_tile, inst->npad);
+    const int sets = lanes_node_sets(cfg);
+    const int npw = sets == 2 ? 56 : 32;  // nodes per warp
     const LanesLayout L = lanes_layout_for(inst, W, resident, chunk,
-                                           lanes_budget(inst, cfg.blocks_per_sm ? cfg.blocks_per_sm : 1));
+                                           lanes_budget(inst, cfg.blocks_per_sm ? cfg.blocks_per_sm : 1), sets);
     LanesArgs a = {};
     a.grec = static_cast<const unsigned char *>(inst->t.grec);
     a.gpairs = inst->t.gpairs;
@@ -583,7 +731,7 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
         const int64_t per_block = std::max<int64_t>(1, W);
         grid = (int)std::min<int64_t>((a.num_batches + per_block - 1) / per_block, (int64_t)num_sms(inst->device));
     } else {
-        a.num_batches = (N + 32 * W - 1) / (32 * W);
+        a.num_batches = (N + (int64_t)npw * W - 1) / ((int64_t)npw * W);
         const int bps = cfg.blocks_per_sm ? cfg.blocks_per_sm : 1;
         const int64_t slots = (int64_t)num_sms(inst->device) * bps;
         a.gper = lanes_groups_per_item(inst, cfg.pairs_per_tile);
@@ -609,8 +757,8 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     st = depth_order(inst, depths, N, s, &order);
     if (st != FSP_OK) return st;
     a.order = order;
-    const cudaError_t e = inst->compact ? launch_lanes_mp<false>(a, inst->mpad, resident, grid, 32 * W, smem, s)
-                                        : launch_lanes_mp<true>(a, inst->mpad, resident, grid, 32 * W, smem, s);
+    const cudaError_t e = inst->compact ? launch_lanes_mp<false>(a, inst->mpad, resident, sets, grid, 32 * W, smem, s)
+                                        : launch_lanes_mp<true>(a, inst->mpad, resident, sets, grid, 32 * W, smem, s);
     const cudaError_t ef = order ? cudaFreeAsync(order, s) : cudaSuccess;
     return (e == cudaSuccess && ef == cudaSuccess) ? FSP_OK : FSP_ECUDA;
 }

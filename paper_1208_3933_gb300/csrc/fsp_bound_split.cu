@@ -140,12 +140,12 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_scan(const LanesArgs a) {
         const int bterm = (int)F[a.n + rows_words + lane];
         const int xid = (int)F[a.n + rows_words + 32 + lane];
         int lb[32];
-        float uf[32];
+        int uf[32];
         int ui[32];
 #pragma unroll
         for (int b = 0; b < 32; ++b) {
             lb[b] = 0;
-            uf[b] = 0.f;
+            uf[b] = 0;
             ui[b] = 0;
         }
         int kk = 0, ll = 1;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_scan(const LanesArgs a) {
             if (ch == 0) {
 #pragma unroll
                 for (int b = 0; b < 32; ++b) {
-                    uf[b] = 0.f;
+                    uf[b] = 0;
                     ui[b] = 0;
                 }
                 kk = sgp[2 * (g * 32 + lane)];

@@ -91,12 +91,12 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_warp(const LanesArgs a, uint
         int bterm = 0;
         const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
         int lb[32];
-        float uf[32];
+        int uf[32];
         int ui[32];
 #pragma unroll
         for (int b = 0; b < 32; ++b) {
             lb[b] = 0;
-            uf[b] = 0.f;
+            uf[b] = 0;
             ui[b] = 0;
         }
         int kk = 0, ll = 1;
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_warp(const LanesArgs a, uint
             if (ch == 0) {
 #pragma unroll
                 for (int b = 0; b < 32; ++b) {
-                    uf[b] = 0.f;
+                    uf[b] = 0;
                     ui[b] = 0;
                 }
                 kk = sgp[2 * (g * 32 + lane)];

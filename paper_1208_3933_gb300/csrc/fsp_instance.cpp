@@ -143,18 +143,13 @@ extern "C" fsp_status fsp_instance_create_ex(const int32_t *p, int32_t n, int32_
         for (int i = 0; i < npad; ++i) {
             const size_t dst = ((size_t)g * npad + i) * 32 + lane;
             if (inst->compact) {
-                // couple-lanes encoding: word 0 = the bits of float(s) with the
-                // job in its lowest 10 mantissa bits (s < 2^13 leaves the lowest
-                // 11 bits zero), word 1 = the bits of float(delta)
+                // couple-lanes encoding: word 0 = 1024 s + j, word 1 =
+                // 1024 delta (two's complement), both used by the scan as they are
                 const uint32_t r = rec_c[(size_t)c * npad + i];
                 const uint32_t j = r & 1023u, sv = (r >> 10) & 8191u;
                 const int32_t dv = (int32_t)r >> 23;
-                const float sf = (float)sv, df = (float)dv;
-                uint32_t sb, db;
-                std::memcpy(&sb, &sf, 4);
-                std::memcpy(&db, &df, 4);
-                grec_c[2 * dst] = sb | j;
-                grec_c[2 * dst + 1] = db;
+                grec_c[2 * dst] = (sv << 10) | j;
+                grec_c[2 * dst + 1] = (uint32_t)(dv * 1024);
             }
             else
                 for (int f = 0; f < 4; ++f) grec_w[dst * 4 + f] = rec_w[((size_t)c * npad + i) * 4 + f];

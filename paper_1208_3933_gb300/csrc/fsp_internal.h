@@ -31,11 +31,12 @@
 //   bits  0..9   j
 //   bits 10..22  s
 //   bits 23..31  delta (two's complement)
-// The couple-lanes copy (grec) stores each compact record as two words the
-// scan uses directly: word 0 = the bits of float(s) with j in its lowest 10
-// mantissa bits (s < 2^13 leaves at least 11 of them zero, so the job adds
-// less than 1/2 to s), word 1 = the bits of float(delta); the no-op record
-// (padding, empty couples) is (0, 0).
+// The couple-lanes copy (grec) stores each compact record as two int32 words
+// the scan uses directly: word 0 = 1024 s + j, word 1 = 1024 delta.  The scan
+// keeps the slack scaled by 1024 with a job in its low 10 bits (a fraction
+// below one unit) and runs one fused integer add-max per entry; with
+// s < 2^13, |delta| <= 256 and n <= 1024 every scaled value stays below
+// 2^29.  The no-op record (padding, empty couples) is (0, 0).
 // Wide record: int4 {j, s, delta, 0}.
 // Padding entries and empty couples are all-zero records: for any u >= 0,
 // max(u + 0, 0) = u, so they never change the result, and an empty couple
@@ -112,6 +113,9 @@ fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &cfg, 
 // Couple groups of 32 per streamed work item for a requested pairs_per_tile
 // (0 or >= P: all G groups; else rounded up to whole groups).
 int lanes_groups_per_item(const fsp_instance *inst, int pairs_per_tile);
+// Node sets per warp of a couple-lanes shape (its nodes_per_thread field: 0 or
+// 32 -> 1 set of 32 nodes, 56 -> 2 sets of 28; anything else -> 0, invalid).
+int lanes_node_sets(const fsp_launch_config &c);
 fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
                         int32_t *out_lb, void *stream, const fsp_launch_config &cfg);
 // The same bound as a prep kernel and a scan kernel (fsp_bound_split.cu).

@@ -444,24 +444,24 @@ __device__ __forceinline__ void load_ptab(const LanesArgs &a, int32_t *ptab) {
 }
 
 // One slack update of the 32 nodes for a couple-lanes record r (the
-// two-word encoding of fsp_internal.h): r.x is float(s) carrying the job in
-// its lowest 10 mantissa bits, r.y is float(delta); then u_b = max(u_b +
-// delta, s) for every node b whose flag bit for that job is set.  The job
-// bits add less than 1/2 to s, and a max never adds them up (only delta,
-// exact, is added), so every u_b is its integer value plus a fraction below
-// 1: the integer parts follow the integer recurrence exactly and the
-// epilogue truncates.
-__device__ __forceinline__ void lanes_step(uint2 r, const uint32_t *F, float (&u)[32]) {
+// two-word encoding of fsp_internal.h): r.x is 1024 s + j, r.y is
+// 1024 delta; then u_b = max(u_b + 1024 delta, 1024 s + j) for every node b
+// whose flag bit for job j is set, one fused integer add-max.  The slack is
+// thus kept as 1024 u plus the job bits of the last record that won a max:
+// a sum only ever adds 1024 delta, which keeps those low bits, and a max of
+// two such values decides as their integer parts do (or ties on them), so
+// u_b >> 10 follows the integer recurrence exactly.
+__device__ __forceinline__ void lanes_step(uint2 r, const uint32_t *F, int (&u)[32]) {
     const uint32_t fw = F[r.x & 1023u];
-    const float sf = __uint_as_float(r.x), df = __uint_as_float(r.y);
+    const int sv = (int)r.x, dv = (int)r.y;
 #pragma unroll
     for (int b = 0; b < 32; ++b)
-        if ((fw >> b) & 1u) u[b] = fmaxf(u[b] + df, sf);
+        if ((fw >> b) & 1u) u[b] = __viaddmax_s32(u[b], dv, sv);
 }
 
 // One couple group's scan over positions [0, npos) of a record tile (lane =
-// couple): fp32 slack for two-word records, int32 for 128-bit records.
-__device__ __forceinline__ void scan_compact(const uint2 *R, int npos, const uint32_t *F, float (&u)[32]) {
+// couple): scaled slack for two-word records, plain int32 for 128-bit ones.
+__device__ __forceinline__ void scan_compact(const uint2 *R, int npos, const uint32_t *F, int (&u)[32]) {
 #pragma unroll 2
     for (int i = 0; i < npos; ++i) lanes_step(R[i * 32], F, u);
 }
@@ -477,16 +477,17 @@ __device__ __forceinline__ void scan_wide(const int4 *R, int npos, const uint32_
     }
 }
 
-// A lane's couple values A_k + q_l + u_b folded into lb; Q32 says how the
-// rows hold q (store_q): int32 with 128-bit records, int16 with compact ones.
-template <bool Q32, typename U>
-__device__ __forceinline__ void couple_epilogue(const int32_t *AQ, int stride, int m, int kk, int ll, const U (&u)[32],
-                                                int (&lb)[32]) {
+// A lane's couple values A_k + q_l + u_b folded into lb.  Q32 marks 128-bit
+// records: their rows hold q as int32 (store_q) and their slack is plain;
+// compact records keep q as int16 and the slack scaled by 1024 (lanes_step).
+template <bool Q32>
+__device__ __forceinline__ void couple_epilogue(const int32_t *AQ, int stride, int m, int kk, int ll,
+                                                const int (&u)[32], int (&lb)[32]) {
 #pragma unroll
     for (int b = 0; b < 32; ++b) {
         const int32_t *rb = AQ + b * stride;
         const int base = rb[kk] + load_q(rb, m, ll, Q32);
-        lb[b] = max(lb[b], base + (int)u[b]);
+        lb[b] = max(lb[b], base + (Q32 ? u[b] : (u[b] >> 10)));
     }
 }
 
@@ -505,6 +506,57 @@ __device__ __forceinline__ int transpose_max(int (&lb)[32], int lane) {
     return lb[0];
 }
 
+
+
+// Two node sets per warp, 28 nodes each (flag bits 7, 15, 23 and 31 unused):
+// the 28 predicates of a flag word come from the low seven bits of its four
+// bytes, which the hardware turns into predicates a byte at a time, and one
+// record and one job index serve 56 nodes.  Bit b (b & 7 != 7) of a set's
+// flag word is its node set28_slot(b) in 0..27.
+constexpr uint32_t kSet28 = 0x7f7f7f7fu;
+__host__ __device__ constexpr int set28_slot(int b) { return b - (b >> 3); }
+
+// lanes_step for the two sets: F0 and F1 are their flag words, u[0..27] and
+// u[28..55] their slacks.
+__device__ __forceinline__ void lanes_step2(uint2 r, const uint32_t *F0, const uint32_t *F1, int (&u)[56]) {
+    const uint32_t j = r.x & 1023u;
+    const uint32_t f0 = F0[j], f1 = F1[j];
+    const int sv = (int)r.x, dv = (int)r.y;
+#pragma unroll
+    for (int b = 0; b < 32; ++b)
+        if ((kSet28 >> b) & 1u)
+            if ((f0 >> b) & 1u) u[set28_slot(b)] = __viaddmax_s32(u[set28_slot(b)], dv, sv);
+#pragma unroll
+    for (int b = 0; b < 32; ++b)
+        if ((kSet28 >> b) & 1u)
+            if ((f1 >> b) & 1u) u[28 + set28_slot(b)] = __viaddmax_s32(u[28 + set28_slot(b)], dv, sv);
+}
+
+__device__ __forceinline__ void scan_compact2(const uint2 *R, int npos, const uint32_t *F0, const uint32_t *F1,
+                                              int (&u)[56]) {
+#pragma unroll 2
+    for (int i = 0; i < npos; ++i) lanes_step2(R[i * 32], F0, F1, u);
+}
+
+// One couple group's values A_k + q_l + u of the 28-node set whose slacks
+// start at u[OFF], reduced over the warp's lanes (couples): lane b receives
+// the maximum for the set's node in bit b (0 in the unused lanes).  Compact
+// records only (int16 latencies, slack scaled by 1024).
+template <int OFF>
+__device__ __forceinline__ int set28_group_max(const int32_t *AQ, int stride, int m, int kk, int ll,
+                                               const int (&u)[56], int lane) {
+    int v[32];
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+        if ((kSet28 >> b) & 1u) {
+            const int32_t *rb = AQ + b * stride;
+            v[b] = rb[kk] + load_q(rb, m, ll, false) + (u[OFF + set28_slot(b)] >> 10);
+        } else {
+            v[b] = 0;
+        }
+    }
+    return transpose_max(v, lane);
+}
 
 
 }  // namespace fspgb

@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(512, 1)
         for (int b = 0; b < 32; ++b) lb[b] = 0;
         for (int g = 0; g < a.G; ++g) {
             const int kk = __ldg(a.gpairs + 2 * (g * 32 + lane)), ll = __ldg(a.gpairs + 2 * (g * 32 + lane) + 1);
-            float u[32];
+            int u[32];
 #pragma unroll
-            for (int b = 0; b < 32; ++b) u[b] = 0.f;
+            for (int b = 0; b < 32; ++b) u[b] = 0;
             const uint2 *R = reinterpret_cast<const uint2 *>(a.grec) + (size_t)g * a.npad * 32 + lane;
             scan_compact_global(R, a.npad, F, u);
             couple_epilogue<false>(AQ, aq_stride, a.m, kk, ll, u, lb);

@@ -137,6 +137,60 @@ def test_global_staging_matches_oracle(gpu_lib, ppt, W, bps, nm):
     assert got[3] == got[50] == got[7] == fsp.FSP_LB_INVALID
 
 
+@pytest.mark.parametrize("ppt", [0, 32, 96, 1000])
+@pytest.mark.parametrize("W,bps,positions", [(1, 0, 12), (4, 2, 0), (3, 1, 64), (6, 1, 96)])
+@pytest.mark.parametrize("nm", [(40, 20), (70, 12), (33, 27), (23, 9), (200, 20)])
+def test_two_node_sets_per_warp_match_oracle(gpu_lib, ppt, W, bps, positions, nm):
+    """Streamed staging with 56 nodes per warp (two sets of 28, flag bits 7,
+    15, 23 and 31 unused): block batches of 56 W nodes with a ragged last
+    batch, couple slices (0 = chosen from the pool size) combined by atomic
+    max, record tiles of 12, 64 or 96 positions or whole groups, and invalid
+    rows in either set."""
+    fsp = gpu_lib
+    n, m = nm
+    p, rows, depths = pool(900 + n + m, n, m, 56 * W * 5 + 23)
+    depths[[3, 50, 40]] = [-1, n + 1, n + 2]
+    rows[7, :2] = [5, 5]
+    depths[7] = max(int(depths[7]), 2)
+    cfg = dict(kernel=2, staging=2, nodes_per_thread=56, warps_per_block=W, blocks_per_sm=bps,
+               positions_per_tile=positions, pairs_per_tile=ppt)
+    with fsp.Instance(p) as inst:
+        got = gpu_bounds(fsp, inst, rows, depths, config=cfg)
+    want = oracle_bounds(p, rows, depths)
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+    assert got[3] == got[50] == got[40] == got[7] == fsp.FSP_LB_INVALID
+
+
+def test_two_node_sets_depth_order_release_and_refusals(gpu_lib):
+    """56 nodes per warp on a depth-ordered pool (n >= 64, N >= 8,192) and with
+    per-job release times; refused with 128-bit records and outside streamed
+    staging."""
+    fsp = gpu_lib
+    w = workloads.named_pool("pool_200x20", N=9000)
+    idx = np.random.default_rng(6).choice(w.N, 300, replace=False)
+    two = dict(kernel=2, staging=2, nodes_per_thread=56, warps_per_block=4, blocks_per_sm=2, positions_per_tile=96)
+    with fsp.Instance(w.p) as inst:
+        a = gpu_bounds(fsp, inst, w.rows, w.depths, config=two)
+        b = gpu_bounds(fsp, inst, w.rows, w.depths, config=dict(kernel=2, staging=2, warps_per_block=8))
+        assert np.array_equal(a, b)
+        assert np.array_equal(a[idx], oracle_bounds(w.p, w.rows[idx], w.depths[idx]))
+        r, d = to_dev(w.rows[:100], w.depths[:100])
+        for bad in (dict(two, staging=1), dict(two, staging=3), dict(two, staging=5), dict(two, nodes_per_thread=40),
+                    dict(two, tail_slices=2)):
+            with pytest.raises(fsp.FspError):
+                fsp.fsp_bound_pool(inst, r, d, config=bad)
+    with fsp.Instance(w.p, flags=fsp.FSP_INSTANCE_RELEASE_PER_JOB) as inst:
+        got = gpu_bounds(fsp, inst, w.rows[:3000], w.depths[:3000], config=two)
+    want = oracle.Tables(w.p).lb_pool(w.rows[:3000], w.depths[:3000], threads=THREADS, release=oracle.RELEASE_EST)
+    assert np.array_equal(got, want)
+    p, rows, depths = pool(9, 45, 11, 170, hi=20000)
+    with fsp.Instance(p) as inst:
+        r, d = to_dev(rows, depths)
+        with pytest.raises(fsp.FspError):
+            fsp.fsp_bound_pool(inst, r, d, config=dict(kernel=2, staging=2, nodes_per_thread=56, warps_per_block=2,
+                                                       positions_per_tile=8))
+
+
 def test_global_staging_depth_order_release_and_refusals(gpu_lib):
     """Global staging on a depth-ordered pool (n >= 64, N >= 8,192), sliced
     and whole, with per-job release times; refused for 128-bit records and
@@ -555,9 +609,10 @@ def _every_path(fsp, inst, rows, depths):
             dict(kernel=1, nodes_per_thread=2)]
     if info.flags:
         cfgs.pop()  # per-job release times: couple-lanes kernels only
-    if info.compact:  # global staging reads two-word records only
+    if info.compact:  # global staging and two node sets per warp take two-word records only
         cfgs += [dict(kernel=2, staging=5, warps_per_block=4), dict(kernel=2, staging=5, warps_per_block=1,
-                                                                    pairs_per_tile=32)]
+                                                                    pairs_per_tile=32),
+                 dict(kernel=2, staging=2, nodes_per_thread=56, warps_per_block=3, positions_per_tile=64)]
     out = {str(c): gpu_bounds(fsp, inst, rows, depths, config=c) for c in cfgs}
     if info.compact:
         r, d = to_dev(rows, depths)
@@ -573,18 +628,18 @@ def _every_path(fsp, inst, rows, depths):
 
 
 @pytest.mark.parametrize("case", ["p200to255", "all255", "all255_per_job"])
-def test_fp32_scan_exact_at_its_limits(gpu_lib, case):
-    """The two-word records of compact instances carry the job in the lowest
-    10 mantissa bits of float(s) and the couple-lanes scan runs in fp32.  Its
-    margin is smallest where s >= 4096 (the job bits of jobs near 1023 then
-    add almost 1/2 to s) and the slack grows large: n = 1024 jobs, m = 32
-    machines, times 200..255 (every s of the couple (0, 31) between 6,200
-    and 7,905; with m <= 32 and p <= 255, s never reaches 8,192), the last
-    34 jobs at 255 on machines 1..31, shallow prefixes so long scans run.
-    With all times 255 every Johnson order is a tie and every minimum tail is
-    31 x 255, the largest latency a compact record's int16 row holds.  Every
-    kernel, staging mode and batched entry point must match the oracle bit
-    for bit."""
+def test_scaled_scan_exact_at_its_limits(gpu_lib, case):
+    """The two-word records of compact instances hold 1024 s + j and
+    1024 delta, and the couple-lanes scan keeps the slack scaled by 1024
+    with a job in its low 10 bits.  The encoding is tightest where s and the
+    job are both near their limits and the slack grows large: n = 1024 jobs
+    (job bits up to 1023), m = 32 machines, times 200..255 (every s of the
+    couple (0, 31) between 6,200 and 7,905; with m <= 32 and p <= 255, s
+    never reaches 8,192), the last 34 jobs at 255 on machines 1..31, shallow
+    prefixes so long scans run.  With all times 255 every Johnson order is a
+    tie and every minimum tail is 31 x 255, the largest latency a compact
+    record's int16 row holds.  Every kernel, staging mode and batched entry
+    point must match the oracle bit for bit."""
     fsp = gpu_lib
     rng = np.random.default_rng(2024)
     n, m, N = 1024, 32, 160
