@@ -45,7 +45,10 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 // ------------------------------------------------------------------ prep
-template <int MP>
+// PS: the block first copies the processing times to shared memory (when they
+// fit beside the warps' state), so the prefix pass reads each job's row in
+// one shared-memory latency instead of an L1 miss.
+template <int MP, bool PS>
 __global__ void __launch_bounds__(32 * kPrepWarps, 2) fsp_lanes_prep(const LanesArgs a, int64_t nbatch32) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -53,7 +56,9 @@ __global__ void __launch_bounds__(32 * kPrepWarps, 2) fsp_lanes_prep(const Lanes
     int2 *tcache = hcache + a.m * 32;
     uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * flag_words(a.n);
     int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
+    int32_t *ptab = PS ? reinterpret_cast<int32_t *>(smem + a.off_ptab) : nullptr;
     load_sorted_heads(a, hcache, tcache);
+    if (PS) load_ptab(a, ptab);
     __syncthreads();
     const int rows_words = 32 * a.aq_stride;
     // warps are independent: each takes 32-node batches by its global index
@@ -61,7 +66,7 @@ __global__ void __launch_bounds__(32 * kPrepWarps, 2) fsp_lanes_prep(const Lanes
          b32 += (int64_t)gridDim.x * kPrepWarps) {
         const int64_t x = node_at(a, b32 * 32 + lane);
         int bterm = 0;
-        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
+        const bool valid = lanes_setup<MP, PS>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache, ptab);
         uint32_t *dst = a.scratch + (size_t)b32 * a.sb_words;
         for (int j = lane; j < a.n; j += 32) dst[j] = F[j];
         const uint32_t *rows = reinterpret_cast<const uint32_t *>(AQ);
@@ -214,16 +219,27 @@ int sb_words_for(const fsp_instance *inst) {
 }
 
 struct PrepLayout {
-    uint32_t off_cache, off_flags, off_aq;
+    uint32_t off_cache, off_flags, off_aq, off_ptab;  // off_ptab 0: no shared copy of the processing times
     size_t total;
 };
 
+// The prep block's shared memory; the processing times (pp, [n][mpad]) join
+// it when the total stays within half an SM (two prep blocks per SM) and the
+// table within 64 KB.
 PrepLayout prep_layout_for(const fsp_instance *inst) {
     PrepLayout L;
     L.off_cache = 0;
     L.off_flags = (uint32_t)align_up((size_t)inst->m * 32 * 8 * 2, 128);
     L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)kPrepWarps * flag_words(inst->n) * 4, 128);
     L.total = align_up(L.off_aq + (size_t)kPrepWarps * 32 * aq_stride_for(inst->m, !inst->compact) * 4, 128);
+    L.off_ptab = 0;
+    const size_t pbytes = (size_t)inst->n * inst->mpad * 4;
+    const size_t budget = std::min((size_t)max_smem_per_block(inst->device),
+                                   (size_t)max_smem_per_sm(inst->device) / 2 - 1024);
+    if (pbytes <= 64 * 1024 && L.total + pbytes <= budget) {
+        L.off_ptab = (uint32_t)L.total;
+        L.total = align_up(L.total + pbytes, 128);
+    }
     return L;
 }
 
@@ -257,20 +273,27 @@ cudaError_t launch_pair(const LanesArgs &ap, int64_t nbatch32, size_t prep_smem,
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = set_smem_attr(fsp_lanes_prep<MP>);
+        attr_err = set_smem_attr(fsp_lanes_prep<MP, false>);
+        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_prep<MP, true>);
         if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_scan<WIDE, MP>);
     });
     if (attr_err != cudaSuccess) return attr_err;
+    const bool ps = ap.off_ptab != 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fsp_lanes_prep<MP>, 32 * kPrepWarps, prep_smem) !=
-            cudaSuccess ||
+    if ((ps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fsp_lanes_prep<MP, true>, 32 * kPrepWarps,
+                                                            prep_smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fsp_lanes_prep<MP, false>, 32 * kPrepWarps,
+                                                            prep_smem)) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
     const int prep_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ap.num_batches, (int64_t)sms * per_sm));
     note_launches(2);
-    fsp_lanes_prep<MP><<<prep_grid, 32 * kPrepWarps, prep_smem, s>>>(ap, nbatch32);
+    if (ps)
+        fsp_lanes_prep<MP, true><<<prep_grid, 32 * kPrepWarps, prep_smem, s>>>(ap, nbatch32);
+    else
+        fsp_lanes_prep<MP, false><<<prep_grid, 32 * kPrepWarps, prep_smem, s>>>(ap, nbatch32);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     fsp_lanes_scan<WIDE, MP><<<scan_grid, threads, scan_smem, s>>>(ac);
@@ -361,6 +384,7 @@ fsp_status launch_split(const fsp_instance *inst, const int16_t *nodes, const in
     ap.off_cache = PL.off_cache;
     ap.off_flags = PL.off_flags;
     ap.off_aq = PL.off_aq;
+    ap.off_ptab = PL.off_ptab;
     ac.off_tables = SL.off_tables;
     ac.tile_stride = SL.tile_stride;
     ac.off_flags = SL.off_prep;
