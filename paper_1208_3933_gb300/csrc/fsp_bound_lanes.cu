@@ -131,7 +131,9 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) 
 }
 
 // ---------------------------------------------------------------- streamed
-template <bool WIDE, int MP>
+// PS: the block holds a shared-memory copy of the processing times
+// (a.off_ptab), which the setup reads instead of global memory.
+template <bool WIDE, int MP, bool PS>
 __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -150,6 +152,8 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
     }
     for (int i = threadIdx.x; i < a.G * 64; i += blockDim.x) sgp[i] = a.gpairs[i];
     load_sorted_heads(a, hcache, tcache);
+    int32_t *ptab = PS ? reinterpret_cast<int32_t *>(smem + a.off_ptab) : nullptr;
+    if (PS) load_ptab(a, ptab);
     __syncthreads();
 
     TilePipe tp{bar, smem + a.off_tables, a.tile_stride, a.ntiles <= 2};
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
         const int64_t bt = sl < 0 ? it : full + (int64_t)((uint32_t)(it - full) / S);
         const int64_t x = node_at(a, bt * (int64_t)(32 * W) + warp * 32 + lane);
         int bterm = 0;
-        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
+        const bool valid = lanes_setup<MP, PS>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache, ptab);
         int lb[32];
         int uf[32];
         int ui[32];
@@ -453,9 +457,9 @@ struct LanesLayout {
     size_t total;
 };
 
-// Global staging copies the processing-time rows (pp, [n][mpad] int32) to
-// shared memory when they fit the block's budget beside the warps' flag words
-// and rows (at most 64 KB):
+// Global and one-set streamed staging copy the processing-time rows (pp,
+// [n][mpad] int32) to shared memory when they fit the block's budget beside
+// everything else (at most 64 KB):
 // the setup's prefix recurrence, walks and release times then read a row in
 // one shared-memory latency instead of an L1 miss.
 constexpr size_t kPtabMaxBytes = 64 * 1024;
@@ -489,7 +493,10 @@ LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident,
     L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)warps * sets * flag_words(inst->n) * 4, 128);
     L.aq_stride = aq_stride_for(inst->m, !inst->compact);
     L.total = align_up(L.off_aq + (size_t)warps * sets * 32 * L.aq_stride * 4, 128);
-    (void)budget;  // the tiled kernels read the processing times from global memory
+    // the one-set streamed kernel keeps a shared copy of the processing times
+    // when it fits (compact records); the others read them from global memory
+    L.off_ptab = 0;
+    if (!resident && sets == 1 && inst->compact) add_ptab(L, inst, budget);
     return L;
 }
 
@@ -508,7 +515,8 @@ cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int sets, in
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
         attr_err = set_smem_attr(fsp_lanes_resident<WIDE, MP>);
-        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP>);
+        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP, false>);
+        if (!WIDE && attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP, !WIDE>);
         if (!WIDE && attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed2<MP>);
     });
     if (attr_err != cudaSuccess) return attr_err;
@@ -517,8 +525,10 @@ cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int sets, in
         fsp_lanes_resident<WIDE, MP><<<grid, threads, smem, s>>>(a);
     else if (!WIDE && sets == 2)
         fsp_lanes_streamed2<MP><<<grid, threads, smem, s>>>(a);
+    else if (!WIDE && a.off_ptab)
+        fsp_lanes_streamed<WIDE, MP, !WIDE><<<grid, threads, smem, s>>>(a);
     else
-        fsp_lanes_streamed<WIDE, MP><<<grid, threads, smem, s>>>(a);
+        fsp_lanes_streamed<WIDE, MP, false><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -720,6 +730,7 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     a.tile_stride = L.tile_stride;
     a.off_flags = L.off_flags;
     a.off_aq = L.off_aq;
+    a.off_ptab = resident ? 0u : L.off_ptab;
     a.aq_stride = L.aq_stride;
     a.release = (inst->flags & FSP_INSTANCE_RELEASE_PER_JOB) ? 1 : 0;
     a.q32 = inst->compact ? 0 : 1;
