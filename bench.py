@@ -66,6 +66,8 @@ def kernel_name(cfg) -> str:
     """The dominant kernel of a launch shape (its name in ncu launch lists)."""
     if not cfg or cfg.get("kernel") == 1:
         return "fsp_bound_kernel (node-lockstep)"
+    if cfg.get("staging") == 2 and cfg.get("nodes_per_thread") in (28, 56):
+        return "fsp_lanes_streamed28"
     return {1: "fsp_lanes_resident", 2: "fsp_lanes_streamed", 3: "fsp_lanes_scan (after fsp_lanes_prep)",
             4: "fsp_lanes_warp", 5: "fsp_lanes_global"}.get(cfg.get("staging"), "fsp_lanes_streamed")
 

@@ -105,8 +105,9 @@ typedef struct fsp_instance_info {
 typedef struct fsp_launch_config {
     int32_t kernel;              /* FSP_KERNEL_* */
     int32_t nodes_per_thread;    /* lockstep: K in {1,2,4,8}; lanes: nodes per warp, 32 (0 = 32) or,
-                                    streamed staging with compact records, 56: two sets of 28 nodes,
-                                    each Johnson record applied to all 56 */
+                                    streamed staging with compact records, 28 or 56: one or two sets
+                                    of 28 nodes (a set's flag word leaves bits 7, 15, 23 and 31
+                                    unused), each Johnson record applied to every node of the warp */
     int32_t blocks_per_sm;       /* resident blocks per SM (lockstep 1 or 2; lanes: streamed staging
                                     1..8, split/warp staging 1 or 2, global staging 1..16; at most
                                     16 warps per SM) */

@@ -407,13 +407,12 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
         c.blocks_per_sm > (c.staging == FSP_STAGING_GLOBAL ? 16 : 8) || c.pairs_per_tile < 0 || c.tail_slices < 0)
         return FSP_EINVAL;
     const int G = inst->G;
-    // nodes per warp (nodes_per_thread for this kernel): 32, or 56 in two
-    // sets of 28 (streamed staging, compact records)
-    const int sets = lanes_node_sets(c);
-    if (!sets) return FSP_EINVAL;
-    if (sets == 2 && ((c.staging && c.staging != FSP_STAGING_STREAMED) || !inst->compact || c.tail_slices > 1))
+    // nodes per warp (nodes_per_thread for this kernel): 32, or 28 and 56 in
+    // one and two sets of 28 (streamed staging, compact records)
+    const int npw = lanes_nodes_per_warp(c);
+    if (!npw) return FSP_EINVAL;
+    if (npw != 32 && ((c.staging && c.staging != FSP_STAGING_STREAMED) || !inst->compact || c.tail_slices > 1))
         return FSP_EINVAL;
-    const int npw = sets == 2 ? 56 : 32;
     c.nodes_per_thread = npw;
     if (c.staging == FSP_STAGING_GLOBAL) {
         // Warps independent, records from L2/L1: every work item (a 32-node

@@ -256,15 +256,16 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
     }
 }
 
-// ------------------------------------------------------ streamed, two sets
-// The streamed kernel with two node sets of 28 per warp (compact records):
-// a block batch is 56 W nodes; every record read serves 56 nodes, and each
-// flag word yields its 28 predicates from four byte-wise conversions.  A
-// warp sets up its two sets one after the other (lane = node, lanes 7, 15,
-// 23 and 31 idle), and the couple values of each group are reduced over the
-// lanes at once, so no per-node maxima are carried across groups.
-template <int MP>
-__global__ void __launch_bounds__(512, 1) fsp_lanes_streamed2(const LanesArgs a) {
+// ------------------------------------------------ streamed, 28-node sets
+// The streamed kernel with NS node sets of 28 per warp (NS = 1 or 2, compact
+// records): a block batch is 28 NS W nodes; each flag word yields its 28
+// predicates from four byte-wise conversions (bits 7, 15, 23 and 31 unused),
+// and with two sets every record read serves 56 nodes.  A warp sets up its
+// sets one after the other (lane = node, lanes 7, 15, 23 and 31 idle), and
+// the couple values of each group are reduced over the lanes at once, so no
+// per-node maxima are carried across groups.
+template <int MP, int NS>
+__global__ void __launch_bounds__(512, 1) fsp_lanes_streamed28(const LanesArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int W = blockDim.x >> 5;
@@ -273,10 +274,10 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed2(const LanesArgs a)
     int2 *hcache = reinterpret_cast<int2 *>(smem + a.off_cache);
     int2 *tcache = hcache + a.m * 32;
     const int nfw = flag_words(a.n);
-    uint32_t *F0 = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * 2 * nfw;
-    uint32_t *F1 = F0 + nfw;
-    int32_t *AQ0 = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 2 * 32 * a.aq_stride;
-    int32_t *AQ1 = AQ0 + 32 * a.aq_stride;
+    uint32_t *F0 = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * NS * nfw;
+    uint32_t *F1 = F0 + (NS - 1) * nfw;
+    int32_t *AQ0 = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * NS * 32 * a.aq_stride;
+    int32_t *AQ1 = AQ0 + (NS - 1) * 32 * a.aq_stride;
 
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed2(const LanesArgs a)
         const unsigned char *src = a.grec + ((size_t)g * a.npad + (size_t)ch * a.chunk) * 32 * a.rec_bytes;
         tp.issue(fill, src, (uint32_t)pos * 32u * a.rec_bytes);
     };
-    // work items as in fsp_lanes_streamed, block batches of 56 W nodes
+    // work items as in fsp_lanes_streamed, block batches of 28 NS W nodes
     const uint32_t S = a.gslices > 1 ? (uint32_t)a.gslices : 1u;
     const int64_t full = S > 1 ? a.full_batches : a.num_batches;
     const int gper = S > 1 ? a.gper : a.G;
@@ -316,13 +317,13 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed2(const LanesArgs a)
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int sl = slice_of(it);
         const int64_t bt = sl < 0 ? it : full + (int64_t)((uint32_t)(it - full) / S);
-        const int64_t base = bt * (int64_t)(56 * W) + warp * 56;
+        const int64_t base = bt * (int64_t)(28 * NS * W) + warp * 28 * NS;
         const int64_t x0 = real ? node_at(a, base + r28) : a.N;
-        const int64_t x1 = real ? node_at(a, base + 28 + r28) : a.N;
+        const int64_t x1 = (NS == 2 && real) ? node_at(a, base + 28 + r28) : a.N;
         bool valid0 = false, valid1 = false;
         int bterm0 = 0, bterm1 = 0;
 #pragma unroll 1
-        for (int set = 0; set < 2; ++set) {
+        for (int set = 0; set < NS; ++set) {
             int bt_ = 0;
             const bool v = lanes_setup<MP>(a, set ? x1 : x0, lane, set ? F1 : F0,
                                            (set ? AQ1 : AQ0) + lane * a.aq_stride, bt_, hcache, tcache);
@@ -335,9 +336,9 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed2(const LanesArgs a)
             }
         }
         int M0 = 0, M1 = 0;
-        int u[56];
+        int u[28 * NS];
 #pragma unroll
-        for (int b = 0; b < 56; ++b) u[b] = 0;
+        for (int b = 0; b < 28 * NS; ++b) u[b] = 0;
         int kk = 0, ll = 1;
         const int t1 = sl < 0 ? a.ntiles : min(a.G, (sl + 1) * gper) * a.nchunks;
         for (int t = first_tile(sl); t < t1; ++t) {
@@ -357,15 +358,15 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed2(const LanesArgs a)
             const unsigned char *tb = tp.buf + tp.current(t) * tp.stride;
             if (ch == 0) {
 #pragma unroll
-                for (int b = 0; b < 56; ++b) u[b] = 0;
+                for (int b = 0; b < 28 * NS; ++b) u[b] = 0;
                 kk = sgp[2 * (g * 32 + lane)];
                 ll = sgp[2 * (g * 32 + lane) + 1];
             }
             const int npos = min(a.chunk, a.npad - ch * a.chunk);
-            scan_compact2(reinterpret_cast<const uint2 *>(tb) + lane, npos, F0, F1, u);
+            scan_compact28<NS>(reinterpret_cast<const uint2 *>(tb) + lane, npos, F0, F1, u);
             if (ch == a.nchunks - 1) {
                 M0 = max(M0, set28_group_max<0>(AQ0, a.aq_stride, a.m, kk, ll, u, lane));
-                M1 = max(M1, set28_group_max<28>(AQ1, a.aq_stride, a.m, kk, ll, u, lane));
+                if constexpr (NS == 2) M1 = max(M1, set28_group_max<28>(AQ1, a.aq_stride, a.m, kk, ll, u, lane));
             }
             if (!tp.resident) {
                 __syncthreads();
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed2(const LanesArgs a)
             }
         }
 #pragma unroll
-        for (int set = 0; set < 2; ++set) {
+        for (int set = 0; set < NS; ++set) {
             const int64_t x = set ? x1 : x0;
             const bool valid = set ? valid1 : valid0;
             const int best = max(set ? M1 : M0, set ? bterm1 : bterm0);
@@ -476,9 +477,10 @@ void add_ptab(LanesLayout &L, const fsp_instance *inst, size_t budget) {
 // ints per node row: A_k as int32, then q_l as int16 (compact records) or int32
 int aq_stride_for(int m, bool q32) { return (m + (q32 ? m : (m + 1) / 2)) | 1; }
 
-// sets: node sets per warp (1: 32 nodes; 2: two sets of 28, streamed only)
+// npw: nodes per warp (32; or 28 and 56, one and two sets of 28, streamed only)
 LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident, int chunk, size_t budget,
-                             int sets = 1) {
+                             int npw = 32) {
+    const int sets = npw == 56 ? 2 : 1;
     LanesLayout L = {};
     L.off_cache = (uint32_t)align_up(16 + (size_t)inst->G * 64, 128);
     L.off_tables = (uint32_t)align_up(L.off_cache + (size_t)inst->m * 32 * 8 * 2, 128);
@@ -496,7 +498,7 @@ LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident,
     // the one-set streamed kernel keeps a shared copy of the processing times
     // when it fits (compact records); the others read them from global memory
     L.off_ptab = 0;
-    if (!resident && sets == 1 && inst->compact) add_ptab(L, inst, budget);
+    if (!resident && npw == 32 && inst->compact) add_ptab(L, inst, budget);
     return L;
 }
 
@@ -509,7 +511,7 @@ cudaError_t set_smem_attr(K kernel) {
 }
 
 template <bool WIDE, int MP>
-cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int sets, int grid, int threads, size_t smem,
+cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int npw, int grid, int threads, size_t smem,
                                  cudaStream_t s) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
@@ -517,14 +519,17 @@ cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int sets, in
         attr_err = set_smem_attr(fsp_lanes_resident<WIDE, MP>);
         if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP, false>);
         if (!WIDE && attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP, !WIDE>);
-        if (!WIDE && attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed2<MP>);
+        if (!WIDE && attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed28<MP, 1>);
+        if (!WIDE && attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed28<MP, 2>);
     });
     if (attr_err != cudaSuccess) return attr_err;
     note_launches(1);
     if (resident)
         fsp_lanes_resident<WIDE, MP><<<grid, threads, smem, s>>>(a);
-    else if (!WIDE && sets == 2)
-        fsp_lanes_streamed2<MP><<<grid, threads, smem, s>>>(a);
+    else if (!WIDE && npw == 56)
+        fsp_lanes_streamed28<MP, 2><<<grid, threads, smem, s>>>(a);
+    else if (!WIDE && npw == 28)
+        fsp_lanes_streamed28<MP, 1><<<grid, threads, smem, s>>>(a);
     else if (!WIDE && a.off_ptab)
         fsp_lanes_streamed<WIDE, MP, !WIDE><<<grid, threads, smem, s>>>(a);
     else
@@ -533,15 +538,15 @@ cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int sets, in
 }
 
 template <bool WIDE>
-cudaError_t launch_lanes_mp(const LanesArgs &a, int mp, bool resident, int sets, int grid, int threads, size_t smem,
+cudaError_t launch_lanes_mp(const LanesArgs &a, int mp, bool resident, int npw, int grid, int threads, size_t smem,
                             cudaStream_t s) {
     switch (mp) {
-        case 8: return launch_lanes_variant<WIDE, 8>(a, resident, sets, grid, threads, smem, s);
-        case 12: return launch_lanes_variant<WIDE, 12>(a, resident, sets, grid, threads, smem, s);
-        case 16: return launch_lanes_variant<WIDE, 16>(a, resident, sets, grid, threads, smem, s);
-        case 20: return launch_lanes_variant<WIDE, 20>(a, resident, sets, grid, threads, smem, s);
-        case 24: return launch_lanes_variant<WIDE, 24>(a, resident, sets, grid, threads, smem, s);
-        default: return launch_lanes_variant<WIDE, 32>(a, resident, sets, grid, threads, smem, s);
+        case 8: return launch_lanes_variant<WIDE, 8>(a, resident, npw, grid, threads, smem, s);
+        case 12: return launch_lanes_variant<WIDE, 12>(a, resident, npw, grid, threads, smem, s);
+        case 16: return launch_lanes_variant<WIDE, 16>(a, resident, npw, grid, threads, smem, s);
+        case 20: return launch_lanes_variant<WIDE, 20>(a, resident, npw, grid, threads, smem, s);
+        case 24: return launch_lanes_variant<WIDE, 24>(a, resident, npw, grid, threads, smem, s);
+        default: return launch_lanes_variant<WIDE, 32>(a, resident, npw, grid, threads, smem, s);
     }
 }
 
@@ -594,9 +599,9 @@ cudaError_t launch_global_mp(const LanesArgs &a, int mp, int grid, int threads, 
 
 }  // namespace
 
-int lanes_node_sets(const fsp_launch_config &c) {
-    if (c.nodes_per_thread == 0 || c.nodes_per_thread == 32) return 1;
-    return c.nodes_per_thread == 56 ? 2 : 0;
+int lanes_nodes_per_warp(const fsp_launch_config &c) {
+    const int v = c.nodes_per_thread;
+    return v == 0 ? 32 : (v == 32 || v == 28 || v == 56) ? v : 0;
 }
 
 int lanes_groups_per_item(const fsp_instance *inst, int pairs_per_tile) {
@@ -623,12 +628,13 @@ fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &c, si
     // pools), 2 otherwise
     if (W < 1 || W > 16 || bps < 1 || bps > (resident ? 2 : 8) || W * bps > 16) return FSP_EINVAL;
     if (!resident && (c.positions_per_tile < 4 || (c.positions_per_tile & 3))) return FSP_EINVAL;
-    // nodes per warp: 32, or 56 (two sets of 28: streamed staging, compact records)
-    const int sets = lanes_node_sets(c);
-    if (sets < 1 || (sets == 2 && (resident || !inst->compact))) return FSP_EINVAL;
+    // nodes per warp: 32, or 28 and 56 (one and two sets of 28: streamed
+    // staging, compact records)
+    const int npw = lanes_nodes_per_warp(c);
+    if (!npw || (npw != 32 && (resident || !inst->compact))) return FSP_EINVAL;
     const int chunk = resident ? inst->npad : std::min(c.positions_per_tile, inst->npad);
     const size_t budget = lanes_budget(inst, bps);
-    const LanesLayout L = lanes_layout_for(inst, W, resident, chunk, budget, sets);
+    const LanesLayout L = lanes_layout_for(inst, W, resident, chunk, budget, npw);
     if (L.total > budget) return FSP_EINVAL;
     // the resident copy completes on one mbarrier: its byte count must fit the transaction counter
     if (resident && (size_t)inst->npad * 32 * inst->grec_bytes * inst->G >= (1u << 20)) return FSP_EINVAL;
@@ -700,10 +706,9 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     const int W = cfg.warps_per_block;
     const bool resident = cfg.staging == FSP_STAGING_RESIDENT;
     const int chunk = resident ? inst->npad : std::min(cfg.positions_per_tile, inst->npad);
-    const int sets = lanes_node_sets(cfg);
-    const int npw = sets == 2 ? 56 : 32;  // nodes per warp
+    const int npw = lanes_nodes_per_warp(cfg);
     const LanesLayout L = lanes_layout_for(inst, W, resident, chunk,
-                                           lanes_budget(inst, cfg.blocks_per_sm ? cfg.blocks_per_sm : 1), sets);
+                                           lanes_budget(inst, cfg.blocks_per_sm ? cfg.blocks_per_sm : 1), npw);
     LanesArgs a = {};
     a.grec = static_cast<const unsigned char *>(inst->t.grec);
     a.gpairs = inst->t.gpairs;
@@ -768,8 +773,8 @@ fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const in
     st = depth_order(inst, depths, N, s, &order);
     if (st != FSP_OK) return st;
     a.order = order;
-    const cudaError_t e = inst->compact ? launch_lanes_mp<false>(a, inst->mpad, resident, sets, grid, 32 * W, smem, s)
-                                        : launch_lanes_mp<true>(a, inst->mpad, resident, sets, grid, 32 * W, smem, s);
+    const cudaError_t e = inst->compact ? launch_lanes_mp<false>(a, inst->mpad, resident, npw, grid, 32 * W, smem, s)
+                                        : launch_lanes_mp<true>(a, inst->mpad, resident, npw, grid, 32 * W, smem, s);
     const cudaError_t ef = order ? cudaFreeAsync(order, s) : cudaSuccess;
     return (e == cudaSuccess && ef == cudaSuccess) ? FSP_OK : FSP_ECUDA;
 }

@@ -113,9 +113,9 @@ fsp_status lanes_layout(const fsp_instance *inst, const fsp_launch_config &cfg, 
 // Couple groups of 32 per streamed work item for a requested pairs_per_tile
 // (0 or >= P: all G groups; else rounded up to whole groups).
 int lanes_groups_per_item(const fsp_instance *inst, int pairs_per_tile);
-// Node sets per warp of a couple-lanes shape (its nodes_per_thread field: 0 or
-// 32 -> 1 set of 32 nodes, 56 -> 2 sets of 28; anything else -> 0, invalid).
-int lanes_node_sets(const fsp_launch_config &c);
+// Nodes per warp of a couple-lanes shape (its nodes_per_thread field): 32 (0
+// also means 32), 28 or 56 (one or two sets of 28); 0 for any other value.
+int lanes_nodes_per_warp(const fsp_launch_config &c);
 fsp_status launch_lanes(const fsp_instance *inst, const int16_t *nodes, const int32_t *depths, int64_t N,
                         int32_t *out_lb, void *stream, const fsp_launch_config &cfg);
 // The same bound as a prep kernel and a scan kernel (fsp_bound_split.cu).

@@ -516,35 +516,36 @@ __device__ __forceinline__ int transpose_max(int (&lb)[32], int lane) {
 constexpr uint32_t kSet28 = 0x7f7f7f7fu;
 __host__ __device__ constexpr int set28_slot(int b) { return b - (b >> 3); }
 
-// lanes_step for the two sets: F0 and F1 are their flag words, u[0..27] and
-// u[28..55] their slacks.
-__device__ __forceinline__ void lanes_step2(uint2 r, const uint32_t *F0, const uint32_t *F1, int (&u)[56]) {
+// lanes_step for NS sets of 28 (1 or 2): F0 and F1 are their flag words (F1
+// unread for one set), u[0..27] and u[28..55] their slacks.
+template <int NS>
+__device__ __forceinline__ void lanes_step28(uint2 r, const uint32_t *F0, const uint32_t *F1, int (&u)[28 * NS]) {
     const uint32_t j = r.x & 1023u;
-    const uint32_t f0 = F0[j], f1 = F1[j];
     const int sv = (int)r.x, dv = (int)r.y;
 #pragma unroll
-    for (int b = 0; b < 32; ++b)
-        if ((kSet28 >> b) & 1u)
-            if ((f0 >> b) & 1u) u[set28_slot(b)] = __viaddmax_s32(u[set28_slot(b)], dv, sv);
+    for (int set = 0; set < NS; ++set) {
+        const uint32_t f = (set ? F1 : F0)[j];
 #pragma unroll
-    for (int b = 0; b < 32; ++b)
-        if ((kSet28 >> b) & 1u)
-            if ((f1 >> b) & 1u) u[28 + set28_slot(b)] = __viaddmax_s32(u[28 + set28_slot(b)], dv, sv);
+        for (int b = 0; b < 32; ++b)
+            if ((kSet28 >> b) & 1u)
+                if ((f >> b) & 1u) u[28 * set + set28_slot(b)] = __viaddmax_s32(u[28 * set + set28_slot(b)], dv, sv);
+    }
 }
 
-__device__ __forceinline__ void scan_compact2(const uint2 *R, int npos, const uint32_t *F0, const uint32_t *F1,
-                                              int (&u)[56]) {
+template <int NS>
+__device__ __forceinline__ void scan_compact28(const uint2 *R, int npos, const uint32_t *F0, const uint32_t *F1,
+                                               int (&u)[28 * NS]) {
 #pragma unroll 2
-    for (int i = 0; i < npos; ++i) lanes_step2(R[i * 32], F0, F1, u);
+    for (int i = 0; i < npos; ++i) lanes_step28<NS>(R[i * 32], F0, F1, u);
 }
 
 // One couple group's values A_k + q_l + u of the 28-node set whose slacks
 // start at u[OFF], reduced over the warp's lanes (couples): lane b receives
 // the maximum for the set's node in bit b (0 in the unused lanes).  Compact
 // records only (int16 latencies, slack scaled by 1024).
-template <int OFF>
+template <int OFF, int NU>
 __device__ __forceinline__ int set28_group_max(const int32_t *AQ, int stride, int m, int kk, int ll,
-                                               const int (&u)[56], int lane) {
+                                               const int (&u)[NU], int lane) {
     int v[32];
 #pragma unroll
     for (int b = 0; b < 32; ++b) {
@@ -557,6 +558,5 @@ __device__ __forceinline__ int set28_group_max(const int32_t *AQ, int stride, in
     }
     return transpose_max(v, lane);
 }
-
 
 }  // namespace fspgb

@@ -103,16 +103,17 @@ std::vector<fsp_launch_config> candidates(const fsp_instance *inst, int64_t N) {
                     c2.blocks_per_sm = 2;
                     add(c2);
                 }
-                // two node sets of 28 per warp (streamed staging, compact records)
-                if (staging == FSP_STAGING_STREAMED && inst->compact) {
-                    fsp_launch_config c2 = c;
-                    c2.nodes_per_thread = 56;
-                    add(c2);
-                    if (W <= 8) {
-                        c2.blocks_per_sm = 2;
+                // one or two node sets of 28 per warp (streamed staging, compact records)
+                if (staging == FSP_STAGING_STREAMED && inst->compact)
+                    for (int npw : {28, 56}) {
+                        fsp_launch_config c2 = c;
+                        c2.nodes_per_thread = npw;
                         add(c2);
+                        if (W <= 8) {
+                            c2.blocks_per_sm = 2;
+                            add(c2);
+                        }
                     }
-                }
                 // pools of more than one wave: the last partial wave's batches
                 // split by couples as well
                 if (staging == FSP_STAGING_STREAMED && pos == 0 && N > 32 * W * (int64_t)sms)

@@ -137,22 +137,23 @@ def test_global_staging_matches_oracle(gpu_lib, ppt, W, bps, nm):
     assert got[3] == got[50] == got[7] == fsp.FSP_LB_INVALID
 
 
+@pytest.mark.parametrize("npw", [28, 56])
 @pytest.mark.parametrize("ppt", [0, 32, 96, 1000])
 @pytest.mark.parametrize("W,bps,positions", [(1, 0, 12), (4, 2, 0), (3, 1, 64), (6, 1, 96)])
 @pytest.mark.parametrize("nm", [(40, 20), (70, 12), (33, 27), (23, 9), (200, 20)])
-def test_two_node_sets_per_warp_match_oracle(gpu_lib, ppt, W, bps, positions, nm):
-    """Streamed staging with 56 nodes per warp (two sets of 28, flag bits 7,
-    15, 23 and 31 unused): block batches of 56 W nodes with a ragged last
+def test_28_node_sets_per_warp_match_oracle(gpu_lib, npw, ppt, W, bps, positions, nm):
+    """Streamed staging with one or two sets of 28 nodes per warp (flag bits
+    7, 15, 23 and 31 unused): block batches of npw W nodes with a ragged last
     batch, couple slices (0 = chosen from the pool size) combined by atomic
     max, record tiles of 12, 64 or 96 positions or whole groups, and invalid
     rows in either set."""
     fsp = gpu_lib
     n, m = nm
-    p, rows, depths = pool(900 + n + m, n, m, 56 * W * 5 + 23)
+    p, rows, depths = pool(900 + n + m, n, m, npw * W * 5 + 23)
     depths[[3, 50, 40]] = [-1, n + 1, n + 2]
     rows[7, :2] = [5, 5]
     depths[7] = max(int(depths[7]), 2)
-    cfg = dict(kernel=2, staging=2, nodes_per_thread=56, warps_per_block=W, blocks_per_sm=bps,
+    cfg = dict(kernel=2, staging=2, nodes_per_thread=npw, warps_per_block=W, blocks_per_sm=bps,
                positions_per_tile=positions, pairs_per_tile=ppt)
     with fsp.Instance(p) as inst:
         got = gpu_bounds(fsp, inst, rows, depths, config=cfg)
@@ -172,11 +173,12 @@ def test_two_node_sets_depth_order_release_and_refusals(gpu_lib):
     with fsp.Instance(w.p) as inst:
         a = gpu_bounds(fsp, inst, w.rows, w.depths, config=two)
         b = gpu_bounds(fsp, inst, w.rows, w.depths, config=dict(kernel=2, staging=2, warps_per_block=8))
-        assert np.array_equal(a, b)
+        c = gpu_bounds(fsp, inst, w.rows, w.depths, config=dict(two, nodes_per_thread=28))
+        assert np.array_equal(a, b) and np.array_equal(a, c)
         assert np.array_equal(a[idx], oracle_bounds(w.p, w.rows[idx], w.depths[idx]))
         r, d = to_dev(w.rows[:100], w.depths[:100])
         for bad in (dict(two, staging=1), dict(two, staging=3), dict(two, staging=5), dict(two, nodes_per_thread=40),
-                    dict(two, tail_slices=2)):
+                    dict(two, tail_slices=2), dict(two, nodes_per_thread=28, staging=3)):
             with pytest.raises(fsp.FspError):
                 fsp.fsp_bound_pool(inst, r, d, config=bad)
     with fsp.Instance(w.p, flags=fsp.FSP_INSTANCE_RELEASE_PER_JOB) as inst:
@@ -612,7 +614,8 @@ def _every_path(fsp, inst, rows, depths):
     if info.compact:  # global staging and two node sets per warp take two-word records only
         cfgs += [dict(kernel=2, staging=5, warps_per_block=4), dict(kernel=2, staging=5, warps_per_block=1,
                                                                     pairs_per_tile=32),
-                 dict(kernel=2, staging=2, nodes_per_thread=56, warps_per_block=3, positions_per_tile=64)]
+                 dict(kernel=2, staging=2, nodes_per_thread=56, warps_per_block=3, positions_per_tile=64),
+                 dict(kernel=2, staging=2, nodes_per_thread=28, warps_per_block=5, positions_per_tile=32)]
     out = {str(c): gpu_bounds(fsp, inst, rows, depths, config=c) for c in cfgs}
     if info.compact:
         r, d = to_dev(rows, depths)
