@@ -209,3 +209,48 @@ def test_batch_autotune_ex_picks_tile_and_couple_split(gpu_lib):
         assert np.array_equal(o.cpu().numpy(), oracle.Tables(w.p).lb_pool(w.rows, w.depths, threads=16))
     for inst in insts:
         inst.close()
+
+
+@pytest.mark.parametrize("W", [0, 3, 16])
+def test_few_couple_instances_in_one_plan_match_oracle(gpu_lib, W):
+    """Instances with few couples (m = 2 .. 12, one group of 32 couple lanes
+    or two) beside one with six groups (m = 20) in one plan: pools of ragged
+    sizes, an empty one, invalid rows at every 32-node boundary of the first
+    128 nodes, per-job release times; automatic and fixed node tiles, and the
+    same pools in a couple-sliced plan, must all match the oracle bit for
+    bit."""
+    import torch
+    fsp = gpu_lib
+    rng = np.random.default_rng(77)
+    specs = [(9, 2, 300), (12, 3, 257), (15, 4, 33), (20, 5, 1000), (25, 6, 129), (18, 8, 200), (30, 10, 999),
+             (22, 12, 513), (40, 20, 300), (16, 5, 0), (20, 5, 97)]
+    ws, insts = [], []
+    for i, (n, m, N) in enumerate(specs):
+        p = rng.integers(1, 100, (n, m), dtype=np.int32)
+        rows, depths = workloads.random_pool(rng, n, N, max_depth=n + 1)
+        if N > 130:
+            for x in (0, 31, 32, 63, 64, 95, 96, 127, 128):  # both ends of the first 32-node batches
+                depths[x] = -1 if x % 2 else n + 1
+        release = i == len(specs) - 1
+        ws.append((p, rows, depths, release))
+        insts.append(fsp.Instance(p, flags=fsp.FSP_INSTANCE_RELEASE_PER_JOB if release else 0))
+    bufs = [(dev(r), dev(d)) for _, r, d, _ in ws]
+    outs = [torch.full((r.shape[0],), -7, dtype=torch.int32, device="cuda") for _, r, _, _ in ws]
+    pools = [(inst, r, d, o) for inst, (r, d), o in zip(insts, bufs, outs)]
+    with fsp.Batch(pools, warps_per_block=W) as b:
+        b.launch()
+        torch.cuda.synchronize()
+    for (p, rows, depths, release), o in zip(ws, outs):
+        want = oracle.Tables(p).lb_pool(rows, depths, threads=8,
+                                        release=oracle.RELEASE_EST if release else oracle.RELEASE_HEADS)
+        assert np.array_equal(o.cpu().numpy(), want), (p.shape, rows.shape)
+    # a couple-sliced plan agrees
+    outs2 = [torch.full_like(o, -7) for o in outs]
+    with fsp.Batch([(inst, r, d, o) for inst, (r, d), o in zip(insts, bufs, outs2)], warps_per_block=4,
+                   couples_per_item=32) as b:
+        b.launch()
+        torch.cuda.synchronize()
+    for o, o2 in zip(outs, outs2):
+        assert torch.equal(o, o2)
+    for inst in insts:
+        inst.close()
