@@ -387,7 +387,7 @@ def load_golden_optima():
     return {int(k): v.get("opt") for k, v in json.load(open(gpath))["results"].items()}
 
 
-def run_served_leg(node_limit: int = 500_000_000, expand: int = 1024, ig_iterations: int = 2000,
+def run_served_leg(node_limit: int = 500_000_000, expand: int = 1024, ig_iterations: int = 2000, slots: int = 8,
                    rate_hz: float = 100.0, pools_per_stream: int = 8):
     """The serving loop: 32 depth-first searches (n=20; m=5 for seeds 200-215,
     m=10 for 216-231) plus 16 streams of 200x20 pools (4,096-32,768 nodes,
@@ -424,7 +424,7 @@ def run_served_leg(node_limit: int = 500_000_000, expand: int = 1024, ig_iterati
 
     def arm(served: bool):
         results, lat = {}, []
-        srv = fsp.Server(hbm_budget_bytes=4 << 30, slots=3) if served else None
+        srv = fsp.Server(hbm_budget_bytes=4 << 30, slots=slots) if served else None
         errors = []
 
         def search(seed):
@@ -493,7 +493,7 @@ def run_served_leg(node_limit: int = 500_000_000, expand: int = 1024, ig_iterati
     for inst in list(s_insts.values()) + st_insts:
         inst.close()
     return {"workload": "32 DFS searches (20x5 seeds 200-215, 20x10 seeds 216-231) + 16 Poisson streams of "
-                        "200x20 pools", "node_budget_per_search": node_limit, "expand": expand,
+                        "200x20 pools", "node_budget_per_search": node_limit, "expand": expand, "slots": slots,
             "ub0": f"library iterated greedy, {ig_iterations} iterations per search ({ig_s:.1f} s, outside both arms)",
             "served_nodes_per_s": total / s_wall, "plain_nodes_per_s": total / p_wall,
             "served_over_plain": p_wall / s_wall, "nodes": total, "search_nodes": nodes_search,
@@ -793,6 +793,7 @@ def main():
     ap.add_argument("--leg", default="", choices=["", "batched", "served", "searches", "sizes"],
                     help="run one extra leg alone (single GPU) and print its JSON line (profiling)")
     ap.add_argument("--served-expand", type=int, default=0, help="served leg: parents per request (profiling)")
+    ap.add_argument("--served-slots", type=int, default=0, help="served leg: server slots (profiling)")
     ap.add_argument("--served-budget", type=int, default=0, help="served leg: node budget per search (profiling)")
     ap.add_argument("--config", default="",
                     help="force a launch shape, e.g. kernel=2,warps_per_block=14 (profiling); default: autotuned")
@@ -806,7 +807,8 @@ def main():
         build.build()
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
-        served_kw = {k: v for k, v in (("expand", args.served_expand), ("node_limit", args.served_budget)) if v}
+        served_kw = {k: v for k, v in (("expand", args.served_expand), ("node_limit", args.served_budget),
+                                       ("slots", args.served_slots)) if v}
         leg = {"batched": lambda: run_batched_leg(dev), "served": lambda: run_served_leg(**served_kw),
                "searches": run_bnb_leg, "sizes": lambda: run_sizes_leg(dev)}[args.leg]()
         print(json.dumps({"leg": args.leg, "result": leg}), flush=True)
