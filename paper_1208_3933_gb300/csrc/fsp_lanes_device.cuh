@@ -114,10 +114,10 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     // lanes never share a word) with an atomic OR whose result is not read,
     // so the marks form no chain of dependent shared-memory reads; a job
     // outside [0,n) invalidates the row, and so does a job marked twice,
-    // found afterwards as fewer marked bits than the depth.  Recurrence: C(sigma,k) by the flow-shop recurrence
-    // and the prefix column sums, one step max(c + p, C_k + p) = a single
-    // fused add-max.  An invalid row still runs the loop on clamped jobs; its
-    // result is discarded.
+    // found afterwards as fewer marked bits than the depth.  Recurrence:
+    // C(sigma,k) by the flow-shop recurrence and the prefix column sums, one
+    // step max(c + p, C_k + p) = a single fused add-max.  An invalid row
+    // still runs the loop on clamped jobs; its result is discarded.
     for (int w = 0; w < nw; ++w) F[w * 32 + lane] = 0u;
     int C[MP], Ps[MP];
 #pragma unroll
