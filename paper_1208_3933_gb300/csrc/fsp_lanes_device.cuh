@@ -461,9 +461,18 @@ __device__ __forceinline__ void lanes_step(uint2 r, const uint32_t *F, int (&u)[
 
 // One couple group's scan over positions [0, npos) of a record tile (lane =
 // couple): scaled slack for two-word records, plain int32 for 128-bit ones.
+// npos is a multiple of 4 (couple rows are padded to 4 entries and tiles hold
+// multiples of 4 positions), so the loop takes four positions a round with
+// no remainder.
 __device__ __forceinline__ void scan_compact(const uint2 *R, int npos, const uint32_t *F, int (&u)[32]) {
-#pragma unroll 2
-    for (int i = 0; i < npos; ++i) lanes_step(R[i * 32], F, u);
+#pragma unroll 1
+    for (int i = 0; i < npos; i += 4) {
+        const uint2 r0 = R[i * 32], r1 = R[(i + 1) * 32], r2 = R[(i + 2) * 32], r3 = R[(i + 3) * 32];
+        lanes_step(r0, F, u);
+        lanes_step(r1, F, u);
+        lanes_step(r2, F, u);
+        lanes_step(r3, F, u);
+    }
 }
 
 __device__ __forceinline__ void scan_wide(const int4 *R, int npos, const uint32_t *F, int (&u)[32]) {
