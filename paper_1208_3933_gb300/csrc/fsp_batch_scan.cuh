@@ -10,8 +10,10 @@ namespace fspgb {
 // scan_compact over records read from global memory (L1/L2): the records
 // of the next kScanAhead positions are loaded while the current ones are
 // applied, so each load's latency (longer than a shared-memory read's) is
-// covered by the updates before it is needed.
+// covered by the updates before it is needed.  npos (a couple row's padded
+// length) is a multiple of kScanAhead, so every round applies all of them.
 constexpr int kScanAhead = 4;
+static_assert(kScanAhead == kRecAlign, "a round of the ring covers one padding unit of a couple row");
 __device__ __forceinline__ void scan_compact_global(const uint2 *R, int npos, const uint32_t *F, int (&u)[32]) {
     uint2 buf[kScanAhead];
 #pragma unroll
@@ -22,7 +24,7 @@ __device__ __forceinline__ void scan_compact_global(const uint2 *R, int npos, co
             const uint2 r = buf[t];
             const int nx = i + kScanAhead + t;
             buf[t] = nx < npos ? __ldg(R + nx * 32) : make_uint2(0u, 0u);
-            if (i + t < npos) lanes_step(r, F, u);
+            lanes_step(r, F, u);
         }
     }
 }

@@ -541,11 +541,18 @@ __device__ __forceinline__ void lanes_step28(uint2 r, const uint32_t *F0, const 
     }
 }
 
+// npos is a multiple of 4, as in scan_compact.
 template <int NS>
 __device__ __forceinline__ void scan_compact28(const uint2 *R, int npos, const uint32_t *F0, const uint32_t *F1,
                                                int (&u)[28 * NS]) {
-#pragma unroll 2
-    for (int i = 0; i < npos; ++i) lanes_step28<NS>(R[i * 32], F0, F1, u);
+#pragma unroll 1
+    for (int i = 0; i < npos; i += 4) {
+        const uint2 r0 = R[i * 32], r1 = R[(i + 1) * 32], r2 = R[(i + 2) * 32], r3 = R[(i + 3) * 32];
+        lanes_step28<NS>(r0, F0, F1, u);
+        lanes_step28<NS>(r1, F0, F1, u);
+        lanes_step28<NS>(r2, F0, F1, u);
+        lanes_step28<NS>(r3, F0, F1, u);
+    }
 }
 
 // One couple group's values A_k + q_l + u of the 28-node set whose slacks
