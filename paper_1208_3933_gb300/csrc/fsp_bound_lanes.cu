@@ -22,8 +22,8 @@
 // Per node the shared memory holds one flag bit per job and a row with A_k
 // (int32) and q_l (int16 with compact records, whose tails stay below 2^15;
 // int32 with 128-bit ones), so a block keeps hundreds of nodes in flight.
-// Large pools are bounded in depth order (fsp_order.cu).  Two staging modes
-// here (fsp_bound_split.cu and fsp_bound_warp.cu hold two more):
+// Large pools are bounded in depth order (fsp_order.cu).  Three staging
+// modes here (fsp_bound_split.cu and fsp_bound_warp.cu hold two more):
 //   resident  all record groups are copied to shared memory once per block
 //             (one cp.async.bulk per group on one mbarrier); warps are then
 //             independent and claim 32-node batches from a per-block counter,
@@ -33,14 +33,21 @@
 //             from tile to tile together (the paper's "does not fit" case).
 //             A pool too small to occupy every SM splits each block batch by
 //             couple groups over several work items, whose couple maxima meet
-//             in an atomic max on the zeroed bounds.
+//             in an atomic max on the zeroed bounds.  A variant holds one or
+//             two sets of 28 nodes per warp instead of 32 (fsp_lanes_streamed28);
+//   global    no tiles: every warp reads its groups' records from L2/L1
+//             through a register ring and takes its own work items, so a
+//             small pool spreads one warp per item over the GPU.
+// Global and one-set streamed staging keep the processing times in shared
+// memory when they fit.
 //
 // Setup, one lane per node (fsp_lanes_device.cuh): (1) one pass over the
 // prefix for the membership bitmaps, row validation, the prefix recurrence
 // C(sigma,k) (Section II-B) and the prefix's column sums, (2) the flag words
 // by bit-matrix transposes, (3) the minima of RM and QM as the first
 // unscheduled job of each machine's head- (tail-) sorted job list, 32 list
-// entries per round.
+// entries per round, or, for nodes with at most 32 unscheduled jobs, by
+// walking those jobs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
