@@ -414,6 +414,21 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     if (npw != 32 && ((c.staging && c.staging != FSP_STAGING_STREAMED) || !inst->compact || c.tail_slices > 1))
         return FSP_EINVAL;
     c.nodes_per_thread = npw;
+    // Default shape of a pool of a few thousand work items (32-node batches x
+    // couple groups) for instances of at least four couple groups: global
+    // staging with two warps per block and eight blocks per SM, couple slices
+    // from the pool size.  At 200x20 the autotuner picks it for 8,192 and
+    // 16,384 nodes (1,536 and 3,072 items) and streamed or split staging for
+    // 4,096 and 32,768.
+    if (!c.staging && !c.warps_per_block && !c.blocks_per_sm && !c.pairs_per_tile && !c.positions_per_tile &&
+        c.tail_slices <= 1 && npw == 32 && inst->compact && G >= 4) {
+        const int64_t items = (std::max<int64_t>(N, 1) + 31) / 32 * G;
+        if (items >= 1024 && items <= 4096) {
+            c.staging = FSP_STAGING_GLOBAL;
+            c.warps_per_block = 2;
+            c.blocks_per_sm = 8;
+        }
+    }
     if (c.staging == FSP_STAGING_GLOBAL) {
         // Warps independent, records from L2/L1: every work item (a 32-node
         // batch and a slice of the couples) gets a warp of its own when the
