@@ -413,6 +413,7 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     if (!npw) return FSP_EINVAL;
     if (npw != 32 && ((c.staging && c.staging != FSP_STAGING_STREAMED) || !inst->compact || c.tail_slices > 1))
         return FSP_EINVAL;
+    const bool npw_free = c.nodes_per_thread == 0;
     c.nodes_per_thread = npw;
     // Default shape of a pool of a few thousand work items (32-node batches x
     // couple groups) for instances of at least four couple groups: global
@@ -598,6 +599,22 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     }
     if (!c.positions_per_tile) c.positions_per_tile = best_chunk(c.warps_per_block);
     if (c.positions_per_tile < 4) return FSP_EINVAL;
+    // Pools of under two and a half waves of 32-node block batches take 28
+    // nodes per warp by default (long scans of many couple groups): at 200x20
+    // the autotuner picks 28 from 16,384 to 131,072 nodes (131,072: 0.77 of the
+    // ALU peak against 0.69 with 32; the batches fill the waves better) and 32
+    // at 262,144 (3.4 waves).
+    if (npw_free && tiled == FSP_STAGING_STREAMED && inst->compact && G >= 4 && npad >= 64 &&
+        c.tail_slices <= 1) {
+        const int64_t slots = (int64_t)d.num_sms * c.blocks_per_sm;
+        const int64_t b32 = (std::max<int64_t>(N, 1) + 32 * c.warps_per_block - 1) / (32 * c.warps_per_block);
+        if (b32 * 2 < slots * 5) {
+            fsp_launch_config t = c;
+            t.nodes_per_thread = 28;
+            size_t smem = 0;
+            if (lanes_layout(inst, t, &smem) == FSP_OK) c.nodes_per_thread = 28;
+        }
+    }
     return fits(c.warps_per_block, tiled, c.positions_per_tile) ? FSP_OK : FSP_EINVAL;
 }
 
