@@ -51,8 +51,9 @@ def algorithmic_int_ops(n: int, m: int, depths: np.ndarray) -> float:
     return float(np.sum(P * (n + 4 * nu) + 2 * m * n + 2 * m * d))
 
 
-LANES_SOURCES = ("fsp_bound_lanes.cu", "fsp_lanes_device.cuh", "fsp_batch_scan.cuh", "fsp_plan.h", "fsp_internal.h",
-                 "fsp_ptx.cuh", "fsp_instance.cpp")
+LANES_SOURCES = ("fsp_bound_lanes.cu", "fsp_bound_streamed28.cu", "fsp_bound_global.cu", "fsp_bound_resident.cu",
+                 "fsp_lanes_device.cuh",
+                 "fsp_batch_scan.cuh", "fsp_plan.h", "fsp_internal.h", "fsp_ptx.cuh", "fsp_instance.cpp")
 
 
 def kernel_source_hash() -> str:

@@ -22,22 +22,27 @@
 // Per node the shared memory holds one flag bit per job and a row with A_k
 // (int32) and q_l (int16 with compact records, whose tails stay below 2^15;
 // int32 with 128-bit ones), so a block keeps hundreds of nodes in flight.
-// Large pools are bounded in depth order (fsp_order.cu).  Three staging
-// modes here (fsp_bound_split.cu and fsp_bound_warp.cu hold two more):
+// Large pools are bounded in depth order (fsp_order.cu).  The streamed kernel
+// and the host side of all the couple-lanes modes are here; the kernels of
+// the other modes are in files of their own:
 //   resident  all record groups are copied to shared memory once per block
 //             (one cp.async.bulk per group on one mbarrier); warps are then
 //             independent and claim 32-node batches from a per-block counter,
-//             so one warp's setup overlaps the others' scans;
+//             so one warp's setup overlaps the others' scans
+//             (fsp_bound_resident.cu);
 //   streamed  records too large for shared memory are staged in tiles of
 //             (group, positions) through two buffers, the whole block moving
 //             from tile to tile together (the paper's "does not fit" case).
 //             A pool too small to occupy every SM splits each block batch by
 //             couple groups over several work items, whose couple maxima meet
 //             in an atomic max on the zeroed bounds.  A variant holds one or
-//             two sets of 28 nodes per warp instead of 32 (fsp_lanes_streamed28);
+//             two sets of 28 nodes per warp instead of 32
+//             (fsp_bound_streamed28.cu);
 //   global    no tiles: every warp reads its groups' records from L2/L1
 //             through a register ring and takes its own work items, so a
-//             small pool spreads one warp per item over the GPU.
+//             small pool spreads one warp per item over the GPU
+//             (fsp_bound_global.cu);
+//   split     and warp staging: fsp_bound_split.cu, fsp_bound_warp.cu.
 // Global and one-set streamed staging keep the processing times in shared
 // memory when they fit.
 //
@@ -56,86 +61,10 @@
 #include <mutex>
 
 #include "fsp_internal.h"
-#include "fsp_batch_scan.cuh"
 #include "fsp_lanes_device.cuh"
 #include "fsp_ptx.cuh"
 
 namespace fspgb {
-
-// ---------------------------------------------------------------- resident
-template <bool WIDE, int MP>
-__global__ void __launch_bounds__(512, 1) fsp_lanes_resident(const LanesArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    int *ctr = reinterpret_cast<int *>(smem + 8);
-    uint8_t *sgp = smem + 16;
-    int2 *hcache = reinterpret_cast<int2 *>(smem + a.off_cache);
-    int2 *tcache = hcache + a.m * 32;
-    const unsigned char *tables = smem + a.off_tables;
-    uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * flag_words(a.n);
-    int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
-
-    // this block's share of the warp batches
-    const int64_t b0 = (int64_t)blockIdx.x * a.num_batches / gridDim.x;
-    const int64_t b1 = (int64_t)(blockIdx.x + 1) * a.num_batches / gridDim.x;
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        mbar_fence_init();
-        *ctr = 0;
-    }
-    for (int i = threadIdx.x; i < a.G * 64; i += blockDim.x) sgp[i] = a.gpairs[i];
-    load_sorted_heads(a, hcache, tcache);
-    __syncthreads();
-    const size_t group_bytes = (size_t)a.npad * 32 * a.rec_bytes;
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(bar, (uint32_t)(group_bytes * a.G));
-        for (int g = 0; g < a.G; ++g)
-            bulk_g2s(smem + a.off_tables + g * group_bytes, a.grec + g * group_bytes, (uint32_t)group_bytes, bar);
-    }
-    bool ready = false;
-    for (;;) {
-        int claim = 0;
-        if (lane == 0) claim = atomicAdd(ctr, 1);
-        const int64_t bt = b0 + __shfl_sync(kFull, claim, 0);
-        if (bt >= b1) break;
-        const int64_t x = node_at(a, bt * 32 + lane);
-        int bterm = 0;
-        const bool valid = lanes_setup<MP>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, hcache, tcache);
-        if (!ready) {
-            if (!mbar_wait_bounded(bar, 0, a.wait_limit)) {
-                if (lane == 0) report_status(a.status, (int32_t)FSP_ETIMEDOUT);
-                if (threadIdx.x == 0) mbar_wait_bounded(bar, 0, a.wait_limit);  // let the copy land
-                return;
-            }
-            ready = true;
-        }
-        int lb[32];
-#pragma unroll
-        for (int b = 0; b < 32; ++b) lb[b] = 0;
-        for (int g = 0; g < a.G; ++g) {
-            const int kk = sgp[2 * (g * 32 + lane)], ll = sgp[2 * (g * 32 + lane) + 1];
-            if (!WIDE) {
-                int u[32];
-#pragma unroll
-                for (int b = 0; b < 32; ++b) u[b] = 0;
-                scan_compact(reinterpret_cast<const uint2 *>(tables + g * group_bytes) + lane, a.npad, F, u);
-                couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, u, lb);
-            } else {
-                int u[32];
-#pragma unroll
-                for (int b = 0; b < 32; ++b) u[b] = 0;
-                scan_wide(reinterpret_cast<const int4 *>(tables + g * group_bytes) + lane, a.npad, F, u);
-                couple_epilogue<WIDE>(AQ, a.aq_stride, a.m, kk, ll, u, lb);
-            }
-        }
-        const int best = transpose_max(lb, lane);
-        if (x < a.N) a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
-        __syncwarp();  // the flag and row arrays are rewritten by the next batch
-    }
-    // the issuing thread never leaves while its copy may still be landing
-    if (threadIdx.x == 0 && !ready) mbar_wait_bounded(bar, 0, a.wait_limit);
-}
 
 // ---------------------------------------------------------------- streamed
 // PS: the block holds a shared-memory copy of the processing times
@@ -263,196 +192,6 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
     }
 }
 
-// ------------------------------------------------ streamed, 28-node sets
-// The streamed kernel with NS node sets of 28 per warp (NS = 1 or 2, compact
-// records): a block batch is 28 NS W nodes; each flag word yields its 28
-// predicates from four byte-wise conversions (bits 7, 15, 23 and 31 unused),
-// and with two sets every record read serves 56 nodes.  A warp sets up its
-// sets one after the other (lane = node, lanes 7, 15, 23 and 31 idle), and
-// the couple values of each group are reduced over the lanes at once, so no
-// per-node maxima are carried across groups.
-template <int MP, int NS>
-__global__ void __launch_bounds__(512, 1) fsp_lanes_streamed28(const LanesArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int W = blockDim.x >> 5;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    uint8_t *sgp = smem + 16;
-    int2 *hcache = reinterpret_cast<int2 *>(smem + a.off_cache);
-    int2 *tcache = hcache + a.m * 32;
-    const int nfw = flag_words(a.n);
-    uint32_t *F0 = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * NS * nfw;
-    uint32_t *F1 = F0 + (NS - 1) * nfw;
-    int32_t *AQ0 = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * NS * 32 * a.aq_stride;
-    int32_t *AQ1 = AQ0 + (NS - 1) * 32 * a.aq_stride;
-
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_fence_init();
-    }
-    for (int i = threadIdx.x; i < a.G * 64; i += blockDim.x) sgp[i] = a.gpairs[i];
-    load_sorted_heads(a, hcache, tcache);
-    __syncthreads();
-
-    TilePipe tp{bar, smem + a.off_tables, a.tile_stride, a.ntiles <= 2};
-    auto tile_issue = [&](uint32_t fill, int t) {
-        const int g = t / a.nchunks, ch = t - g * a.nchunks;
-        const int pos = min(a.chunk, a.npad - ch * a.chunk);
-        const unsigned char *src = a.grec + ((size_t)g * a.npad + (size_t)ch * a.chunk) * 32 * a.rec_bytes;
-        tp.issue(fill, src, (uint32_t)pos * 32u * a.rec_bytes);
-    };
-    // work items as in fsp_lanes_streamed, block batches of 28 NS W nodes
-    const uint32_t S = a.gslices > 1 ? (uint32_t)a.gslices : 1u;
-    const int64_t full = S > 1 ? a.full_batches : a.num_batches;
-    const int gper = S > 1 ? a.gper : a.G;
-    const int64_t items = full + (a.num_batches - full) * S;
-    auto slice_of = [&](int64_t it) { return it < full ? -1 : (int)((uint32_t)(it - full) % S); };
-    auto first_tile = [&](int sl) { return sl < 0 ? 0 : sl * gper * a.nchunks; };
-    if (threadIdx.x == 0 && (int64_t)blockIdx.x < items) {
-        if (tp.resident) {
-            tile_issue(0, 0);
-            if (a.ntiles == 2) tile_issue(1, 1);
-        } else {
-            tile_issue(0, first_tile(slice_of(blockIdx.x)));
-        }
-    }
-    // lane -> node of each set: lanes 7, 15, 23, 31 hold no node
-    const bool real = (kSet28 >> lane) & 1u;
-    const int r28 = set28_slot(lane);
-
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-        const int sl = slice_of(it);
-        const int64_t bt = sl < 0 ? it : full + (int64_t)((uint32_t)(it - full) / S);
-        const int64_t base = bt * (int64_t)(28 * NS * W) + warp * 28 * NS;
-        const int64_t x0 = real ? node_at(a, base + r28) : a.N;
-        const int64_t x1 = (NS == 2 && real) ? node_at(a, base + 28 + r28) : a.N;
-        bool valid0 = false, valid1 = false;
-        int bterm0 = 0, bterm1 = 0;
-#pragma unroll 1
-        for (int set = 0; set < NS; ++set) {
-            int bt_ = 0;
-            const bool v = lanes_setup<MP>(a, set ? x1 : x0, lane, set ? F1 : F0,
-                                           (set ? AQ1 : AQ0) + lane * a.aq_stride, bt_, hcache, tcache);
-            if (set) {
-                valid1 = v;
-                bterm1 = bt_;
-            } else {
-                valid0 = v;
-                bterm0 = bt_;
-            }
-        }
-        int M0 = 0, M1 = 0;
-        int u[28 * NS];
-#pragma unroll
-        for (int b = 0; b < 28 * NS; ++b) u[b] = 0;
-        int kk = 0, ll = 1;
-        const int t1 = sl < 0 ? a.ntiles : min(a.G, (sl + 1) * gper) * a.nchunks;
-        for (int t = first_tile(sl); t < t1; ++t) {
-            const int g = t / a.nchunks, ch = t - g * a.nchunks;
-            if (!tp.resident && threadIdx.x == 0) {
-                const int next = t + 1 < t1 ? t + 1
-                                 : (it + gridDim.x < items ? first_tile(slice_of(it + gridDim.x)) : -1);
-                if (next >= 0) tile_issue(tp.fill + 1, next);
-            }
-            if (!tp.wait(t, a.wait_limit)) {
-                if (threadIdx.x == 0) {
-                    report_status(a.status, (int32_t)FSP_ETIMEDOUT);
-                    tp.drain(a.wait_limit);
-                }
-                return;
-            }
-            const unsigned char *tb = tp.buf + tp.current(t) * tp.stride;
-            if (ch == 0) {
-#pragma unroll
-                for (int b = 0; b < 28 * NS; ++b) u[b] = 0;
-                kk = sgp[2 * (g * 32 + lane)];
-                ll = sgp[2 * (g * 32 + lane) + 1];
-            }
-            const int npos = min(a.chunk, a.npad - ch * a.chunk);
-            scan_compact28<NS>(reinterpret_cast<const uint2 *>(tb) + lane, npos, F0, F1, u);
-            if (ch == a.nchunks - 1) {
-                M0 = max(M0, set28_group_max<0>(AQ0, a.aq_stride, a.m, kk, ll, u, lane));
-                if constexpr (NS == 2) M1 = max(M1, set28_group_max<28>(AQ1, a.aq_stride, a.m, kk, ll, u, lane));
-            }
-            if (!tp.resident) {
-                __syncthreads();
-                ++tp.fill;
-            }
-        }
-#pragma unroll
-        for (int set = 0; set < NS; ++set) {
-            const int64_t x = set ? x1 : x0;
-            const bool valid = set ? valid1 : valid0;
-            const int best = max(set ? M1 : M0, set ? bterm1 : bterm0);
-            if (x < a.N) {
-                if (sl < 0)
-                    a.out[x] = valid ? best : FSP_LB_INVALID;
-                else if (!valid)
-                    a.out[x] = FSP_LB_INVALID;  // every slice finds the row invalid
-                else
-                    atomicMax(a.out + x, best);  // out was zeroed; bounds are >= 0
-            }
-        }
-        __syncwarp();  // the flag and row arrays are rewritten by the next batch
-    }
-}
-
-// ---------------------------------------------------------------- global
-// No shared-memory tiles: every warp reads its couple groups' records from
-// global memory (L2/L1) through the register ring of scan_compact_global, so
-// the warps of a block never wait for each other and a pool too small to fill
-// the GPU with block batches can give each work item a warp of its own.  Work
-// item it = 32-node batch it / S, couple slice it % S (S = gslices, slices of
-// gper groups); the grid's T warps take items w, w + T, w + 2T, ... in order.
-template <int MP, bool PS>
-__global__ void __launch_bounds__(512, 1) fsp_lanes_global(const LanesArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int W = blockDim.x >> 5;
-    uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * flag_words(a.n);
-    int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
-    const int64_t S = a.gslices > 1 ? a.gslices : 1;
-    const int64_t items = a.num_batches * S;
-    const int64_t T = (int64_t)gridDim.x * W;
-    // PS: the block's shared-memory copy of the processing times
-    int32_t *ptab = PS ? reinterpret_cast<int32_t *>(smem + a.off_ptab) : nullptr;
-    if (PS) {
-        load_ptab(a, ptab);
-        __syncthreads();
-    }
-    for (int64_t it = (int64_t)blockIdx.x * W + warp; it < items; it += T) {
-        const int64_t bt = it / S;
-        const int sl = (int)(it - bt * S);
-        const int64_t x = node_at(a, bt * 32 + lane);
-        int bterm = 0;
-        const bool valid = lanes_setup<MP, PS>(a, x, lane, F, AQ + lane * a.aq_stride, bterm, nullptr, nullptr, ptab);
-        int lb[32];
-#pragma unroll
-        for (int b = 0; b < 32; ++b) lb[b] = 0;
-        const int g0 = S > 1 ? sl * a.gper : 0, g1 = S > 1 ? min(a.G, g0 + a.gper) : a.G;
-        for (int g = g0; g < g1; ++g) {
-            const int kk = __ldg(a.gpairs + 2 * (g * 32 + lane)), ll = __ldg(a.gpairs + 2 * (g * 32 + lane) + 1);
-            int u[32];
-#pragma unroll
-            for (int b = 0; b < 32; ++b) u[b] = 0;
-            const uint2 *R = reinterpret_cast<const uint2 *>(a.grec) + (size_t)g * a.npad * 32 + lane;
-            scan_compact_global(R, a.npad, F, u);
-            couple_epilogue<false>(AQ, a.aq_stride, a.m, kk, ll, u, lb);
-        }
-        const int best = transpose_max(lb, lane);
-        if (x < a.N) {
-            if (S == 1)
-                a.out[x] = valid ? max(best, bterm) : FSP_LB_INVALID;
-            else if (!valid)
-                a.out[x] = FSP_LB_INVALID;  // every slice finds the row invalid
-            else
-                atomicMax(a.out + x, max(best, bterm));  // out was zeroed; bounds are >= 0
-        }
-        __syncwarp();  // the flag and row arrays are rewritten by the next item
-    }
-}
-
 // ---------------------------------------------------------------- host side
 namespace {
 
@@ -522,22 +261,15 @@ cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int npw, int
                                  cudaStream_t s) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
+    if (resident) return launch_resident_mp(a, WIDE, MP, grid, threads, smem, s);
+    if (npw != 32) return launch_streamed28_mp(a, MP, npw == 56 ? 2 : 1, grid, threads, smem, s);
     std::call_once(once, [] {
-        attr_err = set_smem_attr(fsp_lanes_resident<WIDE, MP>);
-        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP, false>);
+        attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP, false>);
         if (!WIDE && attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed<WIDE, MP, !WIDE>);
-        if (!WIDE && attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed28<MP, 1>);
-        if (!WIDE && attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_streamed28<MP, 2>);
     });
     if (attr_err != cudaSuccess) return attr_err;
     note_launches(1);
-    if (resident)
-        fsp_lanes_resident<WIDE, MP><<<grid, threads, smem, s>>>(a);
-    else if (!WIDE && npw == 56)
-        fsp_lanes_streamed28<MP, 2><<<grid, threads, smem, s>>>(a);
-    else if (!WIDE && npw == 28)
-        fsp_lanes_streamed28<MP, 1><<<grid, threads, smem, s>>>(a);
-    else if (!WIDE && a.off_ptab)
+    if (!WIDE && a.off_ptab)
         fsp_lanes_streamed<WIDE, MP, !WIDE><<<grid, threads, smem, s>>>(a);
     else
         fsp_lanes_streamed<WIDE, MP, false><<<grid, threads, smem, s>>>(a);
@@ -576,33 +308,6 @@ size_t lanes_budget(const fsp_instance *inst, int bps) {
                                (size_t)max_smem_per_sm(inst->device) / bps - 1024);
 }
 
-template <int MP>
-cudaError_t launch_global_variant(const LanesArgs &a, int grid, int threads, size_t smem, cudaStream_t s) {
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = set_smem_attr(fsp_lanes_global<MP, false>);
-        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_global<MP, true>);
-    });
-    if (attr_err != cudaSuccess) return attr_err;
-    note_launches(1);
-    if (a.off_ptab)
-        fsp_lanes_global<MP, true><<<grid, threads, smem, s>>>(a);
-    else
-        fsp_lanes_global<MP, false><<<grid, threads, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_global_mp(const LanesArgs &a, int mp, int grid, int threads, size_t smem, cudaStream_t s) {
-    switch (mp) {
-        case 8: return launch_global_variant<8>(a, grid, threads, smem, s);
-        case 12: return launch_global_variant<12>(a, grid, threads, smem, s);
-        case 16: return launch_global_variant<16>(a, grid, threads, smem, s);
-        case 20: return launch_global_variant<20>(a, grid, threads, smem, s);
-        case 24: return launch_global_variant<24>(a, grid, threads, smem, s);
-        default: return launch_global_variant<32>(a, grid, threads, smem, s);
-    }
-}
 
 }  // namespace
 

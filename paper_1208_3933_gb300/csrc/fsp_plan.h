@@ -71,6 +71,18 @@ struct PlanParams {
 // of its instance's couple groups.
 fsp_status build_plan(const fsp_pool_desc *pools, int32_t count, int32_t warps_per_block, int32_t couples_per_item,
                       int device, std::vector<LanesArgs> &args, std::vector<int2> &items, PlanParams &pp);
+// Launchers of the couple-lanes kernels that live in translation units of
+// their own (mp = the kernel's padded machine count 8, 12, 16, 20, 24 or 32):
+// streamed staging with ns sets of 28 nodes per warp (fsp_bound_streamed28.cu)
+// and global staging (fsp_bound_global.cu, a.off_ptab != 0: the processing
+// times in shared memory).
+cudaError_t launch_streamed28_mp(const LanesArgs &a, int mp, int ns, int grid, int threads, size_t smem,
+                                 cudaStream_t s);
+cudaError_t launch_global_mp(const LanesArgs &a, int mp, int grid, int threads, size_t smem, cudaStream_t s);
+// resident staging (fsp_bound_resident.cu), wide: 128-bit records
+cudaError_t launch_resident_mp(const LanesArgs &a, bool wide, int mp, int grid, int threads, size_t smem,
+                               cudaStream_t s);
+
 // Enqueues a plan already copied to the device: counter reset + kernel.
 fsp_status launch_plan(const LanesArgs *d_args, const int2 *d_items, int32_t *d_counter, const PlanParams &pp,
                        cudaStream_t s);
