@@ -23,7 +23,7 @@ namespace fspgb {
 // the GPU with block batches can give each work item a warp of its own.  Work
 // item it = 32-node batch it / S, couple slice it % S (S = gslices, slices of
 // gper groups); the grid's T warps take items w, w + T, w + 2T, ... in order.
-template <int MP, bool PS>
+template <int MP, int PS>
 __global__ void __launch_bounds__(512, 1) fsp_lanes_global(const LanesArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -33,10 +33,10 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_global(const LanesArgs a) {
     const int64_t S = a.gslices > 1 ? a.gslices : 1;
     const int64_t items = a.num_batches * S;
     const int64_t T = (int64_t)gridDim.x * W;
-    // PS: the block's shared-memory copy of the processing times
-    int32_t *ptab = PS ? reinterpret_cast<int32_t *>(smem + a.off_ptab) : nullptr;
-    if (PS) {
-        load_ptab(a, ptab);
+    // kPtabByte: the block's shared-memory copy of the processing times
+    void *ptab = PS == kPtabByte ? smem + a.off_ptab : nullptr;
+    if constexpr (PS == kPtabByte) {
+        load_ptab<kPtabByte>(a, ptab);
         __syncthreads();
     }
     for (int64_t it = (int64_t)blockIdx.x * W + warp; it < items; it += T) {
@@ -85,15 +85,15 @@ cudaError_t launch_global_variant(const LanesArgs &a, int grid, int threads, siz
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = set_smem_attr(fsp_lanes_global<MP, false>);
-        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_global<MP, true>);
+        attr_err = set_smem_attr(fsp_lanes_global<MP, kPtabNone>);
+        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_global<MP, kPtabByte>);
     });
     if (attr_err != cudaSuccess) return attr_err;
     note_launches(1);
     if (a.off_ptab)
-        fsp_lanes_global<MP, true><<<grid, threads, smem, s>>>(a);
+        fsp_lanes_global<MP, kPtabByte><<<grid, threads, smem, s>>>(a);
     else
-        fsp_lanes_global<MP, false><<<grid, threads, smem, s>>>(a);
+        fsp_lanes_global<MP, kPtabNone><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -45,10 +45,11 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 // ------------------------------------------------------------------ prep
-// PS: the block first copies the processing times to shared memory (when they
-// fit beside the warps' state), so the prefix pass reads each job's row in
-// one shared-memory latency instead of an L1 miss.
-template <int MP, bool PS>
+// PS = kPtabByte: the block first copies the processing times of a compact
+// instance to shared memory as bytes (when they fit beside the warps' state),
+// so the prefix pass reads each job's row in one shared-memory latency
+// instead of an L1 miss, a quarter of the bytes of an int32 copy.
+template <int MP, int PS>
 __global__ void __launch_bounds__(32 * kPrepWarps, 2) fsp_lanes_prep(const LanesArgs a, int64_t nbatch32) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -56,9 +57,9 @@ __global__ void __launch_bounds__(32 * kPrepWarps, 2) fsp_lanes_prep(const Lanes
     int2 *tcache = hcache + a.m * 32;
     uint32_t *F = reinterpret_cast<uint32_t *>(smem + a.off_flags) + (size_t)warp * flag_words(a.n);
     int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
-    int32_t *ptab = PS ? reinterpret_cast<int32_t *>(smem + a.off_ptab) : nullptr;
+    void *ptab = PS == kPtabByte ? smem + a.off_ptab : nullptr;
     load_sorted_heads(a, hcache, tcache);
-    if (PS) load_ptab(a, ptab);
+    if constexpr (PS == kPtabByte) load_ptab<kPtabByte>(a, ptab);
     __syncthreads();
     const int rows_words = 32 * a.aq_stride;
     // warps are independent: each takes 32-node batches by its global index
@@ -223,9 +224,9 @@ struct PrepLayout {
     size_t total;
 };
 
-// The prep block's shared memory; the processing times (pp, [n][mpad]) join
-// it when the total stays within half an SM (two prep blocks per SM) and the
-// table within 64 KB.
+// The prep block's shared memory; the processing times of a compact instance
+// ([n][mpad] bytes) join it when the total stays within half an SM (two prep
+// blocks per SM) and the table within 64 KB.
 PrepLayout prep_layout_for(const fsp_instance *inst) {
     PrepLayout L;
     L.off_cache = 0;
@@ -233,10 +234,10 @@ PrepLayout prep_layout_for(const fsp_instance *inst) {
     L.off_aq = (uint32_t)align_up(L.off_flags + (size_t)kPrepWarps * flag_words(inst->n) * 4, 128);
     L.total = align_up(L.off_aq + (size_t)kPrepWarps * 32 * aq_stride_for(inst->m, !inst->compact) * 4, 128);
     L.off_ptab = 0;
-    const size_t pbytes = (size_t)inst->n * inst->mpad * 4;
+    const size_t pbytes = (size_t)inst->n * inst->mpad;  // one byte per processing time
     const size_t budget = std::min((size_t)max_smem_per_block(inst->device),
                                    (size_t)max_smem_per_sm(inst->device) / 2 - 1024);
-    if (pbytes <= 64 * 1024 && L.total + pbytes <= budget) {
+    if (inst->compact && pbytes <= 64 * 1024 && L.total + pbytes <= budget) {
         L.off_ptab = (uint32_t)L.total;
         L.total = align_up(L.total + pbytes, 128);
     }
@@ -273,16 +274,16 @@ cudaError_t launch_pair(const LanesArgs &ap, int64_t nbatch32, size_t prep_smem,
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = set_smem_attr(fsp_lanes_prep<MP, false>);
-        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_prep<MP, true>);
+        attr_err = set_smem_attr(fsp_lanes_prep<MP, kPtabNone>);
+        if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_prep<MP, kPtabByte>);
         if (attr_err == cudaSuccess) attr_err = set_smem_attr(fsp_lanes_scan<WIDE, MP>);
     });
     if (attr_err != cudaSuccess) return attr_err;
     const bool ps = ap.off_ptab != 0;
     int per_sm = 0;
-    if ((ps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fsp_lanes_prep<MP, true>, 32 * kPrepWarps,
+    if ((ps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fsp_lanes_prep<MP, kPtabByte>, 32 * kPrepWarps,
                                                             prep_smem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fsp_lanes_prep<MP, false>, 32 * kPrepWarps,
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fsp_lanes_prep<MP, kPtabNone>, 32 * kPrepWarps,
                                                             prep_smem)) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
@@ -291,9 +292,9 @@ cudaError_t launch_pair(const LanesArgs &ap, int64_t nbatch32, size_t prep_smem,
     const int prep_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ap.num_batches, (int64_t)sms * per_sm));
     note_launches(2);
     if (ps)
-        fsp_lanes_prep<MP, true><<<prep_grid, 32 * kPrepWarps, prep_smem, s>>>(ap, nbatch32);
+        fsp_lanes_prep<MP, kPtabByte><<<prep_grid, 32 * kPrepWarps, prep_smem, s>>>(ap, nbatch32);
     else
-        fsp_lanes_prep<MP, false><<<prep_grid, 32 * kPrepWarps, prep_smem, s>>>(ap, nbatch32);
+        fsp_lanes_prep<MP, kPtabNone><<<prep_grid, 32 * kPrepWarps, prep_smem, s>>>(ap, nbatch32);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     fsp_lanes_scan<WIDE, MP><<<scan_grid, threads, scan_smem, s>>>(ac);

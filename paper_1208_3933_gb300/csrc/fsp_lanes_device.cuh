@@ -11,6 +11,7 @@
 
 #include "fsp_internal.h"
 #include "fsp_plan.h"
+#include "fsp_ptx.cuh"
 
 namespace fspgb {
 
@@ -69,6 +70,9 @@ __device__ __forceinline__ void warp_transpose32_n(uint32_t (&x)[NV], int lane) 
     }
 }
 
+// Where the setup reads the processing-time rows (lanes_setup's PS).
+constexpr int kPtabNone = 0, kPtabInt = 1, kPtabByte = 2;
+
 // Machines of the minima search handled together (MP is a multiple of 4).
 constexpr int kMinimaChunk = 4;
 // Nodes with at most this many unscheduled jobs take their minima by walking
@@ -90,19 +94,39 @@ __device__ __forceinline__ void load_sorted_heads(const LanesArgs &a, int2 *hcac
 // (bit b: job j unscheduled in the warp's node b; F holds 32 * ceil(n / 32)
 // words, which first hold the lanes' membership bitmaps), the lane's row
 // (A_k = r_k + S_k as int32, then q_l, see store_q) and the one-machine term
-// max_{l>=1} (A_l + q_l).  Returns whether the row is valid.  With PS the
-// processing-time rows are read from ptab, the block's shared-memory copy of
-// pp ([n][mpad]), instead of global memory.
-template <int MP, bool PS = false>
+// max_{l>=1} (A_l + q_l).  Returns whether the row is valid.  PS says where
+// the processing-time rows are read: kPtabNone from pp in global memory,
+// kPtabInt from ptab, the block's shared-memory copy of pp ([n][mpad] int32),
+// kPtabByte from ptab holding them as bytes ([n][mpad] uint8, compact
+// instances only: every p < 256), a quarter of the shared-memory traffic for
+// one byte extract per value.
+template <int MP, int PS = kPtabNone>
 __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int lane, uint32_t *F, int32_t *myrow,
                                             int &bterm, const int2 *hcache = nullptr,
-                                            const int2 *tcache = nullptr, const int32_t *ptab = nullptr) {
+                                            const int2 *tcache = nullptr, const void *ptab = nullptr) {
     const int n = a.n, m = a.m, nw = (n + 31) >> 5;
-    // row q-th int4 of job j's processing times
+    // job j's row of processing times (kPtabByte: words of four bytes)
     auto prow = [&](int j) {
-        return reinterpret_cast<const int4 *>((PS ? ptab : a.pp) + (size_t)j * a.mpad);
+        if constexpr (PS == kPtabByte)
+            return static_cast<const uint32_t *>(ptab) + (size_t)j * (a.mpad >> 2);
+        else
+            return reinterpret_cast<const int4 *>(
+                (PS == kPtabInt ? static_cast<const int32_t *>(ptab) : a.pp) + (size_t)j * a.mpad);
     };
-    auto pld = [&](const int4 *r, int q) { return PS ? r[q] : __ldg(r + q); };
+    // machines 4q .. 4q+3 of a row; columns past the instance's own padding
+    // read as zeros (no branch)
+    auto pld = [&](auto r, int q) {
+        const bool in = 4 * q < a.mpad;
+        if constexpr (PS == kPtabByte) {
+            const uint32_t w = in ? r[q] : 0u;
+            return make_int4((int)__byte_perm(w, 0u, 0x4440u), (int)__byte_perm(w, 0u, 0x4441u),
+                             (int)__byte_perm(w, 0u, 0x4442u), (int)__byte_perm(w, 0u, 0x4443u));
+        } else if constexpr (PS == kPtabInt) {
+            return in ? r[q] : make_int4(0, 0, 0, 0);
+        } else {
+            return in ? __ldg(r + q) : make_int4(0, 0, 0, 0);
+        }
+    };
     bool valid = false;
     int d = 0;
     if (x < a.N) {
@@ -127,6 +151,9 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     }
     const int16_t *row = a.nodes + x * (int64_t)n;
     const int dv = valid ? d : 0;
+    // the lines of the prefix are requested from DRAM at once; the pass
+    // below then waits on L2, not on one DRAM round trip per four jobs
+    prefetch_l2_range(row, 2 * dv);
     bool bad = false;
     // membership of job j (clamped into range: an invalid row is discarded)
     auto mark = [&](int j) {
@@ -141,18 +168,14 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     // dependent steps for 20 machines instead of 80) and their processing
     // times are loaded together
     auto take4 = [&](int j0, int j1, int j2, int j3) {
-        const int4 *p0 = prow(mark(j0));
-        const int4 *p1 = prow(mark(j1));
-        const int4 *p2 = prow(mark(j2));
-        const int4 *p3 = prow(mark(j3));
+        const auto p0 = prow(mark(j0));
+        const auto p1 = prow(mark(j1));
+        const auto p2 = prow(mark(j2));
+        const auto p3 = prow(mark(j3));
         int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
 #pragma unroll
         for (int q = 0; q < MP / 4; ++q) {
-            const bool in = 4 * q < a.mpad;
-            const int4 v0 = in ? pld(p0, q) : make_int4(0, 0, 0, 0);
-            const int4 v1 = in ? pld(p1, q) : make_int4(0, 0, 0, 0);
-            const int4 v2 = in ? pld(p2, q) : make_int4(0, 0, 0, 0);
-            const int4 v3 = in ? pld(p3, q) : make_int4(0, 0, 0, 0);
+            const int4 v0 = pld(p0, q), v1 = pld(p1, q), v2 = pld(p2, q), v3 = pld(p3, q);
             const int q0[4] = {v0.x, v0.y, v0.z, v0.w}, q1[4] = {v1.x, v1.y, v1.z, v1.w};
             const int q2[4] = {v2.x, v2.y, v2.z, v2.w}, q3[4] = {v3.x, v3.y, v3.z, v3.w};
 #pragma unroll
@@ -168,12 +191,11 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
         }
     };
     auto take = [&](int j) {
-        const int4 *pj = prow(mark(j));
+        const auto pj = prow(mark(j));
         int c = 0;
 #pragma unroll
         for (int q = 0; q < MP / 4; ++q) {
-            // columns past the instance's own padding read as zeros (no branch)
-            const int4 v = 4 * q < a.mpad ? pld(pj, q) : make_int4(0, 0, 0, 0);
+            const int4 v = pld(pj, q);
             const int pv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -230,11 +252,11 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
                 while (un) {
                     const int j = w * 32 + __ffs(un) - 1;
                     un &= un - 1u;
-                    const int4 *pj = prow(j);
+                    const auto pj = prow(j);
                     int est = C[0], prev = 0;
 #pragma unroll
                     for (int q = 0; q < MP / 4; ++q) {
-                        const int4 v = 4 * q < a.mpad ? pld(pj, q) : make_int4(0, 0, 0, 0);
+                        const int4 v = pld(pj, q);
                         const int pv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
@@ -270,11 +292,11 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
                 while (un) {
                     const int j = w * 32 + __ffs(un) - 1;
                     un &= un - 1u;
-                    const int4 *pj = prow(j);
+                    const auto pj = prow(j);
                     int pv[MP];
 #pragma unroll
                     for (int q = 0; q < MP / 4; ++q) {
-                        const int4 v = 4 * q < a.mpad ? pld(pj, q) : make_int4(0, 0, 0, 0);
+                        const int4 v = pld(pj, q);
                         pv[4 * q] = v.x;
                         pv[4 * q + 1] = v.y;
                         pv[4 * q + 2] = v.z;
@@ -434,13 +456,24 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
 }
 
 // Copies pp ([n][mpad] int32, mpad a multiple of 4) into the block's
-// shared-memory table; every thread of the block takes part, the caller
-// synchronises before the table is read.
-__device__ __forceinline__ void load_ptab(const LanesArgs &a, int32_t *ptab) {
+// shared-memory table, as int32 (kPtabInt) or as bytes (kPtabByte, four
+// machines to a word, machine 4q + e in byte e of word q); every thread of the
+// block takes part, the caller synchronises before the table is read.
+template <int PS>
+__device__ __forceinline__ void load_ptab(const LanesArgs &a, void *ptab) {
+    static_assert(PS == kPtabInt || PS == kPtabByte, "a shared-memory table");
     const int4 *src = reinterpret_cast<const int4 *>(a.pp);
-    int4 *dst = reinterpret_cast<int4 *>(ptab);
     const int nq = a.n * a.mpad / 4;
-    for (int i = threadIdx.x; i < nq; i += blockDim.x) dst[i] = __ldg(src + i);
+    if constexpr (PS == kPtabInt) {
+        int4 *dst = static_cast<int4 *>(ptab);
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) dst[i] = __ldg(src + i);
+    } else {
+        uint32_t *dst = static_cast<uint32_t *>(ptab);
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+            const int4 v = __ldg(src + i);
+            dst[i] = (uint32_t)v.x | ((uint32_t)v.y << 8) | ((uint32_t)v.z << 16) | ((uint32_t)v.w << 24);
+        }
+    }
 }
 
 // One slack update of the 32 nodes for a couple-lanes record r (the

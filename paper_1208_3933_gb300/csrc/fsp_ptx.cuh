@@ -1,7 +1,7 @@
 // fsp_ptx.cuh -- inline-PTX helpers shared by the bounding kernels:
-// mbarrier init / expect-tx / bounded wait, and the bulk (non-tensor)
-// global->shared copy that stages Johnson-record tiles (sm_90+ PTX, built for
-// sm_103a).
+// mbarrier init / expect-tx / bounded wait, the bulk (non-tensor)
+// global->shared copy that stages Johnson-record tiles, and an L2 prefetch
+// of a byte range (sm_90+ PTX, built for sm_103a).
 #pragma once
 
 #include <cstdint>
@@ -54,6 +54,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// Asks the memory system to bring the bytes [p, p + bytes) into L2 (a hint:
+// nothing is loaded into registers).  Every address requested lies inside
+// the range, so only lines that hold some of its bytes are touched.
+__device__ __forceinline__ void prefetch_l2_range(const void *p, int bytes) {
+    if (bytes <= 0) return;
+    const char *c = static_cast<const char *>(p);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c));
+    for (int o = 128 - (int)(reinterpret_cast<uintptr_t>(c) & 127); o < bytes; o += 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
 }
 
 // Writes a device-side error code to the instance's host-mapped status word.
