@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_global(const LanesArgs a) {
     // kPtabByte: the block's shared-memory copy of the processing times
     void *ptab = PS == kPtabByte ? smem + a.off_ptab : nullptr;
     if constexpr (PS == kPtabByte) {
-        load_ptab<kPtabByte>(a, ptab);
+        load_ptab(a, ptab);
         __syncthreads();
     }
     for (int64_t it = (int64_t)blockIdx.x * W + warp; it < items; it += T) {

@@ -67,7 +67,7 @@
 namespace fspgb {
 
 // ---------------------------------------------------------------- streamed
-// PS: the block holds a shared-memory copy of the processing times
+// PS: the block holds a shared-memory copy of the processing times as bytes
 // (a.off_ptab), which the setup reads instead of global memory.
 template <bool WIDE, int MP, bool PS>
 __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) {
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
     for (int i = threadIdx.x; i < a.G * 64; i += blockDim.x) sgp[i] = a.gpairs[i];
     load_sorted_heads(a, hcache, tcache);
     void *ptab = PS ? smem + a.off_ptab : nullptr;
-    if constexpr (PS) load_ptab<kPtabInt>(a, ptab);
+    if constexpr (PS) load_ptab(a, ptab);
     __syncthreads();
 
     TilePipe tp{bar, smem + a.off_tables, a.tile_stride, a.ntiles <= 2};
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_streamed(const LanesArgs a) 
         const int64_t bt = sl < 0 ? it : full + (int64_t)((uint32_t)(it - full) / S);
         const int64_t x = node_at(a, bt * (int64_t)(32 * W) + warp * 32 + lane);
         int bterm = 0;
-        const bool valid = lanes_setup<MP, PS ? kPtabInt : kPtabNone>(a, x, lane, F, AQ + lane * a.aq_stride, bterm,
+        const bool valid = lanes_setup<MP, PS ? kPtabByte : kPtabNone>(a, x, lane, F, AQ + lane * a.aq_stride, bterm,
                                                                        hcache, tcache, ptab);
         int lb[32];
         int uf[32];
@@ -206,14 +206,13 @@ struct LanesLayout {
 };
 
 // Global and one-set streamed staging copy the processing-time rows (pp,
-// [n][mpad]) to shared memory when they fit the block's budget beside
+// [n][mpad], as bytes) to shared memory when they fit the block's budget beside
 // everything else (at most 64 KB): the setup's prefix recurrence, walks and
 // release times then read a row in one shared-memory latency instead of an
-// L1 miss.  Entry size: 4 bytes (int32, one-set streamed staging) or 1
-// (global staging; compact instances, every p < 256).
+// L1 miss.  One byte per entry (compact instances: every p < 256).
 constexpr size_t kPtabMaxBytes = 64 * 1024;
-void add_ptab(LanesLayout &L, const fsp_instance *inst, size_t budget, size_t entry_bytes) {
-    const size_t bytes = (size_t)inst->n * inst->mpad * entry_bytes;
+void add_ptab(LanesLayout &L, const fsp_instance *inst, size_t budget) {
+    const size_t bytes = (size_t)inst->n * inst->mpad;
     const size_t off = align_up(L.total, 128);
     L.off_ptab = 0;
     if (bytes <= kPtabMaxBytes && off + bytes <= budget) {
@@ -246,7 +245,7 @@ LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident,
     // the one-set streamed kernel keeps a shared copy of the processing times
     // when it fits (compact records); the others read them from global memory
     L.off_ptab = 0;
-    if (!resident && npw == 32 && inst->compact) add_ptab(L, inst, budget, 4);
+    if (!resident && npw == 32 && inst->compact) add_ptab(L, inst, budget);
     return L;
 }
 
@@ -298,7 +297,7 @@ LanesLayout global_layout_for(const fsp_instance *inst, int warps, size_t budget
     L.off_aq = (uint32_t)align_up((size_t)warps * flag_words(inst->n) * 4, 128);
     L.aq_stride = aq_stride_for(inst->m, !inst->compact);
     L.total = align_up(L.off_aq + (size_t)warps * 32 * L.aq_stride * 4, 128);
-    if (inst->compact) add_ptab(L, inst, budget, 1);
+    if (inst->compact) add_ptab(L, inst, budget);
     return L;
 }
 

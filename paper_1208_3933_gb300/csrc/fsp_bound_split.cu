@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(32 * kPrepWarps, 2) fsp_lanes_prep(const Lanes
     int32_t *AQ = reinterpret_cast<int32_t *>(smem + a.off_aq) + (size_t)warp * 32 * a.aq_stride;
     void *ptab = PS == kPtabByte ? smem + a.off_ptab : nullptr;
     load_sorted_heads(a, hcache, tcache);
-    if constexpr (PS == kPtabByte) load_ptab<kPtabByte>(a, ptab);
+    if constexpr (PS == kPtabByte) load_ptab(a, ptab);
     __syncthreads();
     const int rows_words = 32 * a.aq_stride;
     // warps are independent: each takes 32-node batches by its global index

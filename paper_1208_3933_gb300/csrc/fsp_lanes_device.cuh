@@ -71,7 +71,7 @@ __device__ __forceinline__ void warp_transpose32_n(uint32_t (&x)[NV], int lane) 
 }
 
 // Where the setup reads the processing-time rows (lanes_setup's PS).
-constexpr int kPtabNone = 0, kPtabInt = 1, kPtabByte = 2;
+constexpr int kPtabNone = 0, kPtabByte = 1;
 
 // Machines of the minima search handled together (MP is a multiple of 4).
 constexpr int kMinimaChunk = 4;
@@ -96,10 +96,9 @@ __device__ __forceinline__ void load_sorted_heads(const LanesArgs &a, int2 *hcac
 // (A_k = r_k + S_k as int32, then q_l, see store_q) and the one-machine term
 // max_{l>=1} (A_l + q_l).  Returns whether the row is valid.  PS says where
 // the processing-time rows are read: kPtabNone from pp in global memory,
-// kPtabInt from ptab, the block's shared-memory copy of pp ([n][mpad] int32),
-// kPtabByte from ptab holding them as bytes ([n][mpad] uint8, compact
-// instances only: every p < 256), a quarter of the shared-memory traffic for
-// one byte extract per value.
+// kPtabByte from ptab, the block's shared-memory copy of pp as bytes
+// ([n][mpad] uint8, compact instances only: every p < 256), a quarter of the
+// shared-memory traffic of an int32 copy for one byte extract per value.
 template <int MP, int PS = kPtabNone>
 __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int lane, uint32_t *F, int32_t *myrow,
                                             int &bterm, const int2 *hcache = nullptr,
@@ -110,8 +109,7 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
         if constexpr (PS == kPtabByte)
             return static_cast<const uint32_t *>(ptab) + (size_t)j * (a.mpad >> 2);
         else
-            return reinterpret_cast<const int4 *>(
-                (PS == kPtabInt ? static_cast<const int32_t *>(ptab) : a.pp) + (size_t)j * a.mpad);
+            return reinterpret_cast<const int4 *>(a.pp + (size_t)j * a.mpad);
     };
     // machines 4q .. 4q+3 of a row; columns past the instance's own padding
     // read as zeros (no branch)
@@ -121,8 +119,6 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
             const uint32_t w = in ? r[q] : 0u;
             return make_int4((int)__byte_perm(w, 0u, 0x4440u), (int)__byte_perm(w, 0u, 0x4441u),
                              (int)__byte_perm(w, 0u, 0x4442u), (int)__byte_perm(w, 0u, 0x4443u));
-        } else if constexpr (PS == kPtabInt) {
-            return in ? r[q] : make_int4(0, 0, 0, 0);
         } else {
             return in ? __ldg(r + q) : make_int4(0, 0, 0, 0);
         }
@@ -455,24 +451,17 @@ __device__ __forceinline__ bool lanes_setup(const LanesArgs &a, int64_t x, int l
     return valid;
 }
 
-// Copies pp ([n][mpad] int32, mpad a multiple of 4) into the block's
-// shared-memory table, as int32 (kPtabInt) or as bytes (kPtabByte, four
-// machines to a word, machine 4q + e in byte e of word q); every thread of the
-// block takes part, the caller synchronises before the table is read.
-template <int PS>
+// Copies pp ([n][mpad] int32, mpad a multiple of 4, every entry < 256) into
+// the block's shared-memory table as bytes, four machines to a word (machine
+// 4q + e in byte e of word q); every thread of the block takes part, the
+// caller synchronises before the table is read.
 __device__ __forceinline__ void load_ptab(const LanesArgs &a, void *ptab) {
-    static_assert(PS == kPtabInt || PS == kPtabByte, "a shared-memory table");
     const int4 *src = reinterpret_cast<const int4 *>(a.pp);
+    uint32_t *dst = static_cast<uint32_t *>(ptab);
     const int nq = a.n * a.mpad / 4;
-    if constexpr (PS == kPtabInt) {
-        int4 *dst = static_cast<int4 *>(ptab);
-        for (int i = threadIdx.x; i < nq; i += blockDim.x) dst[i] = __ldg(src + i);
-    } else {
-        uint32_t *dst = static_cast<uint32_t *>(ptab);
-        for (int i = threadIdx.x; i < nq; i += blockDim.x) {
-            const int4 v = __ldg(src + i);
-            dst[i] = (uint32_t)v.x | ((uint32_t)v.y << 8) | ((uint32_t)v.z << 16) | ((uint32_t)v.w << 24);
-        }
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+        const int4 v = __ldg(src + i);
+        dst[i] = (uint32_t)v.x | ((uint32_t)v.y << 8) | ((uint32_t)v.z << 16) | ((uint32_t)v.w << 24);
     }
 }
 

@@ -40,8 +40,7 @@ struct LanesArgs {
     uint32_t tile_stride;
     uint32_t off_flags, off_aq;  // split scan: off_flags = the prepared-state region
     uint32_t off_cache;   // first 32 entries of each machine's head/tail-sorted list (0 = none)
-    uint32_t off_ptab;    // shared-memory copy of pp, [n][mpad] int32 (one-set streamed) or bytes (global
-                          // staging, split prep); 0 = none: read pp from global
+    uint32_t off_ptab;    // shared-memory copy of pp as bytes, [n][mpad] uint8 (0 = none: read pp from global)
     const int32_t *order; // slot -> node (depth order), or null: slot i bounds node i
     uint32_t *scratch;    // split kernels: prepared state, [32-node batch][sb_words]
     int32_t sb_words;
