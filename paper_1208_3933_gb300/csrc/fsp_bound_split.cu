@@ -62,8 +62,11 @@ __global__ void __launch_bounds__(32 * kPrepWarps, 2) fsp_lanes_prep(const Lanes
     if constexpr (PS == kPtabByte) load_ptab(a, ptab);
     __syncthreads();
     const int rows_words = 32 * a.aq_stride;
-    // warps are independent: each takes 32-node batches by its global index
-    for (int64_t b32 = (int64_t)blockIdx.x * kPrepWarps + warp; b32 < nbatch32;
+    // warps are independent: warp w of block i takes the 32-node batches
+    // w * gridDim.x + i, then every gridDim.x * kPrepWarps after it, so the
+    // batches of a depth-ordered pool (deeper = longer setup) are dealt
+    // across the blocks instead of the deepest ones landing on a few SMs
+    for (int64_t b32 = (int64_t)warp * gridDim.x + blockIdx.x; b32 < nbatch32;
          b32 += (int64_t)gridDim.x * kPrepWarps) {
         const int64_t x = node_at(a, b32 * 32 + lane);
         int bterm = 0;
@@ -289,7 +292,9 @@ cudaError_t launch_pair(const LanesArgs &ap, int64_t nbatch32, size_t prep_smem,
         cudaGetLastError();
         per_sm = 1;
     }
-    const int prep_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ap.num_batches, (int64_t)sms * per_sm));
+    // every SM takes per_sm blocks (the batches are dealt across them), but no
+    // block is launched without a batch of its own
+    const int prep_grid = (int)std::max<int64_t>(1, std::min<int64_t>(nbatch32, (int64_t)sms * per_sm));
     note_launches(2);
     if (ps)
         fsp_lanes_prep<MP, kPtabByte><<<prep_grid, 32 * kPrepWarps, prep_smem, s>>>(ap, nbatch32);
