@@ -757,7 +757,7 @@ def run_gpu(args, world, rank, local):
                      "kernel_ms_mean": mean_kernel_s * 1e3, "kernel": kernel_name(launch),
                      "timed": "CUDA events around each step's fsp_bound_pool on its stream: the bounding "
                               "kernel(s) of the launch shape plus, for pools of >= 8192 nodes and >= 64 jobs, the "
-                              "three small depth-order kernels"},
+                              "two small depth-order kernels"},
         "cpu_baseline": None if world > 1 else {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                          "sample": f"first {cpu_sample} nodes of the pool, plain C oracle on {cpu_threads} threads, "
                                    f"best of 3 runs of {cpu_s:.2f} s",

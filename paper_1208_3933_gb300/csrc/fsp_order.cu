@@ -20,8 +20,7 @@ namespace fspgb {
 namespace {
 
 constexpr int kOrderThreads = 256;
-constexpr int kOrderBlocks = 48;     // blocks of the histogram and scatter passes
-constexpr int kOrderScanMax = 12000;  // bins x blocks scanned in shared memory (< 48 KB)
+constexpr int kOrderBlocks = 48;  // blocks of the histogram and scatter passes
 
 __device__ __forceinline__ int depth_bin(int d, int n) { return min(max(d, -1), n + 1) + 1; }  // [0, n + 2]
 
@@ -39,57 +38,50 @@ __global__ void __launch_bounds__(kOrderThreads) order_hist(const int32_t *depth
     for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[(int64_t)i * gridDim.x + blockIdx.x] = h[i];
 }
 
-// Exclusive scan of hist in place, bin-major: block k's nodes of bin b start
-// after all nodes of smaller bins and of bin b in blocks before k.  One block:
-// hist is staged in shared memory (at most kOrderScanMax entries), each
-// thread sums a contiguous segment, the 1024 sums are scanned with warp
-// shuffles, and each thread rewrites its segment.
-__global__ void __launch_bounds__(1024) order_scan(int32_t *hist, int total) {
-    extern __shared__ int32_t sh[];
-    __shared__ int32_t wsum[32];
-    for (int i = threadIdx.x; i < total; i += blockDim.x) sh[i] = hist[i];
-    __syncthreads();
+// Block k writes its nodes at its offsets, counting within a bin in shared
+// memory (the order among equal depths is arbitrary).  Block k's first slot
+// in bin b lies after every node of a smaller bin and after bin b's nodes in
+// blocks before k; each block takes these offsets from the histogram itself
+// (hist is nb x blocks, a few thousand entries read from L2): thread t sums a
+// contiguous segment of bins, the segment sums are scanned across the block
+// with warp shuffles, and each thread then walks its segment.
+__global__ void __launch_bounds__(kOrderThreads) order_scatter(const int32_t *depths, int64_t N, int n, int64_t per,
+                                                               const int32_t *hist, int32_t *order) {
+    extern __shared__ int32_t cur[];  // [nb] slots, then [nb] bin totals
+    __shared__ int32_t wsum[kOrderThreads / 32];
+    const int nb = n + 3, K = gridDim.x, k = blockIdx.x;
+    int32_t *tot = cur + nb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int seg = (total + 1023) / 1024;
-    const int i0 = min(total, (int)threadIdx.x * seg), i1 = min(total, i0 + seg);
+    const int seg = (nb + kOrderThreads - 1) / kOrderThreads;
+    const int b0 = min(nb, (int)threadIdx.x * seg), b1 = min(nb, b0 + seg);
     int sum = 0;
-    for (int i = i0; i < i1; ++i) sum += sh[i];
-    int incl = sum;  // inclusive scan across the warp
+    for (int b = b0; b < b1; ++b) {
+        const int32_t *hb = hist + (int64_t)b * K;
+        int t = 0, before = 0;
+        for (int kk = 0; kk < K; ++kk) {
+            const int h = __ldg(hb + kk);
+            t += h;
+            before += kk < k ? h : 0;
+        }
+        cur[b] = before;
+        tot[b] = t;
+        sum += t;
+    }
+    int incl = sum;  // inclusive scan of the segment sums across the warp
     for (int off = 1; off < 32; off <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += t;
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
     }
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    if (warp == 0) {
-        const int w = wsum[lane];
-        int wi = w;
-        for (int off = 1; off < 32; off <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, wi, off);
-            if (lane >= off) wi += t;
-        }
-        wsum[lane] = wi - w;  // exclusive over warps
+    int run = incl - sum;  // exclusive within the warp, plus the warps before
+    for (int w = 0; w < warp; ++w) run += wsum[w];
+    for (int b = b0; b < b1; ++b) {
+        cur[b] += run;
+        run += tot[b];
     }
     __syncthreads();
-    int run = wsum[warp] + incl - sum;
-    for (int i = i0; i < i1; ++i) {
-        const int v = sh[i];
-        sh[i] = run;
-        run += v;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < total; i += blockDim.x) hist[i] = sh[i];
-}
-
-// Block k writes its nodes at its offsets, counting within a bin in shared
-// memory (the order among equal depths is arbitrary).
-__global__ void __launch_bounds__(kOrderThreads) order_scatter(const int32_t *depths, int64_t N, int n, int64_t per,
-                                                               const int32_t *offs, int32_t *order) {
-    extern __shared__ int32_t cur[];
-    const int nb = n + 3;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = offs[(int64_t)i * gridDim.x + blockIdx.x];
-    __syncthreads();
-    const int64_t x0 = (int64_t)blockIdx.x * per, x1 = min(N, x0 + per);
+    const int64_t x0 = (int64_t)k * per, x1 = min(N, x0 + per);
     for (int64_t x = x0 + threadIdx.x; x < x1; x += blockDim.x)
         order[atomicAdd(&cur[depth_bin(__ldg(depths + x), n)], 1)] = (int32_t)x;
 }
@@ -131,8 +123,8 @@ fsp_status depth_order(const fsp_instance *inst, const int32_t *depths, int64_t 
     fsp_status st = scratch_pool(inst->device, &pool);
     if (st != FSP_OK) return st;
     const int nb = inst->n + 3;
-    const int blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>({(int64_t)kOrderBlocks, (int64_t)(kOrderScanMax / nb), (N + kOrderThreads - 1) / kOrderThreads}));
+    const int blocks =
+        (int)std::max<int64_t>(1, std::min<int64_t>(kOrderBlocks, (N + kOrderThreads - 1) / kOrderThreads));
     const int64_t per = (N + blocks - 1) / blocks;
     const int total = nb * blocks;
     int32_t *buf = nullptr;
@@ -142,10 +134,9 @@ fsp_status depth_order(const fsp_instance *inst, const int32_t *depths, int64_t 
     }
     int32_t *hist = buf + N;
     const size_t hsmem = sizeof(int32_t) * nb;
-    note_launches(3);
+    note_launches(2);
     order_hist<<<blocks, kOrderThreads, hsmem, s>>>(depths, N, inst->n, per, hist);
-    order_scan<<<1, 1024, sizeof(int32_t) * total, s>>>(hist, total);
-    order_scatter<<<blocks, kOrderThreads, hsmem, s>>>(depths, N, inst->n, per, hist, buf);
+    order_scatter<<<blocks, kOrderThreads, 2 * hsmem, s>>>(depths, N, inst->n, per, hist, buf);
     if (cudaGetLastError() != cudaSuccess) {
         cudaFreeAsync(buf, s);
         return FSP_ECUDA;

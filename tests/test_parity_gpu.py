@@ -550,6 +550,24 @@ def test_depth_ordered_pools_with_invalid_and_extreme_depths(gpu_lib):
             assert (got[(depths < 0) | (depths > n)] == fsp.FSP_LB_INVALID).all()
 
 
+def test_depth_order_with_more_depth_bins_than_threads(gpu_lib):
+    """Depth order of a pool whose jobs give more depth bins (n + 3 = 303)
+    than the scatter kernel has threads, so each thread sums a segment of
+    several bins: every bound lands at its node, invalid depths included."""
+    fsp = gpu_lib
+    rng = np.random.default_rng(78)
+    n, m = 300, 4
+    p = rng.integers(1, 100, (n, m), dtype=np.int32)
+    with fsp.Instance(p) as inst:
+        for N in (8192, 12345):
+            rows, depths = workloads.random_pool(rng, n, N, max_depth=n + 1)
+            depths[rng.choice(N, 40, replace=False)] = -1
+            depths[rng.choice(N, 40, replace=False)] = n + 1
+            depths[:n + 1] = np.arange(n + 1)
+            got = gpu_bounds(fsp, inst, rows, depths)
+            assert np.array_equal(got, oracle_bounds(p, rows, depths)), N
+
+
 def test_host_entry_point_mixed_pinned_and_pageable(gpu_lib):
     """fsp_bound_pool_host with a mix of page-locked and pageable buffers
     (pinned rows, pageable depths) and with all three page-locked: both give
