@@ -112,11 +112,12 @@ typedef struct fsp_launch_config {
                                     1..8, split/warp staging 1 or 2, global staging 1..16; at most
                                     16 warps per SM) */
     int32_t pairs_per_tile;      /* lockstep: couples staged in shared memory at a time;
-                                    lanes, streamed and global: couples per work item, rounded up to whole
-                                    groups of 32 (fewer than all: a block batch is split by
-                                    couples over several work items, for pools too small to
-                                    occupy every SM); other stagings: all couples.  0 = chosen
-                                    from the pool size; the resolved value is P for all. */
+                                    lanes, streamed, split and global: couples per work item,
+                                    rounded up to whole groups of 32 (fewer than all: a block
+                                    batch is split by couples over several work items, for pools
+                                    too small to occupy every SM); other stagings: all couples.
+                                    0 = chosen from the pool size; the resolved value is P for
+                                    all. */
     int32_t warps_per_block;     /* lanes: 1..16 warps of 32 nodes */
     int32_t positions_per_tile;  /* lanes, streamed/split/warp: Johnson positions per tile (multiple of 4) */
     int32_t staging;             /* lanes: FSP_STAGING_* */

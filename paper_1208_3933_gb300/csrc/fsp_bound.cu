@@ -416,18 +416,22 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
     const bool npw_free = c.nodes_per_thread == 0;
     c.nodes_per_thread = npw;
     // Default shape of a pool of a few thousand work items (32-node batches x
-    // couple groups) for instances of at least four couple groups: global
-    // staging with two warps per block and eight blocks per SM, couple slices
-    // from the pool size.  At 200x20 the autotuner picks it for 8,192 and
-    // 16,384 nodes (1,536 and 3,072 items) and streamed or split staging for
-    // 4,096 and 32,768.
+    // couple groups) for instances of at least four couple groups: split
+    // staging (the setups in a prep kernel of their own, the scan in work
+    // items of one couple group, two above 4,096 items), in the shapes the
+    // autotuner picks at 200x20: 6 warps x 2 blocks per SM below 1,024 items
+    // (4,096 nodes: 0.18 of the ALU peak against 0.16 with two 28-node sets
+    // per warp), 12 warps x 1 up to 2,048 (8,192 nodes: 0.30 against 0.26
+    // with global staging), 8 warps x 2 up to 8,192 (16,384 and 32,768
+    // nodes: 0.43 and 0.55 against 0.38 and 0.49).
     if (!c.staging && !c.warps_per_block && !c.blocks_per_sm && !c.pairs_per_tile && !c.positions_per_tile &&
         c.tail_slices <= 1 && npw == 32 && inst->compact && G >= 4) {
         const int64_t items = (std::max<int64_t>(N, 1) + 31) / 32 * G;
-        if (items >= 1024 && items <= 4096) {
-            c.staging = FSP_STAGING_GLOBAL;
-            c.warps_per_block = 2;
-            c.blocks_per_sm = 8;
+        if (items >= 768 && items <= 8192) {
+            c.staging = FSP_STAGING_SPLIT;
+            c.warps_per_block = items < 1024 ? 6 : items <= 2048 ? 12 : 8;
+            c.blocks_per_sm = c.warps_per_block == 12 ? 1 : 2;
+            c.pairs_per_tile = items > 4096 ? 64 : 32;
         }
     }
     if (c.staging == FSP_STAGING_GLOBAL) {
