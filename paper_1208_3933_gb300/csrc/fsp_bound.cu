@@ -428,10 +428,22 @@ fsp_status resolve_lanes(const fsp_instance *inst, int64_t N, const DeviceLimits
         c.tail_slices <= 1 && npw == 32 && inst->compact && G >= 4) {
         const int64_t items = (std::max<int64_t>(N, 1) + 31) / 32 * G;
         if (items >= 768 && items <= 8192) {
-            c.staging = FSP_STAGING_SPLIT;
-            c.warps_per_block = items < 1024 ? 6 : items <= 2048 ? 12 : 8;
-            c.blocks_per_sm = c.warps_per_block == 12 ? 1 : 2;
-            c.pairs_per_tile = items > 4096 ? 64 : 32;
+            fsp_launch_config t = c;
+            t.staging = FSP_STAGING_SPLIT;
+            t.warps_per_block = items < 1024 ? 6 : items <= 2048 ? 12 : 8;
+            t.blocks_per_sm = t.warps_per_block == 12 ? 1 : 2;
+            t.pairs_per_tile = items > 4096 ? 64 : 32;
+            // only where a tile of 64 positions (or all of them) fits: the
+            // tile chosen below is at least that large, else the pool keeps
+            // the shape chosen further down
+            t.positions_per_tile = std::min(inst->npad, 64) & ~3;
+            size_t smem = 0;
+            if (lanes_layout(inst, t, &smem) == FSP_OK) {
+                c.staging = t.staging;
+                c.warps_per_block = t.warps_per_block;
+                c.blocks_per_sm = t.blocks_per_sm;
+                c.pairs_per_tile = t.pairs_per_tile;
+            }
         }
     }
     if (c.staging == FSP_STAGING_GLOBAL) {
