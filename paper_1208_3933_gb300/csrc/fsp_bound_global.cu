@@ -72,14 +72,6 @@ __global__ void __launch_bounds__(512, 1) fsp_lanes_global(const LanesArgs a) {
 }
 namespace {
 
-template <typename K>
-cudaError_t set_smem_attr(K kernel) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-}
-
 template <int MP>
 cudaError_t launch_global_variant(const LanesArgs &a, int grid, int threads, size_t smem, cudaStream_t s) {
     static std::once_flag once;

@@ -249,14 +249,6 @@ LanesLayout lanes_layout_for(const fsp_instance *inst, int warps, bool resident,
     return L;
 }
 
-template <typename K>
-cudaError_t set_smem_attr(K kernel) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-}
-
 template <bool WIDE, int MP>
 cudaError_t launch_lanes_variant(const LanesArgs &a, bool resident, int npw, int grid, int threads, size_t smem,
                                  cudaStream_t s) {

@@ -261,14 +261,6 @@ ScanLayout scan_layout_for(const fsp_instance *inst, int warps, int chunk) {
     return L;
 }
 
-template <typename K>
-cudaError_t set_smem_attr(K kernel) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-}
-
 // Launches prep then scan for one chunk; the prep grid fills the device once
 // (resident blocks per SM from the occupancy calculator).
 template <bool WIDE, int MP>

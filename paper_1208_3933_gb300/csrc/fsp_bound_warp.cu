@@ -170,14 +170,6 @@ WarpLayout warp_layout_for(const fsp_instance *inst, int warps, int chunk) {
     return L;
 }
 
-template <typename K>
-cudaError_t set_smem_attr(K kernel) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-}
-
 template <bool WIDE, int MP>
 cudaError_t launch_warp_variant(const LanesArgs &a, const WarpLayout &L, int grid, int threads, cudaStream_t s) {
     static std::once_flag once;

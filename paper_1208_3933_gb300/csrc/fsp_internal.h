@@ -55,6 +55,16 @@
 
 namespace fspgb {
 
+// Lets a kernel take the device's opt-in maximum of dynamic shared memory
+// (the current device; callers do this once per kernel and device).
+template <typename K>
+inline cudaError_t set_smem_attr(K kernel) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
 constexpr int kThreads = 128;          // threads per bounding block
 constexpr int kRecAlign = 4;           // couple rows padded to 4 entries (16 B compact)
 
