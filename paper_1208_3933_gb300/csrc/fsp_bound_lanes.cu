@@ -43,8 +43,8 @@
 //             small pool spreads one warp per item over the GPU
 //             (fsp_bound_global.cu);
 //   split     and warp staging: fsp_bound_split.cu, fsp_bound_warp.cu.
-// Global and one-set streamed staging keep the processing times in shared
-// memory when they fit.
+// Global, one-set streamed and split staging (its prep kernel) keep the
+// processing times in shared memory, one byte each, when they fit.
 //
 // Setup, one lane per node (fsp_lanes_device.cuh): (1) one pass over the
 // prefix for the membership bitmaps, row validation, the prefix recurrence
